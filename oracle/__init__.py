@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for the reformulated Phase Locking Value.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only callers.  The product library never
+imports this package and shares no code with it.
+
+The arithmetic lives in ``plv_oracle.c`` (plain C, FP64, OpenMP over rows):
+direct-DFT analytic signal (Section II.A, Eq. 3), phase extraction, the
+original pairwise mean of exp(i(phi_i - phi_j)) (Eq. 2) and the read-outs PLV
+(Eq. 7), iPLV (Eq. 13) and ciPLV (Eq. 14).  ``backward.py`` holds the gradient
+references (central finite differences of this oracle, and a plain-torch FP64
+autograd graph).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "plv_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, -O2, no fast-math, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d = ctypes.POINTER(ctypes.c_double)
+            L = ctypes.c_long
+            lib.oracle_analytic.argtypes = [d, L, L, L, d, d]
+            lib.oracle_plv_pairwise_rows.argtypes = [
+                d, d, L, L, ctypes.POINTER(ctypes.c_long), L, d, d, d, d, d]
+            lib.oracle_plv_pairwise.argtypes = [d, d, L, L, d, d, d, d, d]
+            lib.oracle_gram_direct.argtypes = [d, d, L, L, d, d]
+            lib.oracle_metrics.argtypes = [d, d, L, d, d, d]
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_max_threads.restype = ctypes.c_int
+            for f in ("oracle_analytic", "oracle_plv_pairwise_rows",
+                      "oracle_plv_pairwise", "oracle_gram_direct",
+                      "oracle_metrics"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return ctypes.POINTER(ctypes.c_double)()
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def analytic(x: np.ndarray) -> np.ndarray:
+    """Analytic signal z = x + i H{x} of each row of real ``x`` (..., T), by
+    direct DFT in FP64 (Eq. 3).  Returns complex128 of the same shape."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    shape = x.shape
+    T = shape[-1]
+    rows = int(np.prod(shape[:-1])) if len(shape) > 1 else 1
+    x2 = x.reshape(rows, T)
+    zr = np.empty((rows, T))
+    zi = np.empty((rows, T))
+    rc = _load().oracle_analytic(_p(x2), rows, T, T, _p(zr), _p(zi))
+    if rc != 0:
+        raise RuntimeError("oracle_analytic failed")
+    return (zr + 1j * zi).reshape(shape)
+
+
+def pairwise(z: np.ndarray, rows=None) -> dict:
+    """Original pairwise definition (Eq. 2) on one analytic signal ``z``
+    (N, T) complex.  Returns dict with c (complex), plv, iplv, ciplv for pairs
+    (rows[r], j); ``rows`` defaults to all rows."""
+    z = np.asarray(z)
+    N, T = z.shape
+    zr = np.ascontiguousarray(z.real, dtype=np.float64)
+    zi = np.ascontiguousarray(z.imag, dtype=np.float64)
+    if rows is None:
+        rows = np.arange(N)
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    nr = rows.shape[0]
+    cr = np.empty((nr, N))
+    ci = np.empty((nr, N))
+    plv = np.empty((nr, N))
+    iplv = np.empty((nr, N))
+    ciplv = np.empty((nr, N))
+    rp = rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long))
+    rc = _load().oracle_plv_pairwise_rows(_p(zr), _p(zi), N, T, rp, nr,
+                                          _p(cr), _p(ci), _p(plv), _p(iplv),
+                                          _p(ciplv))
+    if rc != 0:
+        raise RuntimeError("oracle_plv_pairwise_rows failed")
+    return {"c": cr + 1j * ci, "plv": plv, "iplv": iplv, "ciplv": ciplv}
+
+
+def gram_direct(z: np.ndarray) -> np.ndarray:
+    """Reformulated definition (Eq. 5-7) as a plain FP64 loop; (N, N)
+    complex.  Used only to check the paper's equivalence claim."""
+    z = np.asarray(z)
+    N, T = z.shape
+    zr = np.ascontiguousarray(z.real, dtype=np.float64)
+    zi = np.ascontiguousarray(z.imag, dtype=np.float64)
+    cr = np.empty((N, N))
+    ci = np.empty((N, N))
+    rc = _load().oracle_gram_direct(_p(zr), _p(zi), N, T, _p(cr), _p(ci))
+    if rc != 0:
+        raise RuntimeError("oracle_gram_direct failed")
+    return cr + 1j * ci
+
+
+def metrics(c: np.ndarray) -> dict:
+    """Read-outs PLV (Eq. 7), iPLV (Eq. 13, absolute) and ciPLV (Eq. 14) of
+    complex values ``c``; ciPLV = 0 where (1 - Re c)(1 + Re c) <= 0."""
+    c = np.asarray(c, dtype=np.complex128)
+    cr = np.ascontiguousarray(c.real).ravel()
+    ci = np.ascontiguousarray(c.imag).ravel()
+    n = cr.shape[0]
+    plv = np.empty(n)
+    iplv = np.empty(n)
+    ciplv = np.empty(n)
+    rc = _load().oracle_metrics(_p(cr), _p(ci), n, _p(plv), _p(iplv),
+                                _p(ciplv))
+    if rc != 0:
+        raise RuntimeError("oracle_metrics failed")
+    return {"plv": plv.reshape(c.shape), "iplv": iplv.reshape(c.shape),
+            "ciplv": ciplv.reshape(c.shape)}
+
+
+def connectivity(x: np.ndarray) -> dict:
+    """Whole path for one epoch: real x (N, T) -> analytic signal (Eq. 3) ->
+    pairwise PLV / iPLV / ciPLV (Eq. 2, 13, 14) for all ordered pairs."""
+    z = analytic(x)
+    out = pairwise(z)
+    out["z"] = z
+    return out
+
+
+def connectivity_pairs(x: np.ndarray, pairs_i, pairs_j) -> dict:
+    """Sampled outputs of the whole path for one epoch: only the rows named
+    in ``pairs_i`` / ``pairs_j`` get their analytic signal, then the pairwise
+    definition is evaluated for each (i, j).  Cost scales with the sample,
+    not with N."""
+    pairs_i = np.asarray(pairs_i, dtype=np.int64)
+    pairs_j = np.asarray(pairs_j, dtype=np.int64)
+    need = np.unique(np.concatenate([pairs_i, pairs_j]))
+    pos = {int(r): k for k, r in enumerate(need)}
+    z = analytic(np.asarray(x)[need])
+    c = np.empty(pairs_i.shape[0], dtype=np.complex128)
+    # one pairwise call per distinct row i over the needed columns
+    for i in np.unique(pairs_i):
+        sel = np.nonzero(pairs_i == i)[0]
+        res = pairwise(z, rows=[pos[int(i)]])
+        cols = np.array([pos[int(j)] for j in pairs_j[sel]])
+        c[sel] = res["c"][0, cols]
+    out = metrics(c)
+    diag = pairs_i == pairs_j
+    out["iplv"][diag] = 0.0
+    out["ciplv"][diag] = 0.0
+    out["c"] = c
+    return out
