@@ -1,0 +1,161 @@
+/*
+ * plv.h -- C ABI of the GB300 Phase Locking Value library.
+ *
+ * Computes, for every epoch of real band-limited signals x (N channels x T
+ * samples), the time-averaged phase locking value of Bruna, Maestu & Pereda,
+ * "Phase Locking Value revisited", in its reformulated form:
+ *
+ *   z   = x + i H{x}                 analytic signal            (Eq. 3)
+ *   P   = z / |z|                    unit phasors               (Eq. 4)
+ *   C   = P P^H / T                  Hermitian Gram             (Eq. 5-7)
+ *   PLV = |C|, iPLV = |Im C|,                                   (Eq. 7, 13)
+ *   ciPLV = Im C / sqrt((1 - Re C)(1 + Re C))                   (Eq. 14)
+ *
+ * Conventions shared by every entry point
+ *   - All data pointers are DEVICE pointers unless stated otherwise, owned by
+ *     the caller; the library never frees them.  The handle owns its own
+ *     workspace (twiddle tables, a device status word, backward scratch).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Every call is asynchronous on that stream.
+ *   - Arguments are validated on the host before anything is launched; a
+ *     validation failure returns PLV_ERR_INVALID (or PLV_ERR_UNSUPPORTED for
+ *     a valid but unimplemented shape) and launches nothing.
+ *   - Device-side failures (a bounded wait that gave up) are recorded in the
+ *     handle's device status word; plv_sync_status() reads and clears it.
+ *   - plv_last_error() returns a message for the last failing call made on
+ *     the calling thread; the string is owned by the library.
+ *   - Sign convention: C_ij = (1/T) sum_t P_i(t) conj(P_j(t)), so Im C_ij > 0
+ *     (and ciPLV_ij > 0) when channel i leads channel j.
+ *   - Readings where the paper is silent: a sample with |z| = 0 has P = 0 and
+ *     contributes nothing; ciPLV = 0 where (1 - Re C)(1 + Re C) <= 0; the
+ *     diagonal of iPLV and ciPLV is 0; the analytic signal is the periodic
+ *     discrete one over exactly the T samples given (no padding inside).
+ *   - Outputs are full N x N squares per epoch: the upper triangle is
+ *     computed and mirrored (PLV, iPLV symmetric; ciPLV antisymmetric, bit
+ *     for bit).
+ */
+#ifndef PLV_H
+#define PLV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct plv_handle plv_handle;
+
+typedef enum {
+    PLV_OK = 0,
+    PLV_ERR_INVALID = 1,     /* bad argument: null pointer, negative size... */
+    PLV_ERR_ALLOC = 2,       /* device or host allocation failed            */
+    PLV_ERR_CUDA = 3,        /* a CUDA runtime call failed                  */
+    PLV_ERR_UNSUPPORTED = 4, /* valid request this build does not implement */
+    PLV_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up          */
+    PLV_ERR_NUMERIC = 6      /* reserved: non-finite data in checked mode   */
+} plv_status;
+
+typedef enum { PLV_F32 = 0, PLV_F64 = 1 } plv_dtype;
+
+/* Arithmetic of the Gram (Eq. 7).  FP32: FP32 phasors, FP32 FMA on the CUDA
+ * cores.  BF16X3: each phasor component split as hi + lo, two BF16 numbers;
+ * the Gram is hi*hi + hi*lo + lo*hi on the tensor cores (tcgen05) with FP32
+ * accumulation. */
+typedef enum { PLV_PREC_FP32 = 0, PLV_PREC_BF16X3 = 1 } plv_precision;
+
+enum {
+    PLV_OUT_PLV = 1,   /* |C|                         (Eq. 7)  */
+    PLV_OUT_IPLV = 2,  /* |Im C|                      (Eq. 13) */
+    PLV_OUT_CIPLV = 4, /* Im C / sqrt(1 - (Re C)^2)   (Eq. 14) */
+    PLV_OUT_C = 8      /* C itself, complex64 interleaved      */
+};
+
+/* Create a handle bound to CUDA device `device` with Gram arithmetic `prec`.
+ * `workspace_limit` caps the handle's device workspace in bytes (0 = no
+ * cap).  Allocates (cudaMalloc) -- call outside stream capture.
+ * Errors: PLV_ERR_INVALID (h NULL, bad device or precision), PLV_ERR_CUDA,
+ * PLV_ERR_ALLOC. */
+plv_status plv_create(plv_handle **h, int device, plv_precision prec,
+                      size_t workspace_limit);
+
+/* Destroy a handle and free its workspace (synchronises the device).  NULL
+ * is accepted and ignored. */
+plv_status plv_destroy(plv_handle *h);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *plv_last_error(const plv_handle *h);
+
+/* Gram arithmetic the handle was created with. */
+plv_precision plv_get_precision(const plv_handle *h);
+
+/* Row length (in elements) of the phasor operand layout for T samples: T
+ * rounded up to a multiple of 32; the padding samples are zero. */
+int64_t plv_phasor_ld(int T);
+
+/* Bytes of the phasor operand buffer P for `batch` epochs of N x T (both
+ * precisions use 8 bytes per padded sample):
+ *   FP32:   float  P[batch][N][2][ld]        plane 0 = Re P, 1 = Im P
+ *   BF16X3: bf16   P[batch][4][N][ld]        planes Re_hi, Re_lo, Im_hi, Im_lo
+ * with ld = plv_phasor_ld(T).  Returns 0 for invalid sizes. */
+size_t plv_phasor_bytes(const plv_handle *h, int batch, int N, int T);
+
+/* Make the handle's per-length tables for T samples (twiddles).  The first
+ * plv_analytic / plv_backward call for a new T does this implicitly; call it
+ * beforehand when those calls are to be captured in a CUDA graph. */
+plv_status plv_prepare(plv_handle *h, int T);
+
+/* Eq. 3 + Eq. 4, fused (Section II.A): analytic signal of every row of x by
+ * FFT (forward transform, multiply by the analytic mask, inverse transform)
+ * and unit phasors P = z/|z| written in the handle's operand layout.
+ *   x    : real, [batch][N][ldx] (ldx >= T), dtype F32 or F64 (F64 is
+ *          converted to FP32 on load; the arithmetic is FP32).
+ *   P    : plv_phasor_bytes(h, batch, N, T) bytes, written completely
+ *          (including zero padding).
+ * Supported T: powers of two, 32 <= T <= 16384 (others: PLV_ERR_UNSUPPORTED).
+ * batch = 0 or N = 0 is a no-op. */
+plv_status plv_analytic(plv_handle *h, void *stream, const void *x,
+                        plv_dtype dtype, int batch, int N, int T, int64_t ldx,
+                        void *P);
+
+/* Eq. 4 alone, for callers that already hold an analytic signal (for
+ * example from a wavelet transform): P = z/|z| in the operand layout.
+ *   z    : complex interleaved (re, im), [batch][N][ldz] complex elements,
+ *          ldz >= T; dtype F32 (complex64) or F64 (complex128).
+ * Any T >= 1. */
+plv_status plv_normalize(plv_handle *h, void *stream, const void *z,
+                         plv_dtype dtype, int batch, int N, int T, int64_t ldz,
+                         void *P);
+
+/* Eq. 7, 13, 14 (Section II.A, II.C): the Hermitian Gram C = P P^H / T of
+ * every epoch (upper-triangle tiles only) with the read-outs fused into its
+ * epilogue.
+ *   P        : operand buffer written by plv_analytic / plv_normalize for the
+ *              same (batch, N, T) and the same handle precision.
+ *   out_mask : OR of PLV_OUT_*; an output whose bit is clear, or whose
+ *              pointer is NULL, is not written.
+ *   plv, iplv, ciplv : float [batch][N][N] row-major.
+ *   C        : complex64 interleaved [batch][N][N] (8 bytes per entry).
+ *   diag_dev : double [batch] or NULL: max_i |C_ii - 1| per epoch, the unit-
+ *              modulus check of Eq. 4 (1/T applied in FP64).
+ * FP64 is used only for the ciPLV denominator (1 - Re C)(1 + Re C) and the
+ * diagonal check. */
+plv_status plv_gram(plv_handle *h, void *stream, const void *P, int batch,
+                    int N, int T, unsigned out_mask, float *plv, float *iplv,
+                    float *ciplv, void *C, double *diag_dev);
+
+/* Eq. 7, 13, 14 applied elementwise to a stored C (complex64 interleaved,
+ * [batch][N][N]); the same arithmetic as the fused epilogue, including the
+ * zero diagonal of iPLV / ciPLV.  NULL outputs are skipped. */
+plv_status plv_metrics(plv_handle *h, void *stream, const void *C, int batch,
+                       int N, float *plv, float *iplv, float *ciplv);
+
+/* Read (and clear) the handle's device status word after synchronising
+ * `stream`.  *device_status receives PLV_OK or the recorded error. */
+plv_status plv_sync_status(plv_handle *h, void *stream, int *device_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLV_H */

@@ -1,0 +1,169 @@
+"""GB300 Phase Locking Value: Python binding of the C ABI (include/plv.h).
+
+    import torch, paper_1710_08037_gb300 as plv
+    h = plv.Handle(precision="bf16x3")
+    out = h.connectivity(x)           # x: (E, N, T) float32 / float64, cuda
+    out["plv"], out["iplv"], out["ciplv"]   # (E, N, N) float32 each
+
+The functions mirror the C entry points (``plv_analytic``, ``plv_gram``, ...)
+and only marshal arguments: torch supplies device memory and the current
+stream; every computation runs in the library's CUDA kernels.  There is no
+CPU fallback -- without a GPU or without the built library, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (PLV_F32, PLV_F64, PLV_OUT_C, PLV_OUT_CIPLV, PLV_OUT_IPLV,
+                   PLV_OUT_PLV, PLV_PREC_BF16X3, PLV_PREC_FP32, PlvError)
+
+__all__ = ["Handle", "PlvError", "phasor_ld", "PLV_PREC_FP32",
+           "PLV_PREC_BF16X3"]
+
+_PREC = {"fp32": PLV_PREC_FP32, "bf16x3": PLV_PREC_BF16X3,
+         PLV_PREC_FP32: PLV_PREC_FP32, PLV_PREC_BF16X3: PLV_PREC_BF16X3}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dtype_code(t):
+    if t.dtype in (torch.float32, torch.complex64):
+        return PLV_F32
+    if t.dtype in (torch.float64, torch.complex128):
+        return PLV_F64
+    raise PlvError(_lib.PLV_ERR_INVALID, f"unsupported dtype {t.dtype}")
+
+
+def phasor_ld(T: int) -> int:
+    """Padded row length of the phasor operand layout."""
+    return int(_lib.load().plv_phasor_ld(int(T)))
+
+
+class Handle:
+    """Owns a ``plv_handle`` (device, Gram precision, workspace)."""
+
+    def __init__(self, precision="fp32", device=None, workspace_limit=0):
+        if not torch.cuda.is_available():
+            raise PlvError(_lib.PLV_ERR_UNSUPPORTED,
+                           "no CUDA device: this library has no CPU path")
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()
+                                   if device is None else int(device))
+        self.precision = _PREC[precision]
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.plv_create(ctypes.byref(h), self.device.index,
+                                       self.precision, int(workspace_limit)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.plv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- C entry points ---------------------------------------------------
+    def phasor_bytes(self, batch, N, T) -> int:
+        return int(self.lib.plv_phasor_bytes(self.h, batch, N, T))
+
+    def empty_phasors(self, batch, N, T):
+        nb = self.phasor_bytes(batch, N, T)
+        return torch.empty(max(nb, 16) // 4, dtype=torch.float32,
+                           device=self.device)
+
+    def prepare(self, T: int):
+        _lib.check(self.lib.plv_prepare(self.h, int(T)), self.h)
+
+    def plv_analytic(self, x, P=None):
+        """Eq. 3 + 4: x (batch, N, T) real on the device -> phasors P."""
+        assert x.is_cuda and x.dim() == 3
+        B, N, T = x.shape
+        if not (x.stride(-1) == 1 and (N == 1 or x.stride(0) == N * x.stride(1))):
+            x = x.contiguous()
+        ldx = x.stride(1) if N > 1 else max(x.stride(0), T)
+        if P is None:
+            P = self.empty_phasors(B, N, T)
+        _lib.check(self.lib.plv_analytic(self.h, _stream(self.device), _ptr(x),
+                                         _dtype_code(x), B, N, T, ldx,
+                                         _ptr(P)), self.h)
+        return P
+
+    def plv_normalize(self, z, P=None):
+        """Eq. 4 on a given complex analytic signal z (batch, N, T)."""
+        assert z.is_cuda and z.dim() == 3 and z.is_complex()
+        z = z.contiguous()
+        B, N, T = z.shape
+        if P is None:
+            P = self.empty_phasors(B, N, T)
+        _lib.check(self.lib.plv_normalize(self.h, _stream(self.device),
+                                          _ptr(z), _dtype_code(z), B, N, T, T,
+                                          _ptr(P)), self.h)
+        return P
+
+    def plv_gram(self, P, batch, N, T, plv=True, iplv=True, ciplv=True,
+                 C=False, diag=False, out=None):
+        """Eq. 7, 13, 14: Gram of the phasors with fused read-outs."""
+        dev = self.device
+        res = {} if out is None else dict(out)
+
+        def mk(key, want, shape, dtype):
+            if not want:
+                return None
+            if key not in res:
+                res[key] = torch.empty(shape, dtype=dtype, device=dev)
+            return res[key]
+
+        o_plv = mk("plv", plv, (batch, N, N), torch.float32)
+        o_iplv = mk("iplv", iplv, (batch, N, N), torch.float32)
+        o_ci = mk("ciplv", ciplv, (batch, N, N), torch.float32)
+        o_C = mk("C", C, (batch, N, N), torch.complex64)
+        o_d = mk("diag", diag, (batch,), torch.float64)
+        mask = ((PLV_OUT_PLV if plv else 0) | (PLV_OUT_IPLV if iplv else 0) |
+                (PLV_OUT_CIPLV if ciplv else 0) | (PLV_OUT_C if C else 0))
+        _lib.check(self.lib.plv_gram(self.h, _stream(dev), _ptr(P), batch, N,
+                                     T, mask, _ptr(o_plv), _ptr(o_iplv),
+                                     _ptr(o_ci), _ptr(o_C), _ptr(o_d)),
+                   self.h)
+        return res
+
+    def plv_metrics(self, C):
+        """Eq. 7, 13, 14 elementwise on a stored complex64 C (batch, N, N)."""
+        assert C.is_cuda and C.dtype == torch.complex64
+        C = C.contiguous()
+        B, N, _ = C.shape
+        res = {k: torch.empty((B, N, N), dtype=torch.float32,
+                              device=self.device)
+               for k in ("plv", "iplv", "ciplv")}
+        _lib.check(self.lib.plv_metrics(self.h, _stream(self.device), _ptr(C),
+                                        B, N, _ptr(res["plv"]),
+                                        _ptr(res["iplv"]),
+                                        _ptr(res["ciplv"])), self.h)
+        return res
+
+    def plv_sync_status(self) -> int:
+        v = ctypes.c_int(0)
+        _lib.check(self.lib.plv_sync_status(self.h, _stream(self.device),
+                                            ctypes.byref(v)), self.h)
+        return int(v.value)
+
+    # ---- convenience ------------------------------------------------------
+    def connectivity(self, x, C=False, diag=False, out=None, P=None):
+        """Whole forward path on real x (E, N, T): analytic signal, phasors,
+        Gram and read-outs.  Returns a dict of (E, N, N) tensors."""
+        E, N, T = x.shape
+        P = self.plv_analytic(x, P)
+        res = self.plv_gram(P, E, N, T, C=C, diag=diag, out=out)
+        return res

@@ -1,0 +1,95 @@
+"""ctypes binding to libplv.so (the C ABI of include/plv.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind these entry points.  There is no CPU fallback: if the library
+is missing or a call fails, a ``PlvError`` is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PLV_OK = 0
+PLV_ERR_INVALID = 1
+PLV_ERR_ALLOC = 2
+PLV_ERR_CUDA = 3
+PLV_ERR_UNSUPPORTED = 4
+PLV_ERR_TIMEOUT = 5
+PLV_ERR_NUMERIC = 6
+
+PLV_F32 = 0
+PLV_F64 = 1
+PLV_PREC_FP32 = 0
+PLV_PREC_BF16X3 = 1
+PLV_OUT_PLV = 1
+PLV_OUT_IPLV = 2
+PLV_OUT_CIPLV = 4
+PLV_OUT_C = 8
+
+STATUS_NAMES = {0: "PLV_OK", 1: "PLV_ERR_INVALID", 2: "PLV_ERR_ALLOC",
+                3: "PLV_ERR_CUDA", 4: "PLV_ERR_UNSUPPORTED",
+                5: "PLV_ERR_TIMEOUT", 6: "PLV_ERR_NUMERIC"}
+
+# every entry point include/plv.h declares: name -> (restype, argtypes)
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_u = ctypes.c_uint
+_sz = ctypes.c_size_t
+SIGNATURES = {
+    "plv_create": (_i, [ctypes.POINTER(_vp), _i, _i, _sz]),
+    "plv_destroy": (_i, [_vp]),
+    "plv_last_error": (ctypes.c_char_p, [_vp]),
+    "plv_get_precision": (_i, [_vp]),
+    "plv_phasor_ld": (_i64, [_i]),
+    "plv_phasor_bytes": (_sz, [_vp, _i, _i, _i]),
+    "plv_prepare": (_i, [_vp, _i]),
+    "plv_analytic": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i64, _vp]),
+    "plv_normalize": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i64, _vp]),
+    "plv_gram": (_i, [_vp, _vp, _vp, _i, _i, _i, _u, _vp, _vp, _vp, _vp,
+                      _vp]),
+    "plv_metrics": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp]),
+    "plv_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PlvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) libplv.so and declare signatures."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(path):
+                raise PlvError(PLV_ERR_UNSUPPORTED,
+                               f"CUDA library not built: {path}")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(status: int, handle=None):
+    if status != PLV_OK:
+        msg = load().plv_last_error(handle)
+        raise PlvError(status, msg.decode() if msg else "")

@@ -1,0 +1,274 @@
+// plv_api.cu -- the C ABI (include/plv.h): handle life cycle, host-side
+// validation, dispatch to the kernels, status reporting.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace plv {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+plv_status fail(plv_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+plv_status check_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return PLV_OK;
+    return fail(PLV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes the handle's device current for the scope and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+            cudaSetDevice(prev);
+    }
+};
+
+static int log2_exact(int T) {
+    if (T <= 0 || (T & (T - 1))) return -1;
+    int l = 0;
+    while ((1 << l) < T) ++l;
+    return l;
+}
+
+}  // namespace plv
+
+using namespace plv;
+
+#define PLV_GUARD(hh)                                                      \
+    DeviceGuard guard_((hh)->device);                                      \
+    if (!guard_.ok) return fail(PLV_ERR_CUDA, "cannot select device %d",  \
+                                (hh)->device)
+
+extern "C" {
+
+plv_status plv_create(plv_handle **out, int device, plv_precision prec,
+                      size_t workspace_limit) {
+    if (!out) return fail(PLV_ERR_INVALID, "plv_create: handle pointer is NULL");
+    *out = nullptr;
+    if (prec != PLV_PREC_FP32 && prec != PLV_PREC_BF16X3)
+        return fail(PLV_ERR_INVALID, "plv_create: unknown precision %d", (int)prec);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(PLV_ERR_INVALID, "plv_create: no CUDA device %d", device);
+    plv_handle *hp = new (std::nothrow) plv_handle();
+    if (!hp) return fail(PLV_ERR_ALLOC, "plv_create: out of host memory");
+    Handle &h = hp->h;
+    h.device = device;
+    h.prec = prec;
+    h.workspace_limit = workspace_limit;
+    DeviceGuard guard(device);
+    if (!guard.ok) { delete hp; return fail(PLV_ERR_CUDA, "cannot select device %d", device); }
+    plv_status st = check_cuda(
+        cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, device),
+        "cudaDeviceGetAttribute");
+    // twiddle tables exp(-2 pi i m / 2^L), rounded from FP64
+    size_t ntw = ((size_t)1 << (kMaxLog2T + 1)) - ((size_t)1 << kMinLog2T);
+    std::vector<float2> tw(ntw);
+    for (int L = kMinLog2T; L <= kMaxLog2T; ++L) {
+        const size_t base = ((size_t)1 << L) - ((size_t)1 << kMinLog2T);
+        const int T = 1 << L;
+        for (int m = 0; m < T; ++m) {
+            const double a = 2.0 * M_PI * (double)m / (double)T;
+            tw[base + m] = make_float2((float)cos(a), (float)-sin(a));
+        }
+    }
+    const size_t need = ntw * sizeof(float2) + 256;
+    if (st == PLV_OK && workspace_limit && need > workspace_limit)
+        st = fail(PLV_ERR_ALLOC, "plv_create: workspace limit %zu below %zu bytes",
+                  workspace_limit, need);
+    if (st == PLV_OK)
+        st = check_cuda(cudaMalloc(&h.twiddles, ntw * sizeof(float2)), "cudaMalloc(twiddles)");
+    if (st == PLV_OK)
+        st = check_cuda(cudaMemcpy(h.twiddles, tw.data(), ntw * sizeof(float2),
+                                   cudaMemcpyHostToDevice), "cudaMemcpy(twiddles)");
+    if (st == PLV_OK)
+        st = check_cuda(cudaMalloc(&h.status, 256), "cudaMalloc(status)");
+    if (st == PLV_OK)
+        st = check_cuda(cudaMemset(h.status, 0, 256), "cudaMemset(status)");
+    if (st != PLV_OK) {
+        if (h.twiddles) cudaFree(h.twiddles);
+        if (h.status) cudaFree(h.status);
+        delete hp;
+        return st;
+    }
+    h.workspace_used = need;
+    *out = hp;
+    return PLV_OK;
+}
+
+plv_status plv_destroy(plv_handle *hp) {
+    if (!hp) return PLV_OK;
+    Handle &h = hp->h;
+    {
+        DeviceGuard guard(h.device);
+        cudaDeviceSynchronize();
+        if (h.twiddles) cudaFree(h.twiddles);
+        if (h.status) cudaFree(h.status);
+    }
+    delete hp;
+    return PLV_OK;
+}
+
+const char *plv_last_error(const plv_handle *) { return g_err.c_str(); }
+
+plv_precision plv_get_precision(const plv_handle *hp) {
+    return hp ? hp->h.prec : PLV_PREC_FP32;
+}
+
+int64_t plv_phasor_ld(int T) { return T > 0 ? padded_len(T) : 0; }
+
+size_t plv_phasor_bytes(const plv_handle *, int batch, int N, int T) {
+    if (batch < 0 || N < 0 || T <= 0) return 0;
+    return (size_t)batch * (size_t)N * (size_t)padded_len(T) * 8u;
+}
+
+plv_status plv_prepare(plv_handle *hp, int T) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_prepare: handle is NULL");
+    if (T <= 0) return fail(PLV_ERR_INVALID, "plv_prepare: T = %d", T);
+    const int L = log2_exact(T);
+    if (L < kMinLog2T || L > kMaxLog2T)
+        return fail(PLV_ERR_UNSUPPORTED,
+                    "plv_prepare: T = %d (this build's FFT takes powers of two "
+                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2T);
+    return PLV_OK;  // power-of-two tables are made by plv_create
+}
+
+plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
+                        plv_dtype dtype, int batch, int N, int T, int64_t ldx,
+                        void *P) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_analytic: handle is NULL");
+    if (batch < 0 || N < 0 || T <= 0)
+        return fail(PLV_ERR_INVALID, "plv_analytic: bad sizes batch=%d N=%d T=%d", batch, N, T);
+    if (dtype != PLV_F32 && dtype != PLV_F64)
+        return fail(PLV_ERR_INVALID, "plv_analytic: unknown dtype %d", (int)dtype);
+    if (ldx < T) return fail(PLV_ERR_INVALID, "plv_analytic: ldx %lld < T %d", (long long)ldx, T);
+    if (batch == 0 || N == 0) return PLV_OK;
+    if (!x || !P) return fail(PLV_ERR_INVALID, "plv_analytic: NULL data pointer");
+    const int L = log2_exact(T);
+    if (L < kMinLog2T || L > kMaxLog2T)
+        return fail(PLV_ERR_UNSUPPORTED,
+                    "plv_analytic: T = %d (this build's FFT takes powers of two "
+                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2T);
+    const size_t esz = dtype == PLV_F32 ? 4 : 8;
+    if (((uintptr_t)x % esz) != 0)
+        return fail(PLV_ERR_INVALID, "plv_analytic: x is not %zu-byte aligned", esz);
+    if (((uintptr_t)P % 16) != 0)
+        return fail(PLV_ERR_INVALID, "plv_analytic: P is not 16-byte aligned");
+    PLV_GUARD(&hp->h);
+    return check_cuda(launch_analytic_pow2(&hp->h, (cudaStream_t)stream, x, dtype,
+                                           (int64_t)batch * N, N, L, ldx, P),
+                      "plv_analytic launch");
+}
+
+plv_status plv_normalize(plv_handle *hp, void *stream, const void *z,
+                         plv_dtype dtype, int batch, int N, int T, int64_t ldz,
+                         void *P) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_normalize: handle is NULL");
+    if (batch < 0 || N < 0 || T <= 0)
+        return fail(PLV_ERR_INVALID, "plv_normalize: bad sizes batch=%d N=%d T=%d", batch, N, T);
+    if (dtype != PLV_F32 && dtype != PLV_F64)
+        return fail(PLV_ERR_INVALID, "plv_normalize: unknown dtype %d", (int)dtype);
+    if (ldz < T) return fail(PLV_ERR_INVALID, "plv_normalize: ldz < T");
+    if (batch == 0 || N == 0) return PLV_OK;
+    if (!z || !P) return fail(PLV_ERR_INVALID, "plv_normalize: NULL data pointer");
+    if (((uintptr_t)z % (dtype == PLV_F32 ? 8 : 16)) != 0 || ((uintptr_t)P % 16) != 0)
+        return fail(PLV_ERR_INVALID, "plv_normalize: misaligned pointer");
+    PLV_GUARD(&hp->h);
+    return check_cuda(launch_normalize(&hp->h, (cudaStream_t)stream, z, dtype,
+                                       (int64_t)batch * N, N, T, ldz, P),
+                      "plv_normalize launch");
+}
+
+plv_status plv_gram(plv_handle *hp, void *stream, const void *P, int batch,
+                    int N, int T, unsigned out_mask, float *plv, float *iplv,
+                    float *ciplv, void *C, double *diag_dev) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_gram: handle is NULL");
+    if (batch < 0 || N < 0 || T <= 0)
+        return fail(PLV_ERR_INVALID, "plv_gram: bad sizes batch=%d N=%d T=%d", batch, N, T);
+    if (out_mask & ~15u) return fail(PLV_ERR_INVALID, "plv_gram: unknown output bits");
+    if (batch == 0 || N == 0) return PLV_OK;
+    if (!P) return fail(PLV_ERR_INVALID, "plv_gram: P is NULL");
+    if (((uintptr_t)P % 16) != 0) return fail(PLV_ERR_INVALID, "plv_gram: P misaligned");
+    GramOut o;
+    o.plv = (out_mask & PLV_OUT_PLV) ? plv : nullptr;
+    o.iplv = (out_mask & PLV_OUT_IPLV) ? iplv : nullptr;
+    o.ciplv = (out_mask & PLV_OUT_CIPLV) ? ciplv : nullptr;
+    o.C = (out_mask & PLV_OUT_C) ? (float2 *)C : nullptr;
+    o.diag = diag_dev;
+    if (o.C && ((uintptr_t)o.C % 8) != 0)
+        return fail(PLV_ERR_INVALID, "plv_gram: C is not 8-byte aligned");
+    if ((int64_t)N * N > ((int64_t)1 << 40))
+        return fail(PLV_ERR_UNSUPPORTED, "plv_gram: N = %d too large", N);
+    PLV_GUARD(&hp->h);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (o.diag) {
+        plv_status st = check_cuda(cudaMemsetAsync(o.diag, 0, sizeof(double) * batch, s),
+                                   "plv_gram: clear diag");
+        if (st != PLV_OK) return st;
+    }
+    if (hp->h.prec == PLV_PREC_FP32)
+        return check_cuda(launch_gram_fp32(&hp->h, s, (const float *)P, batch, N, T, o),
+                          "plv_gram launch");
+    return fail(PLV_ERR_UNSUPPORTED, "plv_gram: BF16X3 Gram not built in this version");
+}
+
+plv_status plv_metrics(plv_handle *hp, void *stream, const void *C, int batch,
+                       int N, float *plv, float *iplv, float *ciplv) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_metrics: handle is NULL");
+    if (batch < 0 || N < 0) return fail(PLV_ERR_INVALID, "plv_metrics: bad sizes");
+    if (batch == 0 || N == 0) return PLV_OK;
+    if (!C) return fail(PLV_ERR_INVALID, "plv_metrics: C is NULL");
+    if (((uintptr_t)C % 8) != 0) return fail(PLV_ERR_INVALID, "plv_metrics: C misaligned");
+    PLV_GUARD(&hp->h);
+    return check_cuda(launch_metrics((cudaStream_t)stream, (const float2 *)C, batch, N,
+                                     plv, iplv, ciplv),
+                      "plv_metrics launch");
+}
+
+plv_status plv_sync_status(plv_handle *hp, void *stream, int *device_status) {
+    if (!hp || !device_status) return fail(PLV_ERR_INVALID, "plv_sync_status: NULL argument");
+    PLV_GUARD(&hp->h);
+    cudaStream_t s = (cudaStream_t)stream;
+    int v = 0;
+    plv_status st = check_cuda(cudaMemcpyAsync(&v, hp->h.status, sizeof(int),
+                                               cudaMemcpyDeviceToHost, s),
+                               "plv_sync_status: read");
+    if (st == PLV_OK) st = check_cuda(cudaStreamSynchronize(s), "plv_sync_status: sync");
+    if (st == PLV_OK && v != 0)
+        st = check_cuda(cudaMemsetAsync(hp->h.status, 0, sizeof(int), s),
+                        "plv_sync_status: clear");
+    *device_status = v;
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+"""Shared helpers for the GPU parity tests: reading the phasor operand
+layout back, and the tolerance rules."""
+import numpy as np
+import torch
+
+# Gram arithmetic tolerances against the FP64 oracle (absolute, on C, PLV and
+# iPLV).  FP32 path: 1e-5.  BF16x3 path: each component is hi + lo with
+# relative error <= 2^-17 after the split and the dropped lo*lo term, so every
+# product term of the Gram carries <= ~3 * 2^-17 ~ 2.3e-5 worst case; the
+# mean over T samples averages these, the stated bound is 2e-5.
+TOL = {"fp32": 1e-5, "bf16x3": 2e-5}
+
+
+def unpack_phasors(P, precision, B, N, T):
+    """Operand buffer -> complex128 numpy (B, N, T) (layout of plv.h)."""
+    ld = ((T + 31) // 32) * 32
+    if precision == "fp32":
+        a = P[: B * N * 2 * ld].view(B, N, 2, ld).double().cpu().numpy()
+        return a[:, :, 0, :T] + 1j * a[:, :, 1, :T]
+    b = P.view(torch.bfloat16)[: B * 4 * N * ld].view(B, 4, N, ld)
+    b = b.double().cpu().numpy()
+    return (b[:, 0, :, :T] + b[:, 1, :, :T]) + 1j * (b[:, 2, :, :T] +
+                                                     b[:, 3, :, :T])
+
+
+def ciplv_bound(c, eps):
+    """First-order error bound of ciPLV given an absolute error eps on Re C
+    and Im C: eps/sqrt(d) + |Im Re| eps / d^(3/2), d = 1 - Re^2 (Eq. 14)."""
+    re, im = c.real, c.imag
+    d = np.maximum((1 - re) * (1 + re), 1e-12)
+    return eps / np.sqrt(d) + np.abs(im * re) * eps / d ** 1.5
+
+
+def compare(gpu, ref, eps, off_diag_only=False):
+    """Assert |gpu - ref| within eps for PLV / iPLV and the conditioned
+    bound for ciPLV; ref holds the oracle's c, plv, iplv, ciplv (numpy)."""
+    c = ref["c"]
+    errs = {}
+    for k in ("plv", "iplv"):
+        e = np.abs(gpu[k] - ref[k])
+        errs[k] = float(e.max()) if e.size else 0.0
+        assert errs[k] <= eps, (k, errs[k])
+    bound = ciplv_bound(c, eps) + 1e-6
+    e = np.abs(gpu["ciplv"] - ref["ciplv"])
+    bad = e > bound
+    if off_diag_only:
+        pass
+    assert not np.any(bad), ("ciplv", float(e.max()), int(bad.sum()))
+    errs["ciplv"] = float(e.max()) if e.size else 0.0
+    return errs

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every symbol include/plv.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1710_08037_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "plv.h")
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(plv_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for n in ("plv_create", "plv_destroy", "plv_analytic", "plv_gram",
+              "plv_metrics", "plv_normalize", "plv_sync_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert sorted(_lib.SIGNATURES) == header_functions()
+
+
+def test_phasor_layout_helpers(lib):
+    """Pure host helpers: padded row length and operand bytes."""
+    lib.plv_phasor_ld.restype = ctypes.c_int64
+    lib.plv_phasor_ld.argtypes = [ctypes.c_int]
+    assert lib.plv_phasor_ld(1) == 32
+    assert lib.plv_phasor_ld(32) == 32
+    assert lib.plv_phasor_ld(500) == 512
+    assert lib.plv_phasor_ld(4096) == 4096
+    lib.plv_phasor_bytes.restype = ctypes.c_size_t
+    lib.plv_phasor_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int]
+    assert lib.plv_phasor_bytes(None, 30, 4096, 4096) == 30 * 4096 * 4096 * 8
+    assert lib.plv_phasor_bytes(None, -1, 4, 4) == 0
+
+
+def test_null_handle_is_rejected_without_a_device(lib):
+    """Host-side validation runs before any CUDA call."""
+    lib.plv_gram.restype = ctypes.c_int
+    rc = lib.plv_gram(None, None, None, 1, 4, 4, 1, None, None, None, None,
+                      None)
+    assert rc == _lib.PLV_ERR_INVALID
+    lib.plv_last_error.restype = ctypes.c_char_p
+    assert b"NULL" in lib.plv_last_error(None)
+    rc = lib.plv_create(None, 0, 0, ctypes.c_size_t(0))
+    assert rc == _lib.PLV_ERR_INVALID
