@@ -61,8 +61,13 @@ typedef enum { PLV_F32 = 0, PLV_F64 = 1 } plv_dtype;
 /* Arithmetic of the Gram (Eq. 7).  FP32: FP32 phasors, FP32 FMA on the CUDA
  * cores.  BF16X3: each phasor component split as hi + lo, two BF16 numbers;
  * the Gram is hi*hi + hi*lo + lo*hi on the tensor cores (tcgen05) with FP32
- * accumulation. */
-typedef enum { PLV_PREC_FP32 = 0, PLV_PREC_BF16X3 = 1 } plv_precision;
+ * accumulation.  FP16X3: the same with FP16 hi + lo (11-bit significands,
+ * so the split carries 22 bits instead of 16; same tensor-core rate). */
+typedef enum {
+    PLV_PREC_FP32 = 0,
+    PLV_PREC_BF16X3 = 1,
+    PLV_PREC_FP16X3 = 2
+} plv_precision;
 
 enum {
     PLV_OUT_PLV = 1,   /* |C|                         (Eq. 7)  */
@@ -97,6 +102,7 @@ int64_t plv_phasor_ld(int T);
  * precisions use 8 bytes per padded sample):
  *   FP32:   float  P[batch][N][2][ld]        plane 0 = Re P, 1 = Im P
  *   BF16X3: bf16   P[batch][4][N][ld]        planes Re_hi, Re_lo, Im_hi, Im_lo
+ *   FP16X3: half   P[batch][4][N][ld]        same planes, FP16 hi / lo
  * with ld = plv_phasor_ld(T).  Returns 0 for invalid sizes. */
 size_t plv_phasor_bytes(const plv_handle *h, int batch, int N, int T);
 

@@ -18,13 +18,15 @@ import torch
 
 from . import _lib
 from ._lib import (PLV_F32, PLV_F64, PLV_OUT_C, PLV_OUT_CIPLV, PLV_OUT_IPLV,
-                   PLV_OUT_PLV, PLV_PREC_BF16X3, PLV_PREC_FP32, PlvError)
+                   PLV_OUT_PLV, PLV_PREC_BF16X3, PLV_PREC_FP16X3,
+                   PLV_PREC_FP32, PlvError)
 
 __all__ = ["Handle", "PlvError", "phasor_ld", "PLV_PREC_FP32",
            "PLV_PREC_BF16X3"]
 
 _PREC = {"fp32": PLV_PREC_FP32, "bf16x3": PLV_PREC_BF16X3,
-         PLV_PREC_FP32: PLV_PREC_FP32, PLV_PREC_BF16X3: PLV_PREC_BF16X3}
+         "fp16x3": PLV_PREC_FP16X3, PLV_PREC_FP32: PLV_PREC_FP32,
+         PLV_PREC_BF16X3: PLV_PREC_BF16X3, PLV_PREC_FP16X3: PLV_PREC_FP16X3}
 
 
 def _ptr(t):

@@ -24,6 +24,7 @@ PLV_F32 = 0
 PLV_F64 = 1
 PLV_PREC_FP32 = 0
 PLV_PREC_BF16X3 = 1
+PLV_PREC_FP16X3 = 2
 PLV_OUT_PLV = 1
 PLV_OUT_IPLV = 2
 PLV_OUT_CIPLV = 4

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <map>
@@ -67,9 +68,13 @@ struct GramOut {
     float *plv, *iplv, *ciplv;
     float2 *C;
     double *diag;
+    bool vec_ok;  // N % 4 == 0 and every output 16-byte aligned
 };
 cudaError_t launch_gram_fp32(const Handle *h, cudaStream_t s, const float *P,
                              int batch, int N, int T, GramOut out);
+// K3: split-precision tensor-core Gram + fused read-outs (BF16X3 / FP16X3).
+cudaError_t launch_gram_tc(const Handle *h, cudaStream_t s, const void *P,
+                           int batch, int N, int T, GramOut out);
 // K6: read-outs from a stored C.
 cudaError_t launch_metrics(cudaStream_t s, const float2 *C, int batch, int N,
                            float *plv, float *iplv, float *ciplv);

@@ -1,0 +1,123 @@
+// epilogue.cuh -- the Gram epilogue shared by the SIMT and the tensor-core
+// kernels: read-outs of one Gram entry written to (i, j) and mirrored to
+// (j, i), plus the FP64 unit-modulus check of the diagonal.
+#pragma once
+
+#include "common.cuh"
+#include "readout.cuh"
+
+namespace plv {
+
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+    // for non-negative doubles the IEEE bit pattern orders like an integer
+    atomicMax((unsigned long long *)addr,
+              (unsigned long long)__double_as_longlong(v));
+}
+
+// Write the read-outs of C_ij (already scaled by 1/T) to (i, j) and their
+// mirror to (j, i): PLV and iPLV symmetric, ciPLV negated, C conjugated.
+// On the diagonal Im C_ii = sum_t |P_i|^2 / T is real: it is stored as 0 and
+// iPLV = ciPLV = 0 there.
+__device__ __forceinline__ void emit(const GramOut &o, int64_t eNN, int N,
+                                     int i, int j, float re, float im) {
+    const int64_t ij = eNN + (int64_t)i * N + j;
+    const int64_t ji = eNN + (int64_t)j * N + i;
+    float p, ip, cp;
+    if (i == j) {
+        im = 0.f;
+        p = sqrtf(fmaf(re, re, im * im));
+        ip = 0.f;
+        cp = 0.f;
+    } else {
+        readout(re, im, p, ip, cp);
+    }
+    if (o.plv) { o.plv[ij] = p; if (i != j) o.plv[ji] = p; }
+    if (o.iplv) { o.iplv[ij] = ip; if (i != j) o.iplv[ji] = ip; }
+    if (o.ciplv) { o.ciplv[ij] = cp; if (i != j) o.ciplv[ji] = -cp; }
+    if (o.C) {
+        o.C[ij] = make_float2(re, im);
+        if (i != j) o.C[ji] = make_float2(re, -im);
+    }
+}
+
+// max_i |C_ii - 1| with the 1/T applied in FP64 (the unit-modulus check of
+// Eq. 4: |P| = 1 makes C_ii = 1 exactly in exact arithmetic).
+__device__ __forceinline__ void diag_check(double *diag, float acc_re,
+                                           float acc_im, double invT_d) {
+    const double dr = (double)acc_re * invT_d - 1.0;
+    const double di = (double)acc_im * invT_d;
+    atomic_max_nonneg(diag, sqrt(dr * dr + di * di));
+}
+
+// One thread's W consecutive Gram sums of row i, columns j0 .. j0+W-1, of an
+// upper-triangle tile (unscaled accumulators): scale by 1/T, read-outs,
+// direct store along the row (16-byte vector stores where the row segment is
+// complete and aligned) and mirrored store to (j, i).  Within a warp the
+// lanes hold consecutive rows i, so every mirrored store is one coalesced
+// segment.  On a diagonal tile only i <= j is stored (its mirror covers the
+// rest).
+template <int W>
+__device__ __forceinline__ void store_tile_row(const GramOut &o, int64_t eNN, int N,
+                                               int i, int j0, bool diag_tile,
+                                               const float (&sre)[W],
+                                               const float (&sim)[W], float invT,
+                                               double invT_d, double *diag) {
+    const bool row_ok = i < N;
+    const bool vec = o.vec_ok && row_ok && !diag_tile && (j0 + W <= N);
+    const int64_t rowbase = eNN + (int64_t)i * N;
+#pragma unroll
+    for (int g = 0; g < W / 4; ++g) {
+        float p[4], ip[4], cp[4], rr[4], mm[4];
+        bool valid[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int jj = 4 * g + u;
+            const int j = j0 + jj;
+            valid[u] = row_ok && j < N && (!diag_tile || i <= j);
+            float re = sre[jj] * invT, im = sim[jj] * invT;
+            if (i == j) {
+                if (valid[u] && diag) diag_check(diag, sre[jj], sim[jj], invT_d);
+                im = 0.f;
+                p[u] = sqrtf(fmaf(re, re, im * im));
+                ip[u] = 0.f;
+                cp[u] = 0.f;
+            } else {
+                readout(re, im, p[u], ip[u], cp[u]);
+            }
+            rr[u] = re;
+            mm[u] = im;
+        }
+        const int64_t d0 = rowbase + j0 + 4 * g;
+        if (vec) {
+            if (o.plv) *(float4 *)(o.plv + d0) = make_float4(p[0], p[1], p[2], p[3]);
+            if (o.iplv) *(float4 *)(o.iplv + d0) = make_float4(ip[0], ip[1], ip[2], ip[3]);
+            if (o.ciplv) *(float4 *)(o.ciplv + d0) = make_float4(cp[0], cp[1], cp[2], cp[3]);
+            if (o.C) {
+                float4 *c4 = (float4 *)(o.C + d0);
+                c4[0] = make_float4(rr[0], mm[0], rr[1], mm[1]);
+                c4[1] = make_float4(rr[2], mm[2], rr[3], mm[3]);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!valid[u]) continue;
+                if (o.plv) o.plv[d0 + u] = p[u];
+                if (o.iplv) o.iplv[d0 + u] = ip[u];
+                if (o.ciplv) o.ciplv[d0 + u] = cp[u];
+                if (o.C) o.C[d0 + u] = make_float2(rr[u], mm[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + 4 * g + u;
+            if (!valid[u] || i == j) continue;
+            const int64_t m = eNN + (int64_t)j * N + i;
+            if (o.plv) o.plv[m] = p[u];
+            if (o.iplv) o.iplv[m] = ip[u];
+            if (o.ciplv) o.ciplv[m] = -cp[u];
+            if (o.C) o.C[m] = make_float2(rr[u], -mm[u]);
+        }
+    }
+}
+
+}  // namespace plv

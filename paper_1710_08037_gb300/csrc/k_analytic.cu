@@ -105,10 +105,11 @@ __device__ __forceinline__ float ldx_f(const Tin *p) {
 template <int T, int R, int NS, int MODE, typename Tin>
 __device__ __forceinline__ void stockham(float2 *s, const float2 *__restrict__ tw,
                                          int lt, const Tin *x0, const Tin *x1,
-                                         float2 (&out)[16]) {
+                                         float2 (&out)[16], float *power = nullptr) {
     constexpr int B = 16 / R;  // butterflies per thread
     constexpr int Q = T / 16;  // threads per sequence
     float2 v[16];
+    float pw = 0.f;
 #pragma unroll
     for (int q = 0; q < B; ++q) {
         const int j = lt + q * Q;
@@ -116,14 +117,17 @@ __device__ __forceinline__ void stockham(float2 *s, const float2 *__restrict__ t
         for (int r = 0; r < R; ++r) {
             const int m = j + r * (T / R);
             if constexpr (MODE == kFromX) {
-                v[q * R + r] = make_float2(x0 ? ldx_f(x0 + m) : 0.f,
-                                           x1 ? ldx_f(x1 + m) : 0.f);
+                const float2 c = make_float2(x0 ? ldx_f(x0 + m) : 0.f,
+                                             x1 ? ldx_f(x1 + m) : 0.f);
+                v[q * R + r] = c;
+                pw = fmaf(c.x, c.x, fmaf(c.y, c.y, pw));
             } else {
                 v[q * R + r] = s[padi(m)];
             }
         }
     }
     if constexpr (MODE != kFromX) __syncthreads();
+    if constexpr (MODE == kFromX) *power = pw;
 #pragma unroll
     for (int q = 0; q < B; ++q) {
         const int j = lt + q * Q;
@@ -167,12 +171,12 @@ __device__ __forceinline__ void middle_passes(float2 *s, const float2 *tw,
     }
 }
 
-// Unit phasor of z = a + i b (Eq. 4); |z| = 0 gives 0.  Very small or very
-// large magnitudes are rescaled by a power of two first so the squared norm
-// neither underflows nor overflows.
-__device__ __forceinline__ float2 unit_phasor(float a, float b) {
+// Unit phasor of z = a + i b (Eq. 4); |z|^2 <= floor2 (|z| = 0 by default)
+// gives 0.  Very small or very large magnitudes are rescaled by a power of
+// two first so the squared norm neither underflows nor overflows.
+__device__ __forceinline__ float2 unit_phasor(float a, float b, float floor2 = 0.0f) {
     float r2 = fmaf(a, a, b * b);
-    if (!(r2 > 0.0f)) return make_float2(0.f, 0.f);
+    if (!(r2 > floor2)) return make_float2(0.f, 0.f);
     if (r2 < 1e-30f || r2 > 1e30f) {
         const float sc = r2 < 1e-30f ? 0x1p+60f : 0x1p-60f;
         a *= sc;
@@ -191,6 +195,16 @@ __device__ __forceinline__ void store_phasor(void *P, int64_t r, int N,
         float *o = (float *)P + r * 2 * ld + m;
         o[0] = p.x;
         o[ld] = p.y;
+    } else if constexpr (PREC == PLV_PREC_FP16X3) {
+        const int64_t e = r / N, n = r - e * N;
+        __half *o = (__half *)P + ((e * 4) * N + n) * ld + m;
+        const int64_t ps = (int64_t)N * ld;  // plane stride
+        const __half rh = __float2half_rn(p.x);
+        const __half ih = __float2half_rn(p.y);
+        o[0] = rh;
+        o[ps] = __float2half_rn(p.x - __half2float(rh));
+        o[2 * ps] = ih;
+        o[3 * ps] = __float2half_rn(p.y - __half2float(ih));
     } else {
         const int64_t e = r / N, n = r - e * N;
         __nv_bfloat16 *o = (__nv_bfloat16 *)P + ((e * 4) * N + n) * ld + m;
@@ -211,7 +225,8 @@ struct K1Cfg {
     static constexpr int SEQ = Q >= 256 ? 1 : 256 / Q;  // sequences / CTA
     static constexpr int THREADS = Q * SEQ;
     static constexpr int SMEM_SEQ = T + T / 32;         // padded elements
-    static constexpr size_t SMEM = (size_t)SEQ * SMEM_SEQ * sizeof(float2);
+    static constexpr size_t SMEM =
+        (size_t)SEQ * SMEM_SEQ * sizeof(float2) + (size_t)SEQ * sizeof(float);
     // resident CTAs per SM the register budget is sized for
     static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;
 };
@@ -232,9 +247,19 @@ k_analytic_pow2(const Tin *__restrict__ x, int64_t rows, int N, int64_t ldx,
     const Tin *x0 = r0 < rows ? x + r0 * ldx : nullptr;
     const Tin *x1 = r1 < rows ? x + r1 * ldx : nullptr;
     float2 out[16];
+    float *s_pow = (float *)(smem + C::SEQ * C::SMEM_SEQ);  // per-sequence power
+    if (lt == 0) s_pow[sq] = 0.f;
+    __syncthreads();
 
     // forward FFT of c = x0 + i x1
-    stockham<T, radix_of(L, 0), 1, kFromX, Tin>(s, tw, lt, x0, x1, out);
+    float pw;
+    stockham<T, radix_of(L, 0), 1, kFromX, Tin>(s, tw, lt, x0, x1, out, &pw);
+    // sum of x0^2 + x1^2 over the sequence (its lanes are an aligned group of
+    // Q threads, or whole warps when Q >= 32)
+#pragma unroll
+    for (int off = 1; off < (C::Q < 32 ? C::Q : 32); off <<= 1)
+        pw += __shfl_xor_sync(0xffffffffu, pw, off);
+    if ((lt & 31) == 0) atomicAdd(&s_pow[sq], pw);
     middle_passes<L, 1, NP - 1, Tin>(s, tw, lt, out);
     stockham<T, radix_of(L, NP - 1), ns_of(L, NP - 1), kToHilbert, Tin>(
         s, tw, lt, x0, x1, out);
@@ -246,13 +271,17 @@ k_analytic_pow2(const Tin *__restrict__ x, int64_t rows, int N, int64_t ldx,
 
     constexpr float invT = 1.0f / (float)T;
     const int64_t ld = T;  // power-of-two T >= 32 needs no padding
+    // |z|^2 below 2^-40 of the pair's mean power is under the FFT's rounding
+    // (the two rows of a sequence leak into each other at that level): such
+    // a sample carries no phase and is treated as |z| = 0.
+    const float floor2 = 0x1p-40f * (s_pow[sq] * invT);
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
         const int m = lt + u * C::Q;
         const float h0 = out[u].x * invT;   // H{x0}[m]
         const float h1 = -out[u].y * invT;  // H{x1}[m]
-        if (x0) store_phasor<PREC>(P, r0, N, ld, m, unit_phasor(ldx_f(x0 + m), h0));
-        if (x1) store_phasor<PREC>(P, r1, N, ld, m, unit_phasor(ldx_f(x1 + m), h1));
+        if (x0) store_phasor<PREC>(P, r0, N, ld, m, unit_phasor(ldx_f(x0 + m), h0, floor2));
+        if (x1) store_phasor<PREC>(P, r1, N, ld, m, unit_phasor(ldx_f(x1 + m), h1, floor2));
     }
 }
 
@@ -316,6 +345,11 @@ cudaError_t launch_analytic_pow2(const Handle *h, cudaStream_t s,
             return launch_t<float, PLV_PREC_FP32>(s, (const float *)x, rows, N, log2T, ldx, P, tw);
         return launch_t<double, PLV_PREC_FP32>(s, (const double *)x, rows, N, log2T, ldx, P, tw);
     }
+    if (h->prec == PLV_PREC_FP16X3) {
+        if (dt == PLV_F32)
+            return launch_t<float, PLV_PREC_FP16X3>(s, (const float *)x, rows, N, log2T, ldx, P, tw);
+        return launch_t<double, PLV_PREC_FP16X3>(s, (const double *)x, rows, N, log2T, ldx, P, tw);
+    }
     if (dt == PLV_F32)
         return launch_t<float, PLV_PREC_BF16X3>(s, (const float *)x, rows, N, log2T, ldx, P, tw);
     return launch_t<double, PLV_PREC_BF16X3>(s, (const double *)x, rows, N, log2T, ldx, P, tw);
@@ -334,6 +368,11 @@ cudaError_t launch_normalize(const Handle *h, cudaStream_t s, const void *z,
             k_normalize<float2, PLV_PREC_FP32><<<grid, block, 0, s>>>((const float2 *)z, rows, N, T, ldz, ld, P);
         else
             k_normalize<double2, PLV_PREC_FP32><<<grid, block, 0, s>>>((const double2 *)z, rows, N, T, ldz, ld, P);
+    } else if (h->prec == PLV_PREC_FP16X3) {
+        if (dt == PLV_F32)
+            k_normalize<float2, PLV_PREC_FP16X3><<<grid, block, 0, s>>>((const float2 *)z, rows, N, T, ldz, ld, P);
+        else
+            k_normalize<double2, PLV_PREC_FP16X3><<<grid, block, 0, s>>>((const double2 *)z, rows, N, T, ldz, ld, P);
     } else {
         if (dt == PLV_F32)
             k_normalize<float2, PLV_PREC_BF16X3><<<grid, block, 0, s>>>((const float2 *)z, rows, N, T, ldz, ld, P);

@@ -12,8 +12,7 @@
 // 256 threads, each owning an 8 x 8 block of complex accumulators; operands
 // staged through double-buffered shared memory in [plane][k][row] order (the
 // global layout is row-major in t, so the load transposes).
-#include "common.cuh"
-#include "readout.cuh"
+#include "epilogue.cuh"
 
 namespace plv {
 namespace {
@@ -29,35 +28,6 @@ __device__ __forceinline__ void tile_of(int t, int &I, int &J) {
     while (j * (j + 1) / 2 > t) --j;
     J = j;
     I = t - j * (j + 1) / 2;
-}
-
-__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
-    // for non-negative doubles the IEEE bit pattern orders like an integer
-    atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
-}
-
-// Write the read-outs of C_ij (already scaled) to (i, j) and mirror them to
-// (j, i).  i == j writes only the diagonal.
-__device__ __forceinline__ void emit(const GramOut &o, int64_t eNN, int N,
-                                     int i, int j, float re, float im) {
-    const int64_t ij = eNN + (int64_t)i * N + j;
-    const int64_t ji = eNN + (int64_t)j * N + i;
-    float p, ip, cp;
-    if (i == j) {
-        im = 0.f;  // Im C_ii = sum |P_i|^2 has no imaginary part
-        p = sqrtf(fmaf(re, re, im * im));
-        ip = 0.f;
-        cp = 0.f;
-    } else {
-        readout(re, im, p, ip, cp);
-    }
-    if (o.plv) { o.plv[ij] = p; if (i != j) o.plv[ji] = p; }
-    if (o.iplv) { o.iplv[ij] = ip; if (i != j) o.iplv[ji] = ip; }
-    if (o.ciplv) { o.ciplv[ij] = cp; if (i != j) o.ciplv[ji] = -cp; }
-    if (o.C) {
-        o.C[ij] = make_float2(re, im);
-        if (i != j) o.C[ji] = make_float2(re, -im);
-    }
 }
 
 __global__ void __launch_bounds__(256, 1)
@@ -150,11 +120,8 @@ k_gram_fp32(const float *__restrict__ P, int N, int T, int64_t ld,
             const int j = J * BM + (b < 4 ? tx * 4 + b : 64 + tx * 4 + b - 4);
             if (j >= N || (I == J && i > j)) continue;
             emit(out, eNN, N, i, j, cre[a][b] * invT, cim[a][b] * invT);
-            if (i == j && out.diag) {
-                const double dr = (double)cre[a][b] * invT_d - 1.0;
-                const double di = (double)cim[a][b] * invT_d;
-                atomic_max_nonneg(out.diag + e, sqrt(dr * dr + di * di));
-            }
+            if (i == j && out.diag)
+                diag_check(out.diag + e, cre[a][b], cim[a][b], invT_d);
         }
     }
 }

@@ -1,0 +1,493 @@
+// k_gram_tc.cu -- K3: the Hermitian Gram C = P P^H / T (Eq. 7) on the
+// 5th-generation tensor cores (tcgen05), with the read-outs (Eq. 7, 13, 14)
+// fused into the epilogue.
+//
+// Split precision.  Each phasor component p (Re or Im) is stored as two
+// 16-bit numbers p = hi + lo (hi = RN(p), lo = RN(p - hi)), in BF16 or FP16.
+// Every real product of the Gram is taken as hi*hi + hi*lo + lo*hi, the
+// lo*lo term dropped, with FP32 accumulation in tensor memory.  With
+// P = a + i b:
+//     Re C = a a^T + b b^T,      Im C = b a^T - a b^T,
+// so one K-block of samples costs 12 MMAs per output tile: 6 into the Re
+// accumulator and 6 into the Im accumulator; the minus sign of a b^T is the
+// MMA's negate-A bit.
+//
+// Accumulation.  The tensor core's FP32 accumulation into TMEM does not
+// round to nearest, and its error grows with the number of K blocks added
+// into one accumulator.  So the K loop runs in chunks of CH_SAMPLES samples:
+// each chunk accumulates into a fresh TMEM region (two regions, ping-pong),
+// and the epilogue warps drain every finished chunk into FP32 running sums
+// in registers (round to nearest), as a two-level summation.
+//
+// Kernel structure (one CTA per SM, persistent over the tile list):
+//   warp 0      TMA producer: per stage, one 3-D box {32 samples, 128 rows,
+//               4 planes} per operand side (64-byte swizzle) into a
+//               3-stage shared-memory ring;
+//   warp 1      TMEM allocator and MMA issuer (one thread): tcgen05.mma
+//               128x128x16, two TMEM regions of [128 Re + 128 Im] FP32
+//               columns (512 columns) alternating per K chunk;
+//   warps 2-17  epilogue: each owns one TMEM lane quarter (32 rows) and one
+//               quarter of the columns (32), keeps 32 Re + 32 Im running
+//               sums, drains each chunk, and at the end of the tile scales
+//               by 1/T, applies the read-outs and stores the tile (vector
+//               stores along rows) and its mirror (coalesced along columns).
+// Only tiles (I, J) with I <= J of each epoch are computed; on a diagonal
+// tile the B operand is the A operand already in shared memory.
+//
+// Every wait on an mbarrier is bounded in time; on expiry the CTA records
+// PLV_ERR_TIMEOUT in the device status word, stops issuing work, lets the
+// copies and MMAs it issued land, frees its TMEM and returns.
+#include <cuda.h>
+
+#include "epilogue.cuh"
+
+namespace plv {
+namespace {
+
+constexpr int TM = 128;                       // tile rows (i)
+constexpr int TN = 128;                       // tile columns (j)
+constexpr int KB = 32;                        // samples per stage
+constexpr int NSTAGE = 3;
+constexpr int PLANE_BYTES = TM * KB * 2;      // one 128 x 32 16-bit plane
+constexpr int SIDE_BYTES = 4 * PLANE_BYTES;   // Re_hi, Re_lo, Im_hi, Im_lo
+constexpr int STAGE_BYTES = 2 * SIDE_BYTES;   // A side + B side
+constexpr int NEPI_WARPS = 16;               // 4 lane quarters x 4 column quarters
+constexpr int NTHREADS = 64 + 32 * NEPI_WARPS;
+constexpr int TMEM_COLS = 512;
+constexpr int ACC_COLS = 256;                 // Re (128) + Im (128)
+constexpr int CH = 4;                         // stages per K chunk (128 samples)
+constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s bound on any wait
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align*/ + 256;
+
+enum { P_RH = 0, P_RL = 1, P_IH = 2, P_IL = 3 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---- mbarrier -----------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase of parity `parity` completed; false on
+// timeout (which raises the CTA's abort flag and the device status) or when
+// another role already aborted.
+__device__ __noinline__ bool wait_bar(uint32_t bar, uint32_t parity,
+                                      volatile int *abort_flag, int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 127) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > kWaitNs) {
+                *abort_flag = 1;
+                atomicExch(status, (int)kDevTimeout);
+                return false;
+            }
+        }
+    }
+}
+
+// ---- TMA ----------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map,
+                                            uint32_t bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// ---- tcgen05 ------------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     dst_smem),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            bar)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+          "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+}
+// Wait for this thread's tcgen05.ld results; the registers are in/out
+// operands so no use of them can be scheduled above the wait.
+__device__ __forceinline__ void tmem_ld_wait8(uint32_t (&a)[8], uint32_t (&b)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]),
+                   "+r"(a[6]), "+r"(a[7]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]),
+                   "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7])
+                 :
+                 : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row
+// core-matrix groups 512 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) |
+           ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16 (fmt 1) or FP16
+// (fmt 0), both K-major, M = 128, N = 128, optional negate-A.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, bool negA) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((negA ? 1u : 0u) << 13) |
+           ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void tile_of(int t, int &I, int &J) {
+    int j = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((j + 1) * (j + 2) / 2 <= t) ++j;
+    while (j * (j + 1) / 2 > t) --j;
+    J = j;
+    I = t - j * (j + 1) / 2;
+}
+
+struct TcArgs {
+    int N;
+    int nkb;              // K blocks of 32 samples
+    int tiles_per_epoch;  // nt (nt + 1) / 2
+    int total_tiles;
+    float invT;
+    double invT_d;
+    GramOut out;
+    int *status;
+};
+
+template <uint32_t FMT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;  // stages, 1024-aligned
+    uint8_t *gbase = smem_raw + (base - raw);
+    uint64_t *bars = (uint64_t *)(gbase + NSTAGE * STAGE_BYTES);
+    // bars: full[0..S), empty[0..S), tfull[2], tempty[2]
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NSTAGE + 4);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    const uint32_t bar0 = smem_u32(bars);
+    auto FULL = [&](int s) { return bar0 + 8u * s; };
+    auto EMPTY = [&](int s) { return bar0 + 8u * (NSTAGE + s); };
+    auto TFULL = [&](int b) { return bar0 + 8u * (2 * NSTAGE + b); };
+    auto TEMPTY = [&](int b) { return bar0 + 8u * (2 * NSTAGE + 2 + b); };
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(FULL(s), 1);
+            mbar_init(EMPTY(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(TFULL(b), 1);
+            mbar_init(TEMPTY(b), 32 * NEPI_WARPS);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int tpe = args.tiles_per_epoch;
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t pending = 0;        // stages with a copy issued
+            uint32_t pend_parity = 0;    // FULL parity each pending copy completes
+            for (int t = blockIdx.x; t < args.total_tiles && !*abort_flag; t += gridDim.x) {
+                const int e = t / tpe;
+                int I, J;
+                tile_of(t - e * tpe, I, J);
+                const bool diag = I == J;
+                for (int kb = 0; kb < args.nkb; ++kb) {
+                    if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status)) break;
+                    const uint32_t sa = base + stage * STAGE_BYTES;
+                    mbar_expect_tx(FULL(stage), diag ? SIDE_BYTES : 2 * SIDE_BYTES);
+                    tma_load_3d(sa, &tmap, FULL(stage), kb * KB, I * TM, 4 * e);
+                    if (!diag)
+                        tma_load_3d(sa + SIDE_BYTES, &tmap, FULL(stage), kb * KB, J * TN,
+                                    4 * e);
+                    pending |= 1u << stage;
+                    pend_parity = (pend_parity & ~(1u << stage)) | (phase << stage);
+                    if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
+                }
+            }
+            if (*abort_flag) {
+                // let the copies already issued land before the CTA exits
+                for (int st = 0; st < NSTAGE; ++st) {
+                    if (!(pending & (1u << st))) continue;
+                    const uint32_t par = (pend_parity >> st) & 1u;
+                    const uint64_t t0 = gtimer();
+                    while (!mbar_try_wait(FULL(st), par) && gtimer() - t0 < 100000000ull) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t ID_POS = idesc_f16(FMT, false);
+            constexpr uint32_t ID_NEG = idesc_f16(FMT, true);
+            int stage = 0;
+            uint32_t phase = 0;
+            int buf = 0;
+            uint32_t buf_phase = 0;
+            bool issued = false;
+            uint32_t last_bar = 0, last_parity = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < args.total_tiles && !*abort_flag;
+                 t += gridDim.x) {
+                const int e = t / tpe;
+                int I, J;
+                tile_of(t - e * tpe, I, J);
+                const bool diag = I == J;
+                for (int kb0 = 0; ok && kb0 < args.nkb; kb0 += CH) {
+                    if (!wait_bar(TEMPTY(buf), buf_phase ^ 1u, abort_flag, args.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_re = tmem + buf * ACC_COLS;
+                    const uint32_t d_im = d_re + TN;
+                    const int kb1 = kb0 + CH < args.nkb ? kb0 + CH : args.nkb;
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!wait_bar(FULL(stage), phase, abort_flag, args.status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = base + stage * STAGE_BYTES;
+                        const uint32_t sb = diag ? sa : sa + SIDE_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < KB / 16; ++ks) {
+                            const uint32_t ko = ks * 32;  // 16 samples x 2 bytes
+                            const uint64_t aRH = sdesc_sw64(sa + P_RH * PLANE_BYTES + ko);
+                            const uint64_t aRL = sdesc_sw64(sa + P_RL * PLANE_BYTES + ko);
+                            const uint64_t aIH = sdesc_sw64(sa + P_IH * PLANE_BYTES + ko);
+                            const uint64_t aIL = sdesc_sw64(sa + P_IL * PLANE_BYTES + ko);
+                            const uint64_t bRH = sdesc_sw64(sb + P_RH * PLANE_BYTES + ko);
+                            const uint64_t bRL = sdesc_sw64(sb + P_RL * PLANE_BYTES + ko);
+                            const uint64_t bIH = sdesc_sw64(sb + P_IH * PLANE_BYTES + ko);
+                            const uint64_t bIL = sdesc_sw64(sb + P_IL * PLANE_BYTES + ko);
+                            const uint32_t first = (kb == kb0 && ks == 0) ? 0u : 1u;
+                            // Re C += a a^T + b b^T (hi*hi + hi*lo + lo*hi each)
+                            mma_f16(d_re, aRH, bRH, ID_POS, first);
+                            mma_f16(d_re, aRH, bRL, ID_POS, 1u);
+                            mma_f16(d_re, aRL, bRH, ID_POS, 1u);
+                            mma_f16(d_re, aIH, bIH, ID_POS, 1u);
+                            mma_f16(d_re, aIH, bIL, ID_POS, 1u);
+                            mma_f16(d_re, aIL, bIH, ID_POS, 1u);
+                            // Im C += b a^T - a b^T
+                            mma_f16(d_im, aIH, bRH, ID_POS, first);
+                            mma_f16(d_im, aIH, bRL, ID_POS, 1u);
+                            mma_f16(d_im, aIL, bRH, ID_POS, 1u);
+                            mma_f16(d_im, aRH, bIH, ID_NEG, 1u);
+                            mma_f16(d_im, aRH, bIL, ID_NEG, 1u);
+                            mma_f16(d_im, aRL, bIH, ID_NEG, 1u);
+                        }
+                        mma_commit(EMPTY(stage));  // frees the stage when done
+                        issued = true;
+                        last_bar = EMPTY(stage);
+                        last_parity = phase;
+                        if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    mma_commit(TFULL(buf));  // chunk ready for the epilogue
+                    if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+                }
+            }
+            if (*abort_flag && issued) {
+                // let the MMAs already issued finish before TMEM is freed: the
+                // last commit completes when every earlier MMA has
+                const uint64_t t0 = gtimer();
+                while (!mbar_try_wait(last_bar, last_parity) && gtimer() - t0 < 100000000ull) {
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;                // TMEM lane quarter of this warp
+        const int cq = (warp - 2) >> 2;        // column quarter of this warp
+        const int row = q * 32 + lane;         // tile row owned by this thread
+        int buf = 0;
+        uint32_t buf_phase = 0;
+        const int N = args.N;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < args.total_tiles; t += gridDim.x) {
+            const int e = t / tpe;
+            int I, J;
+            tile_of(t - e * tpe, I, J);
+            float sre[32], sim[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
+            for (int kb0 = 0; kb0 < args.nkb; kb0 += CH) {
+                if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + buf * ACC_COLS +
+                                    cq * 32;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    uint32_t ur[8], ui[8];
+                    tmem_ld8(tq + 8 * h, ur);
+                    tmem_ld8(tq + TN + 8 * h, ui);
+                    tmem_ld_wait8(ur, ui);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        sre[8 * h + c] += __uint_as_float(ur[c]);
+                        sim[8 * h + c] += __uint_as_float(ui[c]);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(TEMPTY(buf));
+                if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+            }
+            if (!ok) break;
+            const int i = I * TM + row;
+            const int j0 = J * TN + cq * 32;
+            store_tile_row(args.out, (int64_t)e * N * N, N, i, j0, I == J, sre, sim,
+                           args.invT, args.invT_d, args.out.diag ? args.out.diag + e
+                                                                 : nullptr);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+}  // namespace
+
+cudaError_t launch_gram_tc(const Handle *h, cudaStream_t s, const void *P, int batch,
+                           int N, int T, GramOut out) {
+    const int64_t ld = padded_len(T);
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)N, (cuuint64_t)4 * batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)N * ld * 2};
+    const cuuint32_t box[3] = {KB, TM, 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const bool fp16 = h->prec == PLV_PREC_FP16X3;
+    CUresult r = enc(&map,
+                     fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     3, const_cast<void *>(P), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const int nt = (N + TM - 1) / TM;
+    TcArgs a;
+    a.N = N;
+    a.nkb = (int)(ld / KB);
+    a.tiles_per_epoch = nt * (nt + 1) / 2;
+    const int64_t total = (int64_t)a.tiles_per_epoch * batch;
+    if (total > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    a.total_tiles = (int)total;
+    a.invT = 1.0f / (float)T;
+    a.invT_d = 1.0 / (double)T;
+    a.out = out;
+    a.status = h->status;
+    const int grid = (int)(total < h->num_sms ? total : h->num_sms);
+    auto kern = fp16 ? k_gram_tc<0u> : k_gram_tc<1u>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NTHREADS, SMEM_BYTES, s>>>(map, a);
+    return cudaGetLastError();
+}
+
+}  // namespace plv

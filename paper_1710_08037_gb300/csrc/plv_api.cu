@@ -75,7 +75,7 @@ plv_status plv_create(plv_handle **out, int device, plv_precision prec,
                       size_t workspace_limit) {
     if (!out) return fail(PLV_ERR_INVALID, "plv_create: handle pointer is NULL");
     *out = nullptr;
-    if (prec != PLV_PREC_FP32 && prec != PLV_PREC_BF16X3)
+    if (prec != PLV_PREC_FP32 && prec != PLV_PREC_BF16X3 && prec != PLV_PREC_FP16X3)
         return fail(PLV_ERR_INVALID, "plv_create: unknown precision %d", (int)prec);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -227,6 +227,11 @@ plv_status plv_gram(plv_handle *hp, void *stream, const void *P, int batch,
     o.diag = diag_dev;
     if (o.C && ((uintptr_t)o.C % 8) != 0)
         return fail(PLV_ERR_INVALID, "plv_gram: C is not 8-byte aligned");
+    if ((o.plv && ((uintptr_t)o.plv % 4)) || (o.iplv && ((uintptr_t)o.iplv % 4)) ||
+        (o.ciplv && ((uintptr_t)o.ciplv % 4)))
+        return fail(PLV_ERR_INVALID, "plv_gram: float output not 4-byte aligned");
+    o.vec_ok = (N % 4 == 0) && !((uintptr_t)o.plv % 16) && !((uintptr_t)o.iplv % 16) &&
+               !((uintptr_t)o.ciplv % 16) && !((uintptr_t)o.C % 16);
     if ((int64_t)N * N > ((int64_t)1 << 40))
         return fail(PLV_ERR_UNSUPPORTED, "plv_gram: N = %d too large", N);
     PLV_GUARD(&hp->h);
@@ -239,7 +244,7 @@ plv_status plv_gram(plv_handle *hp, void *stream, const void *P, int batch,
     if (hp->h.prec == PLV_PREC_FP32)
         return check_cuda(launch_gram_fp32(&hp->h, s, (const float *)P, batch, N, T, o),
                           "plv_gram launch");
-    return fail(PLV_ERR_UNSUPPORTED, "plv_gram: BF16X3 Gram not built in this version");
+    return check_cuda(launch_gram_tc(&hp->h, s, P, batch, N, T, o), "plv_gram launch");
 }
 
 plv_status plv_metrics(plv_handle *hp, void *stream, const void *C, int batch,

@@ -7,18 +7,28 @@
 
 namespace plv {
 
+// Denominator of Eq. 14, d = 1 - (Re C)^2, formed as (1 - r)(1 + r).  Where
+// |r| > 1/2 the factors are formed and multiplied in FP64 (the region where
+// 1 - r^2 can cancel as |r| -> 1); elsewhere both factors lie in [1/2, 3/2]
+// and the FP32 product is already correct to one rounding.
+__device__ __forceinline__ float ciplv_den(float r) {
+    if (fabsf(r) > 0.5f) {
+        const double rd = (double)r;
+        return (float)((1.0 - rd) * (1.0 + rd));
+    }
+    return (1.0f - r) * (1.0f + r);
+}
+
 // PLV = |C| (Eq. 7), iPLV = |Im C| (Eq. 13, in absolute value) and
-// ciPLV = Im C / sqrt((1 - Re C)(1 + Re C)) (Eq. 14) of one Gram entry
-// C = re + i im that has already been scaled by 1/T.  The denominator is
-// formed in FP64 in the factored form, which does not cancel as |Re C| -> 1;
-// where it is not positive ciPLV is 0.
+// ciPLV = Im C / sqrt((1 - Re C)(1 + Re C)) (Eq. 14) of one off-diagonal
+// Gram entry C = re + i im already scaled by 1/T; ciPLV = 0 where the
+// denominator is not positive.
 __device__ __forceinline__ void readout(float re, float im, float &plv,
                                         float &iplv, float &ciplv) {
     plv = sqrtf(fmaf(re, re, im * im));
     iplv = fabsf(im);
-    const double r = (double)re;
-    const double d = (1.0 - r) * (1.0 + r);
-    ciplv = d > 0.0 ? im / sqrtf((float)d) : 0.0f;
+    const float d = ciplv_den(re);
+    ciplv = d > 0.0f ? im / sqrtf(d) : 0.0f;
 }
 
 }  // namespace plv

@@ -8,7 +8,10 @@ import torch
 # relative error <= 2^-17 after the split and the dropped lo*lo term, so every
 # product term of the Gram carries <= ~3 * 2^-17 ~ 2.3e-5 worst case; the
 # mean over T samples averages these, the stated bound is 2e-5.
-TOL = {"fp32": 1e-5, "bf16x3": 2e-5}
+TOL = {"fp32": 1e-5, "bf16x3": 2e-5, "fp16x3": 1e-5}
+# phasor (operand) representation tolerance and diagonal |C_ii - 1| bound
+PHASOR_TOL = {"fp32": 2e-6, "bf16x3": 4e-5, "fp16x3": 3e-6}
+DIAG_TOL = {"fp32": 1e-6, "bf16x3": 3e-5, "fp16x3": 2e-6}
 
 
 def unpack_phasors(P, precision, B, N, T):
@@ -17,7 +20,8 @@ def unpack_phasors(P, precision, B, N, T):
     if precision == "fp32":
         a = P[: B * N * 2 * ld].view(B, N, 2, ld).double().cpu().numpy()
         return a[:, :, 0, :T] + 1j * a[:, :, 1, :T]
-    b = P.view(torch.bfloat16)[: B * 4 * N * ld].view(B, 4, N, ld)
+    dt = torch.bfloat16 if precision == "bf16x3" else torch.float16
+    b = P.view(dt)[: B * 4 * N * ld].view(B, 4, N, ld)
     b = b.double().cpu().numpy()
     return (b[:, 0, :, :T] + b[:, 1, :, :T]) + 1j * (b[:, 2, :, :T] +
                                                      b[:, 3, :, :T])

@@ -8,11 +8,11 @@ import torch
 
 import oracle
 from paper_1710_08037_gb300 import synth
-from tests.helpers import TOL, compare, unpack_phasors
+from tests.helpers import DIAG_TOL, PHASOR_TOL, TOL, compare, unpack_phasors
 
 pytestmark = pytest.mark.gpu
 
-PRECISIONS = ["fp32"]
+PRECISIONS = ["fp32", "bf16x3", "fp16x3"]
 
 
 @pytest.fixture(scope="module")
@@ -46,8 +46,7 @@ def test_analytic_phasors_on_bin_tones(handles, prec, T):
     P = h.plv_analytic(torch.tensor(x[None], device="cuda"))
     got = unpack_phasors(P, prec, 1, N, T)[0]
     ref = np.exp(1j * (2 * np.pi * k[:, None] * t / T + th[:, None]))
-    tol = 2e-6 if prec == "fp32" else 2e-5
-    assert np.max(np.abs(got - ref)) < tol
+    assert np.max(np.abs(got - ref)) < PHASOR_TOL[prec]
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
@@ -65,8 +64,8 @@ def test_analytic_phasors_random_vs_oracle(handles, prec):
     # the phasor error is the FFT's error in z divided by |z|: compare in z
     rms = np.sqrt(np.mean(np.abs(z) ** 2))
     err_z = np.abs(got - ref) * np.abs(z)
-    assert err_z.max() < (1e-5 if prec == "fp32" else 5e-5) * rms
-    assert np.abs(np.abs(got) - 1).max() < (1e-6 if prec == "fp32" else 2e-5)
+    assert err_z.max() < max(1e-5, PHASOR_TOL[prec]) * rms
+    assert np.abs(np.abs(got) - 1).max() < max(1e-6, PHASOR_TOL[prec])
 
 
 # --- K2/K3: Gram + read-outs ---------------------------------------------------
@@ -102,7 +101,7 @@ def test_end_to_end_tones_workload(handles, prec):
     ref = oracle.connectivity(x[0])
     gpu = {k: res[k][0] for k in ("plv", "iplv", "ciplv")}
     errs = compare(gpu, ref, TOL[prec])
-    assert res["diag"][0] < (1e-6 if prec == "fp32" else 3e-5)
+    assert res["diag"][0] < DIAG_TOL[prec]
     # the closed-form structure survives: coupled pairs lock, sign of lead
     for (a, b), d in zip(meta["pairs"], meta["deltas"]):
         if abs(math.sin(d)) > 0.2:
@@ -200,7 +199,7 @@ def _sampled_check(h, prec, E, N, T, seed, n_rows=12, n_cols=48, n_ep=2):
         for k in worst:
             worst[k] = max(worst[k], errs[k])
     # invariants on the whole output
-    assert float(res["diag"].max()) < (1e-6 if prec == "fp32" else 3e-5)
+    assert float(res["diag"].max()) < DIAG_TOL[prec]
     assert float(res["plv"].max()) <= 1.0 + 1e-5
     assert bool(torch.all(res["iplv"] <= res["plv"] + 1e-6))
     return worst
@@ -213,4 +212,16 @@ def test_full_size_fp32_workload_sampled():
     h = plv.Handle(precision="fp32")
     w = _sampled_check(h, "fp32", 30, 4096, 4096, seed=1002)
     print("fp32 full-size worst errors", w)
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+def test_full_size_split_workload_sampled(prec):
+    """N = 8192 sources, T = 8192, 20 epochs (the split-precision workload),
+    sampled pairs vs the oracle plus invariants on the whole output."""
+    import paper_1710_08037_gb300 as plv
+    h = plv.Handle(precision=prec)
+    w = _sampled_check(h, prec, 20, 8192, 8192, seed=1003, n_rows=8,
+                       n_cols=32)
+    print(prec, "full-size worst errors", w)
     h.close()
