@@ -38,6 +38,8 @@ WORKLOADS = {
     # name: (E, N, T, seed)
     "bandlimited-N4096-T4096-E30": (30, 4096, 4096, 1002),
     "bandlimited-N8192-T8192-E20": (20, 8192, 8192, 1003),
+    # small case of the first, for ncu captures (still larger than L2)
+    "bandlimited-N4096-T4096-E4": (4, 4096, 4096, 1002),
 }
 DEFAULT_WORKLOAD = "bandlimited-N4096-T4096-E30"
 
@@ -108,6 +110,16 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# DRAM traffic per launch of the dominant kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel build,
+# workload and precision.  Captured on the 4-epoch case and scaled to the
+# launch by epochs (profiles/k_gram_tc_and_k_analytic_bandlimited-N4096-T4096-E4.md).
+# An entry is removed when the kernel changes after its capture.
+TRAFFIC = {
+    ("k_gram_tc", "bandlimited-N4096-T4096-E30", "bf16x3"): (1.943164e9 + 1.039759e9) * 30 / 4,
+}
 
 
 def gram_flops(N, T, E, prec):
@@ -226,6 +238,36 @@ def run_ours(args):
                "d2h_bytes_per_step": int(sum(v.numel() * 4 for v in out.values())),
                "ms_per_step": ems / args.steps}
 
+    # the plain FP32 path on the same input: time and agreement
+    fp32 = None
+    if args.precision != "fp32" and not args.no_fp32_compare:
+        h32 = plv.Handle(precision="fp32", device=local)
+        out32 = {k: torch.empty_like(v) for k, v in out.items()}
+        P32 = h32.empty_phasors(E, N, T)
+
+        def step32():
+            h32.plv_analytic(x, P32)
+            h32.plv_gram(P32, E, N, T, out=out32)
+
+        step32()
+        torch.cuda.synchronize(dev)
+        n32 = max(1, min(args.steps, 3))
+        a, b = ev(), ev()
+        a.record(s)
+        for _ in range(n32):
+            step32()
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        ms32 = a.elapsed_time(b) / n32
+        step()  # refresh the split-precision outputs for the comparison
+        torch.cuda.synchronize(dev)
+        agree = {k: float((out[k] - out32[k]).abs().max()) for k in out}
+        fp32 = {"ms_per_step": ms32, "value": units * world / (ms32 / 1e3),
+                "speedup_of_split_path": ms32 / ms_step,
+                "max_abs_diff_vs_split_path": agree, "steps": n32}
+        del out32, P32
+        h32.close()
+
     peaks, peak_kind = _peaks()
     prec = args.precision
     flops = gram_flops(N, T, E, prec)
@@ -247,7 +289,7 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} bf16 dense "
                                f"({'sustained' if args.sustained else 'burst'})"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = TRAFFIC.get((roof["kernel"], args.workload, prec))
     roof["launch_ms"] = gram_ms
     k1b = k1_bytes(N, T, E, x.element_size())
     k1 = {"kernel": "k_analytic_pow2", "bound": "hbm", "launch_ms": k1_ms,
@@ -281,6 +323,7 @@ def run_ours(args):
             "roofline": roof,
             "k1_roofline": k1,
             "cpu_baseline": cpu,
+            "fp32_path": fp32,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
@@ -360,7 +403,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "bf16x3", "fp16x3"],
-                    default="fp32")
+                    default="bf16x3")
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip timing the plain FP32 path beside the split one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS),
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--sustained", action="store_true",
