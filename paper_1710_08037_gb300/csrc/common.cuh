@@ -12,7 +12,7 @@
 #include <mutex>
 #include <string>
 
-#include "../../include/plv.h"
+#include "plv.h"
 
 namespace plv {
 
