@@ -156,6 +156,28 @@ plv_status plv_gram(plv_handle *h, void *stream, const void *P, int batch,
 plv_status plv_metrics(plv_handle *h, void *stream, const void *C, int batch,
                        int N, float *plv, float *iplv, float *ciplv);
 
+/* Gradient of L = sum_ij (g_plv PLV + g_iplv iPLV + g_ciplv ciPLV)_ij with
+ * respect to the real input x, through Eq. 14, 13, 7 (read-outs and Gram),
+ * Eq. 4 (normalisation) and Eq. 3 (analytic signal).  The analytic signal is
+ * recomputed from x (it is not stored by the forward pass).
+ *   x        : the forward input, [batch][N][ldx], F32 or F64.
+ *   C        : complex64 [batch][N][N], the forward Gram (plv_gram with
+ *              PLV_OUT_C, any precision).
+ *   g_plv, g_iplv, g_ciplv : float [batch][N][N] upstream gradients of the
+ *              three outputs; NULL means zero.  Diagonal entries are ignored
+ *              (the forward diagonal does not depend on x).
+ *   grad_x   : float [batch][N][T] (row stride T), written completely.
+ * Conventions: dPLV/dC = C/|C| (0 at |C| = 0); d|Im C|/dIm C = sign(Im C)
+ * (0 at 0); ciPLV is differentiated where (1 - Re C)(1 + Re C) > 0.
+ * Arithmetic FP32.  Supported T: as plv_analytic.  Uses handle scratch of
+ * batch*N*ld*20 + batch*N*N*8 bytes, allocated on first use for a size
+ * (cudaMalloc; fails with PLV_ERR_INVALID if that first use is inside a
+ * stream capture). */
+plv_status plv_backward(plv_handle *h, void *stream, const void *x,
+                        plv_dtype dtype, int batch, int N, int T, int64_t ldx,
+                        const void *C, const float *g_plv, const float *g_iplv,
+                        const float *g_ciplv, float *grad_x);
+
 /* Read (and clear) the handle's device status word after synchronising
  * `stream`.  *device_status receives PLV_OK or the recorded error. */
 plv_status plv_sync_status(plv_handle *h, void *stream, int *device_status);

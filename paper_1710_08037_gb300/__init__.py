@@ -21,8 +21,8 @@ from ._lib import (PLV_F32, PLV_F64, PLV_OUT_C, PLV_OUT_CIPLV, PLV_OUT_IPLV,
                    PLV_OUT_PLV, PLV_PREC_BF16X3, PLV_PREC_FP16X3,
                    PLV_PREC_FP32, PlvError)
 
-__all__ = ["Handle", "PlvError", "phasor_ld", "PLV_PREC_FP32",
-           "PLV_PREC_BF16X3"]
+__all__ = ["Handle", "PlvError", "phasor_ld", "connectivity",
+           "PLV_PREC_FP32", "PLV_PREC_BF16X3", "PLV_PREC_FP16X3"]
 
 _PREC = {"fp32": PLV_PREC_FP32, "bf16x3": PLV_PREC_BF16X3,
          "fp16x3": PLV_PREC_FP16X3, PLV_PREC_FP32: PLV_PREC_FP32,
@@ -155,6 +155,27 @@ class Handle:
                                         _ptr(res["ciplv"])), self.h)
         return res
 
+    def plv_backward(self, x, C, g_plv=None, g_iplv=None, g_ciplv=None,
+                     grad_x=None):
+        """Gradient of sum(g_plv PLV + g_iplv iPLV + g_ciplv ciPLV) with
+        respect to x (batch, N, T); C is the forward's complex64 Gram."""
+        assert x.is_cuda and x.dim() == 3 and C.dtype == torch.complex64
+        B, N, T = x.shape
+        if not (x.stride(-1) == 1 and (N == 1 or x.stride(0) == N * x.stride(1))):
+            x = x.contiguous()
+        ldx = x.stride(1) if N > 1 else max(x.stride(0), T)
+        C = C.contiguous()
+        gs = [None if g is None else g.to(torch.float32).contiguous()
+              for g in (g_plv, g_iplv, g_ciplv)]
+        if grad_x is None:
+            grad_x = torch.empty((B, N, T), dtype=torch.float32,
+                                 device=self.device)
+        _lib.check(self.lib.plv_backward(self.h, _stream(self.device), _ptr(x),
+                                         _dtype_code(x), B, N, T, ldx,
+                                         _ptr(C), _ptr(gs[0]), _ptr(gs[1]),
+                                         _ptr(gs[2]), _ptr(grad_x)), self.h)
+        return grad_x
+
     def plv_sync_status(self) -> int:
         v = ctypes.c_int(0)
         _lib.check(self.lib.plv_sync_status(self.h, _stream(self.device),
@@ -169,3 +190,44 @@ class Handle:
         P = self.plv_analytic(x, P)
         res = self.plv_gram(P, E, N, T, C=C, diag=diag, out=out)
         return res
+
+
+class _Connectivity(torch.autograd.Function):
+    """PLV, iPLV, ciPLV of x (batch, N, T) with a hand-written backward:
+    forward saves x and C (not the analytic signal); backward recomputes the
+    analytic signal from x inside plv_backward."""
+
+    @staticmethod
+    def forward(ctx, x, handle):
+        E, N, T = x.shape
+        P = handle.plv_analytic(x.detach())
+        res = handle.plv_gram(P, E, N, T, C=True)
+        ctx.handle = handle
+        ctx.save_for_backward(x.detach(), res["C"])
+        ctx.x_dtype = x.dtype
+        return res["plv"], res["iplv"], res["ciplv"]
+
+    @staticmethod
+    def backward(ctx, g_plv, g_iplv, g_ciplv):
+        x, C = ctx.saved_tensors
+        g = ctx.handle.plv_backward(x, C, g_plv, g_iplv, g_ciplv)
+        return g.to(ctx.x_dtype), None
+
+
+def connectivity(x, handle=None):
+    """Differentiable (PLV, iPLV, ciPLV) of real x (batch, N, T) on the GPU;
+    gradients flow to x through the library's backward kernels."""
+    if handle is None:
+        handle = _default_handle(x.device)
+    return _Connectivity.apply(x, handle)
+
+
+_handles = {}
+
+
+def _default_handle(device):
+    key = (device.index if device.index is not None
+           else torch.cuda.current_device())
+    if key not in _handles:
+        _handles[key] = Handle(precision="fp32", device=key)
+    return _handles[key]

@@ -41,6 +41,8 @@ struct Handle {
     // table L starting at element (2^L - 2^kMinLog2T)
     float2 *twiddles = nullptr;
     int *status = nullptr;  // device status word
+    void *ws = nullptr;     // scratch for the backward pass (grows on demand)
+    size_t ws_bytes = 0;
     std::mutex mu;
 };
 
@@ -59,6 +61,14 @@ inline const float2 *twiddle_table(const Handle *h, int log2T) {
 cudaError_t launch_analytic_pow2(const Handle *h, cudaStream_t s,
                                  const void *x, plv_dtype dt, int64_t rows,
                                  int N, int log2T, int64_t ldx, void *P);
+// Backward preparation: FP32 phasors P[rows][2][ld] and rinv[rows][ld].
+cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
+                            int64_t rows, int log2T, int64_t ldx, float *P, float *rinv);
+// K5: S = G + G^H, Gamma = S P / T, grad = Re Gamma_z - H{Im Gamma_z}.
+cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
+                            int log2T, const float2 *C, const float *g1, const float *g2,
+                            const float *g3, const float *P, const float *rinv, float *S,
+                            float *Gm, float *grad);
 // Eq. 4 on a given analytic signal.
 cudaError_t launch_normalize(const Handle *h, cudaStream_t s, const void *z,
                              plv_dtype dt, int64_t rows, int N, int T,

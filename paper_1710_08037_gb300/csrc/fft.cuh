@@ -1,0 +1,345 @@
+// fft.cuh -- shared-memory FFT engine for the Hilbert transform of real rows
+// (device code shared by the forward phasor kernel and the backward kernel).
+//
+// The Hilbert transform is a real-linear operator, so one complex FFT serves
+// two real rows: with c = u0 + i u1,
+//     w = IFFT(-i sgn(k) FFT(c)) = H{u0} + i H{u1}.
+// The inverse transform is done with the forward one:
+// IFFT(W) = conj(FFT(conj(W))) / T, and conj(W) is folded into the last
+// forward pass.
+//
+// FFT: Stockham auto-sort (Govindaraju et al., SC'08) in shared memory,
+// radix-16 passes plus one smaller radix for the remaining factor.  Every
+// thread holds 16 elements; a sequence of T samples is served by T/16
+// threads.  Shared-memory indices are padded by one element per 32 to spread
+// banks.  Passes alternate between two shared buffers, so one barrier per
+// pass separates a pass's reads from the next pass's writes.  The kernel is
+// persistent over row pairs.
+#pragma once
+
+#include "common.cuh"
+
+namespace plv {
+namespace fft {
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 5); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    return make_float2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    return make_float2(a.x - b.x, a.y - b.y);
+}
+// a * w with w = (c, s) meaning c + i s
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+
+// Multiply a[r] by the twiddle tw[r * base], r = 1..15, from four table
+// loads (r = 1, 2, 4, 8) and products of those, at most three products deep;
+// only w^1..w^8 are held at once.
+__device__ __forceinline__ void apply_twiddles16(const float2 *__restrict__ tw, int base,
+                                                 float2 (&a)[16]) {
+    float2 w[9];
+    w[1] = __ldg(&tw[base]);
+    w[2] = __ldg(&tw[2 * base]);
+    w[4] = __ldg(&tw[4 * base]);
+    w[8] = __ldg(&tw[8 * base]);
+    w[3] = cmul(w[2], w[1]);
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+#pragma unroll
+    for (int r = 1; r <= 8; ++r) a[r] = cmul(a[r], w[r]);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) a[8 + r] = cmul(a[8 + r], cmul(w[8], w[r]));
+}
+
+// a * exp(-i pi m / 8), m in 0..7 (folds to a constant path after unrolling)
+__device__ __forceinline__ float2 rot16(float2 a, int m) {
+    const float c1 = 0.92387953251128675613f;  // cos(pi/8)
+    const float s1 = 0.38268343236508977173f;  // sin(pi/8)
+    const float h = 0.70710678118654752440f;   // cos(pi/4)
+    switch (m) {
+        case 0: return a;
+        case 1: return make_float2(fmaf(a.x, c1, a.y * s1), fmaf(a.y, c1, -a.x * s1));
+        case 2: return make_float2((a.x + a.y) * h, (a.y - a.x) * h);
+        case 3: return make_float2(fmaf(a.x, s1, a.y * c1), fmaf(a.y, s1, -a.x * c1));
+        case 4: return make_float2(a.y, -a.x);
+        case 5: return make_float2(fmaf(-a.x, s1, a.y * c1), fmaf(-a.y, s1, -a.x * c1));
+        case 6: return make_float2((a.y - a.x) * h, -(a.x + a.y) * h);
+        default: return make_float2(fmaf(-a.x, c1, a.y * s1), fmaf(-a.y, c1, -a.x * s1));
+    }
+}
+
+// In-register forward DFT of length R (R = 2, 4, 8, 16), natural order in
+// and out: radix-2 decimation in time, recursively.
+template <int R>
+struct Dft {
+    __device__ __forceinline__ static void run(float2 (&a)[R]) {
+        float2 e[R / 2], o[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            e[k] = a[2 * k];
+            o[k] = a[2 * k + 1];
+        }
+        Dft<R / 2>::run(e);
+        Dft<R / 2>::run(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const float2 t = rot16(o[k], (16 / R) * k);
+            a[k] = cadd(e[k], t);
+            a[k + R / 2] = csub(e[k], t);
+        }
+    }
+};
+template <>
+struct Dft<1> {
+    __device__ __forceinline__ static void run(float2 (&)[1]) {}
+};
+
+// Pass schedule for T = 2^L: 16 first, then the remainder radix 2^(L mod 4)
+// if any, then radix-16 passes.  For L < 8 the schedule is [16, 2^(L-4)].
+__host__ __device__ constexpr int npasses(int L) {
+    return L / 4 + (L % 4 != 0 ? 1 : 0);
+}
+__host__ __device__ constexpr int radix_of(int L, int p) {
+    return (p == 0) ? 16 : ((p == 1 && (L % 4) != 0) ? (1 << (L % 4)) : 16);
+}
+__host__ __device__ constexpr int ns_of(int L, int p) {
+    return p == 0 ? 1 : ns_of(L, p - 1) * radix_of(L, p - 1);
+}
+
+enum PassMode { kSmem = 0, kFromX = 1, kToHilbert = 2 };
+
+// One Stockham pass of radix R from shared buffer `src` to `dst` (distinct
+// buffers, so no barrier is needed between this pass's reads and writes).
+// NS is the length of the sub-transforms already formed.  MODE selects where
+// the inputs come from (src, or load(m) for the first pass, which also sums
+// |c|^2 into *power) and where the outputs go (dst, or dst with the analytic
+// mask folded in).
+template <int T, int R, int NS, int MODE, typename Load>
+__device__ __forceinline__ void stockham(const float2 *src, float2 *dst,
+                                         const float2 *__restrict__ tw, int lt,
+                                         const Load &load, float *power = nullptr) {
+    constexpr int B = 16 / R;  // butterflies per thread
+    constexpr int Q = T / 16;  // threads per sequence
+    float pw = 0.f;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int j = lt + q * Q;
+        const int k = j & (NS - 1);
+        float2 a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int m = j + r * (T / R);
+            if constexpr (MODE == kFromX) {
+                const float2 c = load(m);
+                a[r] = c;
+                pw = fmaf(c.x, c.x, fmaf(c.y, c.y, pw));
+            } else {
+                a[r] = src[padi(m)];
+            }
+        }
+        if constexpr (NS > 1) {
+            if constexpr (R == 16) {
+                apply_twiddles16(tw, k * (T / (NS * R)), a);
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r)
+                    a[r] = cmul(a[r], __ldg(&tw[r * k * (T / (NS * R))]));
+            }
+        }
+        Dft<R>::run(a);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int m = base + r * NS;
+            if constexpr (MODE == kToHilbert) {
+                // conj(-i sgn(m) C[m]) = sgn(m) (Im C, Re C)
+                const float sg = (m == 0 || m == T / 2) ? 0.f
+                                 : (m < T / 2 ? 1.f : -1.f);
+                dst[padi(m)] = make_float2(sg * a[r].y, sg * a[r].x);
+            } else {
+                dst[padi(m)] = a[r];
+            }
+        }
+    }
+    if constexpr (MODE == kFromX) *power = pw;
+    __syncthreads();
+}
+
+// Passes p in [P, PEND), ping-ponging between the two buffers; pass p reads
+// buffer (p & 1) and writes buffer (p & 1) ^ 1.
+struct NoLoad {
+    __device__ float2 operator()(int) const { return make_float2(0.f, 0.f); }
+};
+
+template <int L, int P, int PEND>
+__device__ __forceinline__ void middle_passes(float2 *const (&buf)[2], const float2 *tw,
+                                              int lt) {
+    if constexpr (P < PEND) {
+        stockham<(1 << L), radix_of(L, P), ns_of(L, P), kSmem>(
+            buf[P & 1], buf[(P & 1) ^ 1], tw, lt, NoLoad{});
+        middle_passes<L, P + 1, PEND>(buf, tw, lt);
+    }
+}
+
+// Unit phasor of z = a + i b (Eq. 4); |z|^2 <= floor2 (|z| = 0 by default)
+// gives 0.  Very small or very large magnitudes are rescaled by a power of
+// two first so the squared norm neither underflows nor overflows.
+__device__ __forceinline__ float2 unit_phasor(float a, float b, float floor2 = 0.0f) {
+    float r2 = fmaf(a, a, b * b);
+    if (!(r2 > floor2)) return make_float2(0.f, 0.f);
+    if (r2 < 1e-30f || r2 > 1e30f) {
+        const float sc = r2 < 1e-30f ? 0x1p+60f : 0x1p-60f;
+        a *= sc;
+        b *= sc;
+        r2 = fmaf(a, a, b * b);
+    }
+    // 1/sqrt(r2): hardware estimate refined by one Newton step
+    float inv = rsqrtf(r2);
+    inv = inv * fmaf(-0.5f * r2 * inv, inv, 1.5f);
+    return make_float2(a * inv, b * inv);
+}
+
+// As unit_phasor, also returning rinv = 1/|z| (0 where the phasor is 0).
+__device__ __forceinline__ float2 unit_phasor_inv(float a, float b, float floor2,
+                                                  float &rinv) {
+    float r2 = fmaf(a, a, b * b);
+    rinv = 0.f;
+    if (!(r2 > floor2)) return make_float2(0.f, 0.f);
+    float sc = 1.0f;
+    if (r2 < 1e-30f || r2 > 1e30f) {
+        sc = r2 < 1e-30f ? 0x1p+60f : 0x1p-60f;
+        a *= sc;
+        b *= sc;
+        r2 = fmaf(a, a, b * b);
+    }
+    float inv = rsqrtf(r2);
+    inv = inv * fmaf(-0.5f * r2 * inv, inv, 1.5f);
+    rinv = inv * sc;
+    return make_float2(a * inv, b * inv);
+}
+
+template <int L>
+struct K1Cfg {
+    static constexpr int T = 1 << L;
+    static constexpr int Q = T / 16;                  // threads / sequence
+    static constexpr int SEQ = Q >= 256 ? 1 : 256 / Q;  // sequences / CTA
+    static constexpr int THREADS = Q * SEQ;
+    static constexpr int SMEM_SEQ = T + T / 32;         // padded elements
+    // two ping-pong buffers per sequence, then the per-sequence power
+    static constexpr size_t SMEM =
+        (size_t)SEQ * 2 * SMEM_SEQ * sizeof(float2) + (size_t)SEQ * sizeof(float);
+    // resident CTAs per SM the register budget is sized for
+    static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;
+};
+
+// The Hilbert transform of real rows, two rows per complex FFT, for any
+// Task providing
+//   float2 load(int64_t r0, bool v0, int64_t r1, bool v1, int m):
+//       the complex sample c[m] = u0[m] + i u1[m] of rows r0, r1;
+//   void finish(int64_t r0, bool v0, int64_t r1, bool v1, int m,
+//               float h0, float h1, float floor2):
+//       consumes H{u0}[m], H{u1}[m]; floor2 is 2^-40 of the pair's mean
+//       |c|^2 (the rounding floor of the transform).
+// With c = u0 + i u1: w = IFFT(-i sgn(k) FFT(c)) = H{u0} + i H{u1}, computed
+// as conj(FFT(conj(W))) / T with conj(W) folded into the last forward pass.
+template <int L, class Task>
+__global__ void __launch_bounds__(K1Cfg<L>::THREADS, K1Cfg<L>::MIN_BLOCKS)
+k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
+                int64_t nbatch) {
+    using C = K1Cfg<L>;
+    constexpr int T = C::T;
+    constexpr int NP = npasses(L);
+    extern __shared__ __align__(16) float2 smem[];
+    const int lt = threadIdx.x % C::Q;
+    const int sq = threadIdx.x / C::Q;
+    float2 *const buf[2] = {smem + (2 * sq) * C::SMEM_SEQ, smem + (2 * sq + 1) * C::SMEM_SEQ};
+    float *s_pow = (float *)(smem + 2 * C::SEQ * C::SMEM_SEQ);
+    constexpr float invT = 1.0f / (float)T;
+    // pass p writes buffer ((p & 1) ^ 1); FWD_OUT holds the masked spectrum
+    constexpr int FWD_OUT = ((NP - 1) & 1) ^ 1;
+
+    for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
+        const int64_t pair = b * C::SEQ + sq;
+        const int64_t r0 = 2 * pair, r1 = 2 * pair + 1;
+        const bool v0 = r0 < rows, v1 = r1 < rows;
+        // the previous pair's final stage is done with the buffers and s_pow
+        __syncthreads();
+        if (lt == 0) s_pow[sq] = 0.f;  // ordered before the adds by pass 0's barrier
+        float pw;
+        auto load = [&](int m) { return task.load(r0, v0, r1, v1, m); };
+        stockham<T, radix_of(L, 0), 1, kFromX>(nullptr, buf[1], tw, lt, load, &pw);
+        // sum of |c|^2 over the sequence (its lanes are an aligned group of Q
+        // threads, or whole warps when Q >= 32)
+#pragma unroll
+        for (int off = 1; off < (C::Q < 32 ? C::Q : 32); off <<= 1)
+            pw += __shfl_xor_sync(0xffffffffu, pw, off);
+        if ((lt & 31) == 0) atomicAdd(&s_pow[sq], pw);
+        middle_passes<L, 1, NP - 1>(buf, tw, lt);
+        stockham<T, radix_of(L, NP - 1), ns_of(L, NP - 1), kToHilbert>(
+            buf[(NP - 1) & 1], buf[FWD_OUT], tw, lt, NoLoad{});
+        float2 *const ibuf[2] = {buf[FWD_OUT], buf[FWD_OUT ^ 1]};
+        stockham<T, radix_of(L, 0), 1, kSmem>(ibuf[0], ibuf[1], tw, lt, NoLoad{});
+        middle_passes<L, 1, NP - 1>(ibuf, tw, lt);
+        stockham<T, radix_of(L, NP - 1), ns_of(L, NP - 1), kSmem>(
+            ibuf[(NP - 1) & 1], ibuf[((NP - 1) & 1) ^ 1], tw, lt, NoLoad{});
+        const float2 *w_out = ibuf[((NP - 1) & 1) ^ 1];
+
+        const float floor2 = 0x1p-40f * (s_pow[sq] * invT);
+#pragma unroll 4
+        for (int u = 0; u < 16; ++u) {
+            const int m = lt + u * C::Q;
+            const float2 w = w_out[padi(m)];
+            task.finish(r0, v0, r1, v1, m, w.x * invT, -w.y * invT, floor2);
+        }
+    }
+}
+
+template <int L, class Task>
+cudaError_t launch_hilbert_pairs(int num_sms, cudaStream_t st, const Task &task,
+                                 const float2 *tw, int64_t rows) {
+    using C = K1Cfg<L>;
+    auto kern = k_hilbert_pairs<L, Task>;
+    if (C::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(
+            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS,
+                                                                  C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t pairs = (rows + 1) / 2;
+    const int64_t nbatch = (pairs + C::SEQ - 1) / C::SEQ;
+    if (nbatch == 0) return cudaSuccess;
+    int64_t grid = (int64_t)per_sm * num_sms * 4;
+    if (grid > nbatch) grid = nbatch;
+    kern<<<(unsigned)grid, C::THREADS, C::SMEM, st>>>(task, tw, rows, nbatch);
+    return cudaGetLastError();
+}
+
+// Dispatch on log2(T) to the compiled lengths.
+template <class Task>
+cudaError_t launch_hilbert_pow2(int num_sms, cudaStream_t st, int log2T, const Task &task,
+                                const float2 *tw, int64_t rows) {
+    switch (log2T) {
+        case 5: return launch_hilbert_pairs<5>(num_sms, st, task, tw, rows);
+        case 6: return launch_hilbert_pairs<6>(num_sms, st, task, tw, rows);
+        case 7: return launch_hilbert_pairs<7>(num_sms, st, task, tw, rows);
+        case 8: return launch_hilbert_pairs<8>(num_sms, st, task, tw, rows);
+        case 9: return launch_hilbert_pairs<9>(num_sms, st, task, tw, rows);
+        case 10: return launch_hilbert_pairs<10>(num_sms, st, task, tw, rows);
+        case 11: return launch_hilbert_pairs<11>(num_sms, st, task, tw, rows);
+        case 12: return launch_hilbert_pairs<12>(num_sms, st, task, tw, rows);
+        case 13: return launch_hilbert_pairs<13>(num_sms, st, task, tw, rows);
+        case 14: return launch_hilbert_pairs<14>(num_sms, st, task, tw, rows);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fft
+}  // namespace plv

@@ -1,0 +1,251 @@
+// k_backward.cu -- K5: gradient of L = sum_ij (g_plv PLV + g_iplv iPLV +
+// g_ciplv ciPLV)_ij with respect to the real input signals x, through the
+// read-outs (Eq. 7, 13, 14), the Gram (Eq. 7), the normalisation (Eq. 4) and
+// the analytic signal (Eq. 3).
+//
+// With R = Re C, I = Im C and d = (1 - R)(1 + R):
+//   G_ij = dL/dR_ij + i dL/dI_ij,
+//     dL/dR = g_plv R/|C| + g_ciplv I R / d^(3/2),
+//     dL/dI = g_plv I/|C| + g_iplv sign(I) + g_ciplv / d^(1/2)
+//   (each term only where the forward read-out is differentiable and
+//   nonzero: |C| > 0, d > 0; the diagonal, whose forward values do not
+//   depend on x, contributes nothing).
+//   dL = Re sum conj(Gamma_P) dP with Gamma_P = (G + G^H) P / T = S P / T.
+//   P = z/|z|:  Gamma_z = i P Im(conj(P) Gamma_P) / |z|.
+//   z = A x with A = IFFT diag(h) FFT Hermitian (real part identity, imaginary
+//   part the Hilbert transform H, H^T = -H):
+//     dL/dx = Re Gamma_z - H{Im Gamma_z}.
+//
+// Stages (all FP32):
+//   1. recompute P and 1/|z| from x (the forward FFT task, fft.cuh);
+//   2. k_bwd_s: S = G + G^H from C and the upstream gradients, 32x32 tiles
+//      staged through shared memory for the transposed reads;
+//   3. k_bwd_gemm: Gamma = S P / T.  S is Hermitian, so
+//      Gamma[i][t] = sum_k conj(S[k][i]) P[k][t] / T and both operands are
+//      read as rows (no transposes): 128x128 tiles, 8x8 complex register
+//      blocks, double-buffered shared memory;
+//   4. BwdTask on the FFT engine: u = -Im(P) s, v = Re(P) s with
+//      s = Im(conj(P) Gamma) / |z|, then grad = u - H{v}.
+#include "fft.cuh"
+#include "readout.cuh"
+
+namespace plv {
+namespace {
+
+using namespace fft;
+
+__device__ __forceinline__ float2 gfun(float2 c, float g1, float g2, float g3) {
+    const float R = c.x, I = c.y;
+    float a = 0.f, b = 0.f;
+    if (g1 != 0.f) {
+        const float mag = sqrtf(fmaf(R, R, I * I));
+        if (mag > 0.f) {
+            a = fmaf(g1, R / mag, a);
+            b = fmaf(g1, I / mag, b);
+        }
+    }
+    if (g2 != 0.f) b += I > 0.f ? g2 : (I < 0.f ? -g2 : 0.f);
+    if (g3 != 0.f) {
+        const float d = ciplv_den(R);
+        if (d > 0.f) {
+            const float sd = sqrtf(d);
+            b += g3 / sd;
+            a += g3 * I * R / (d * sd);
+        }
+    }
+    return make_float2(a, b);
+}
+
+// S = G + G^H for one epoch tile pair; S planar [B][2][N][N].
+__global__ void __launch_bounds__(256)
+k_bwd_s(const float2 *__restrict__ C, const float *__restrict__ g1,
+        const float *__restrict__ g2, const float *__restrict__ g3, int N,
+        float *__restrict__ S) {
+    __shared__ float2 Gt[32][33];
+    const int b = blockIdx.z;
+    const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t NN = (int64_t)N * N;
+    const int64_t eb = (int64_t)b * NN;
+    auto G = [&](int r, int c) -> float2 {
+        if (r >= N || c >= N || r == c) return make_float2(0.f, 0.f);
+        const int64_t q = eb + (int64_t)r * N + c;
+        return gfun(C[q], g1 ? g1[q] : 0.f, g2 ? g2[q] : 0.f, g3 ? g3[q] : 0.f);
+    };
+    // G of the transposed tile: Gt[yy][tx] = G(bj + yy, bi + tx)
+    for (int yy = ty; yy < 32; yy += 8) Gt[yy][tx] = G(bj + yy, bi + tx);
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int i = bi + yy, j = bj + tx;
+        if (i >= N || j >= N) continue;
+        const float2 gij = G(i, j);
+        const float2 gji = Gt[tx][yy];  // G(j, i)
+        const int64_t q = (int64_t)b * 2 * NN + (int64_t)i * N + j;
+        S[q] = gij.x + gji.x;       // Re(G_ij + conj(G_ji))
+        S[q + NN] = gij.y - gji.y;  // Im
+    }
+}
+
+constexpr int BM = 128, BK = 8;
+
+// Gamma[b][i][plane][t] = (1/T) sum_k conj(S[b][k][i]) P[b][k][plane][t].
+__global__ void __launch_bounds__(256, 1)
+k_bwd_gemm(const float *__restrict__ S, const float *__restrict__ P, int N, int64_t ld,
+           float invT, float *__restrict__ Gm) {
+    __shared__ __align__(16) float As[2][2][BK][BM];
+    __shared__ __align__(16) float Bs[2][2][BK][BM];
+    const int b = blockIdx.z;
+    const int i0 = blockIdx.y * BM;
+    const int64_t t0 = (int64_t)blockIdx.x * BM;
+    const int64_t NN = (int64_t)N * N;
+    const float *Sr = S + (int64_t)b * 2 * NN;
+    const float *Si = Sr + NN;
+    const float *Pb = P + (int64_t)b * N * 2 * ld;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int lk = tid >> 5, lc = (tid & 31) * 4;  // loader: row k, 4 columns
+    const bool vi = i0 + lc < N;                   // N % 4 may be nonzero: per element
+    const bool vt = t0 + lc < ld;
+
+    float cre[8][8], cim[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) { cre[a][c] = 0.f; cim[a][c] = 0.f; }
+
+    auto ld_s = [&](const float *base, int k) -> float4 {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < N && vi) {
+            const float *p = base + (int64_t)k * N + i0 + lc;
+            v.x = p[0];
+            if (i0 + lc + 1 < N) v.y = p[1];
+            if (i0 + lc + 2 < N) v.z = p[2];
+            if (i0 + lc + 3 < N) v.w = p[3];
+        }
+        return v;
+    };
+    auto ld_p = [&](int k, int plane) -> float4 {
+        if (k < N && vt)
+            return __ldg((const float4 *)(Pb + ((int64_t)k * 2 + plane) * ld + t0 + lc));
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    float4 sr = ld_s(Sr, lk), si = ld_s(Si, lk), pr = ld_p(lk, 0), pi = ld_p(lk, 1);
+    auto stash = [&](int st) {
+        *(float4 *)&As[st][0][lk][lc] = sr;
+        *(float4 *)&As[st][1][lk][lc] = si;
+        *(float4 *)&Bs[st][0][lk][lc] = pr;
+        *(float4 *)&Bs[st][1][lk][lc] = pi;
+    };
+    stash(0);
+    __syncthreads();
+    const int nk = (N + BK - 1) / BK;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int st = kt & 1;
+        if (kt + 1 < nk) {
+            const int k = (kt + 1) * BK + lk;
+            sr = ld_s(Sr, k);
+            si = ld_s(Si, k);
+            pr = ld_p(k, 0);
+            pi = ld_p(k, 1);
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a_r[8], a_i[8], b_r[8], b_i[8];
+            *(float4 *)&a_r[0] = *(const float4 *)&As[st][0][kk][ty * 4];
+            *(float4 *)&a_r[4] = *(const float4 *)&As[st][0][kk][64 + ty * 4];
+            *(float4 *)&a_i[0] = *(const float4 *)&As[st][1][kk][ty * 4];
+            *(float4 *)&a_i[4] = *(const float4 *)&As[st][1][kk][64 + ty * 4];
+            *(float4 *)&b_r[0] = *(const float4 *)&Bs[st][0][kk][tx * 4];
+            *(float4 *)&b_r[4] = *(const float4 *)&Bs[st][0][kk][64 + tx * 4];
+            *(float4 *)&b_i[0] = *(const float4 *)&Bs[st][1][kk][tx * 4];
+            *(float4 *)&b_i[4] = *(const float4 *)&Bs[st][1][kk][64 + tx * 4];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    // conj(s) p = (sr pr + si pi) + i (sr pi - si pr)
+                    cre[a][c] = fmaf(a_r[a], b_r[c], cre[a][c]);
+                    cre[a][c] = fmaf(a_i[a], b_i[c], cre[a][c]);
+                    cim[a][c] = fmaf(a_r[a], b_i[c], cim[a][c]);
+                    cim[a][c] = fmaf(-a_i[a], b_r[c], cim[a][c]);
+                }
+        }
+        if (kt + 1 < nk) stash(st ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int i = i0 + (a < 4 ? ty * 4 + a : 64 + ty * 4 + a - 4);
+        if (i >= N) continue;
+        float *gr = Gm + ((int64_t)b * N + i) * 2 * ld;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t t = t0 + (h == 0 ? tx * 4 : 64 + tx * 4);
+            if (t >= ld) continue;
+            *(float4 *)(gr + t) = make_float4(cre[a][4 * h] * invT, cre[a][4 * h + 1] * invT,
+                                              cre[a][4 * h + 2] * invT, cre[a][4 * h + 3] * invT);
+            *(float4 *)(gr + ld + t) =
+                make_float4(cim[a][4 * h] * invT, cim[a][4 * h + 1] * invT,
+                            cim[a][4 * h + 2] * invT, cim[a][4 * h + 3] * invT);
+        }
+    }
+}
+
+// Stage 4 on the FFT engine: rows of v = Re(P) s in, grad = -Im(P) s - H{v}
+// out, s = Im(conj(P) Gamma) / |z|.
+struct BwdTask {
+    const float *P;     // [rows][2][ld]
+    const float *Gm;    // [rows][2][ld]
+    const float *rinv;  // [rows][ld]
+    float *grad;        // [rows][T]
+    int64_t ld;
+    int T;
+    __device__ float s_of(int64_t r, int m, float &pr, float &pi) const {
+        const float *p = P + r * 2 * ld + m;
+        const float *g = Gm + r * 2 * ld + m;
+        pr = p[0];
+        pi = p[ld];
+        const float gr = g[0], gi = g[ld];
+        return fmaf(pr, gi, -pi * gr) * rinv[r * ld + m];
+    }
+    __device__ float2 load(int64_t r0, bool v0, int64_t r1, bool v1, int m) const {
+        float pr, pi, a = 0.f, b = 0.f;
+        if (v0) a = s_of(r0, m, pr, pi) * pr;
+        if (v1) b = s_of(r1, m, pr, pi) * pr;
+        return make_float2(a, b);
+    }
+    __device__ void finish(int64_t r0, bool v0, int64_t r1, bool v1, int m, float h0,
+                           float h1, float) const {
+        float pr, pi;
+        if (v0) {
+            const float s = s_of(r0, m, pr, pi);
+            grad[r0 * T + m] = -pi * s - h0;
+        }
+        if (v1) {
+            const float s = s_of(r1, m, pr, pi);
+            grad[r1 * T + m] = -pi * s - h1;
+        }
+    }
+};
+
+}  // namespace
+
+cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
+                            int log2T, const float2 *C, const float *g1, const float *g2,
+                            const float *g3, const float *P, const float *rinv, float *S,
+                            float *Gm, float *grad) {
+    const int64_t ld = padded_len(T);
+    dim3 sg((N + 31) / 32, (N + 31) / 32, batch);
+    k_bwd_s<<<sg, 256, 0, st>>>(C, g1, g2, g3, N, S);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 gg((unsigned)((ld + BM - 1) / BM), (N + BM - 1) / BM, batch);
+    k_bwd_gemm<<<gg, 256, 0, st>>>(S, P, N, ld, 1.0f / (float)T, Gm);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    BwdTask task{P, Gm, rinv, grad, ld, T};
+    return launch_hilbert_pow2(h->num_sms, st, log2T, task, twiddle_table(h, log2T),
+                               (int64_t)batch * N);
+}
+
+}  // namespace plv

@@ -60,6 +60,38 @@ static int log2_exact(int T) {
     return l;
 }
 
+// Grow the handle's scratch to at least `bytes`.  Growing allocates, which
+// is refused while `s` is capturing a graph.
+static plv_status ensure_workspace(Handle &h, cudaStream_t s, size_t bytes) {
+    if (h.ws_bytes >= bytes) return PLV_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(PLV_ERR_INVALID,
+                    "scratch must grow to %zu bytes while the stream is capturing; "
+                    "make one call of the same size outside the capture first", bytes);
+    const size_t others = h.workspace_used - h.ws_bytes;
+    if (h.workspace_limit && others + bytes > h.workspace_limit)
+        return fail(PLV_ERR_ALLOC, "scratch of %zu bytes exceeds the workspace limit %zu",
+                    bytes, h.workspace_limit);
+    if (h.ws) {
+        cudaError_t e = cudaFree(h.ws);  // synchronises with work still using it
+        h.ws = nullptr;
+        h.workspace_used = others;
+        h.ws_bytes = 0;
+        if (e != cudaSuccess) return check_cuda(e, "cudaFree(scratch)");
+    }
+    cudaError_t e = cudaMalloc(&h.ws, bytes);
+    if (e != cudaSuccess) {
+        h.ws = nullptr;
+        cudaGetLastError();
+        return fail(PLV_ERR_ALLOC, "cudaMalloc(%zu) for scratch: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    h.ws_bytes = bytes;
+    h.workspace_used = others + bytes;
+    return PLV_OK;
+}
+
 }  // namespace plv
 
 using namespace plv;
@@ -134,6 +166,7 @@ plv_status plv_destroy(plv_handle *hp) {
         cudaDeviceSynchronize();
         if (h.twiddles) cudaFree(h.twiddles);
         if (h.status) cudaFree(h.status);
+        if (h.ws) cudaFree(h.ws);
     }
     delete hp;
     return PLV_OK;
@@ -258,6 +291,52 @@ plv_status plv_metrics(plv_handle *hp, void *stream, const void *C, int batch,
     return check_cuda(launch_metrics((cudaStream_t)stream, (const float2 *)C, batch, N,
                                      plv, iplv, ciplv),
                       "plv_metrics launch");
+}
+
+plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype dtype,
+                        int batch, int N, int T, int64_t ldx, const void *C,
+                        const float *g_plv, const float *g_iplv, const float *g_ciplv,
+                        float *grad_x) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_backward: handle is NULL");
+    if (batch < 0 || N < 0 || T <= 0)
+        return fail(PLV_ERR_INVALID, "plv_backward: bad sizes batch=%d N=%d T=%d", batch, N, T);
+    if (dtype != PLV_F32 && dtype != PLV_F64)
+        return fail(PLV_ERR_INVALID, "plv_backward: unknown dtype %d", (int)dtype);
+    if (ldx < T) return fail(PLV_ERR_INVALID, "plv_backward: ldx < T");
+    if (batch == 0 || N == 0) return PLV_OK;
+    if (!grad_x) return fail(PLV_ERR_INVALID, "plv_backward: grad_x is NULL");
+    const int L = log2_exact(T);
+    if (L < kMinLog2T || L > kMaxLog2T)
+        return fail(PLV_ERR_UNSUPPORTED,
+                    "plv_backward: T = %d (this build's FFT takes powers of two "
+                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2T);
+    PLV_GUARD(&hp->h);
+    Handle &h = hp->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g_plv && !g_iplv && !g_ciplv)
+        return check_cuda(cudaMemsetAsync(grad_x, 0, sizeof(float) * (size_t)batch * N * T, s),
+                          "plv_backward: zero grad");
+    if (!x || !C) return fail(PLV_ERR_INVALID, "plv_backward: NULL x or C");
+    if (((uintptr_t)C % 8) != 0 || ((uintptr_t)x % (dtype == PLV_F32 ? 4 : 8)) != 0 ||
+        ((uintptr_t)grad_x % 4) != 0)
+        return fail(PLV_ERR_INVALID, "plv_backward: misaligned pointer");
+    const int64_t ld = padded_len(T);
+    const size_t rows = (size_t)batch * N;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t bP = up(rows * 2 * ld * 4), bR = up(rows * ld * 4), bG = up(rows * 2 * ld * 4),
+                 bS = up((size_t)batch * 2 * N * N * 4);
+    std::lock_guard<std::mutex> lock(h.mu);
+    plv_status st = ensure_workspace(h, s, bP + bR + bG + bS);
+    if (st != PLV_OK) return st;
+    char *w = (char *)h.ws;
+    float *P = (float *)w, *rinv = (float *)(w + bP), *Gm = (float *)(w + bP + bR),
+          *S = (float *)(w + bP + bR + bG);
+    st = check_cuda(launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv),
+                    "plv_backward: recompute");
+    if (st != PLV_OK) return st;
+    return check_cuda(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,
+                                      g_ciplv, P, rinv, S, Gm, grad_x),
+                      "plv_backward launch");
 }
 
 plv_status plv_sync_status(plv_handle *hp, void *stream, int *device_status) {

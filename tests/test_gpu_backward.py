@@ -1,0 +1,132 @@
+"""GPU parity of the backward pass (through the C ABI): against FP64
+autograd through plain torch ops and against FP64 central finite
+differences of the C oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import backward as obw
+from paper_1710_08037_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h32():
+    import paper_1710_08037_gb300 as plv
+    h = plv.Handle(precision="fp32")
+    yield h
+    h.close()
+
+
+def _grads(rng, B, N, which):
+    out = []
+    for w in ("plv", "iplv", "ciplv"):
+        if w in which:
+            g = rng.standard_normal((B, N, N))
+            out.append(g)
+        else:
+            out.append(None)
+    return out
+
+
+def _gpu_grad(h, x, gs, prec_forward="fp32"):
+    import paper_1710_08037_gb300 as plv
+    hf = h if prec_forward == "fp32" else plv.Handle(precision=prec_forward)
+    xd = torch.tensor(x, device="cuda", dtype=torch.float32)
+    E, N, T = x.shape
+    P = hf.plv_analytic(xd)
+    C = hf.plv_gram(P, E, N, T, plv=False, iplv=False, ciplv=False, C=True)["C"]
+    gt = [None if g is None else torch.tensor(g, device="cuda",
+                                              dtype=torch.float32) for g in gs]
+    g = h.plv_backward(xd, C, *gt)
+    torch.cuda.synchronize()
+    return g.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("which", [("plv",), ("iplv",), ("ciplv",),
+                                   ("plv", "iplv", "ciplv")])
+@pytest.mark.parametrize("N,T", [(16, 256), (67, 128)])
+def test_backward_vs_torch_fp64(h32, which, N, T):
+    rng = np.random.default_rng(N * 7 + T + len(which))
+    B = 2
+    x = synth.bandlimited(B, N, T, seed=N + T, fs=1000.0, band=(8, 60),
+                          dtype=torch.float64).numpy()
+    x = x.astype(np.float32).astype(np.float64)
+    gs = _grads(rng, B, N, which)
+    got = _gpu_grad(h32, x, gs)
+    ref = np.stack([obw.torch_grad(x[e], *(None if g is None else g[e]
+                                           for g in gs)) for e in range(B)])
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref).max() / scale
+    rel2 = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 2e-3 and rel2 < 5e-4, (err, rel2)
+
+
+def test_backward_vs_finite_differences(h32):
+    """FP64 central differences of the oracle's forward (direct DFT + the
+    pairwise loop) at 24 entries, N = 16, T = 256."""
+    rng = np.random.default_rng(5)
+    N, T = 16, 256
+    x = rng.standard_normal((1, N, T)).astype(np.float32).astype(np.float64)
+    g1 = rng.standard_normal((N, N))
+    g3 = rng.standard_normal((N, N))
+    np.fill_diagonal(g3, 0.0)
+    got = _gpu_grad(h32, x, [g1[None], None, g3[None]])[0].reshape(-1)
+    ent = rng.choice(N * T, size=24, replace=False)
+    fd = obw.fd_grad(x[0], g1, None, g3, entries=ent)
+    scale = np.abs(got).max()
+    assert np.max(np.abs(got[ent] - fd)) < 2e-3 * scale
+
+
+def test_ciplv_loss_workload_sampled(h32):
+    """The differentiable-loss workload: 16 recordings, N = 1024, T = 4096,
+    loss = sum of ciPLV over a seeded 10 % pair mask; two recordings checked
+    against FP64 autograd through plain torch ops."""
+    B, N, T = 16, 1024, 4096
+    x = synth.bandlimited(B, N, T, seed=1005, device="cuda")
+    mask = synth.random_pair_mask(N, 0.10, seed=1005, device="cuda")
+    g3 = mask.to(torch.float32).expand(B, N, N).contiguous()
+    P = h32.plv_analytic(x)
+    C = h32.plv_gram(P, B, N, T, plv=False, iplv=False, ciplv=False,
+                     C=True)["C"]
+    g = h32.plv_backward(x, C, None, None, g3)
+    torch.cuda.synchronize()
+    assert torch.isfinite(g).all()
+    for e in (0, 11):
+        xe = x[e].double().cpu().numpy()
+        ref = obw.torch_grad(xe, None, None, mask.double().cpu().numpy())
+        got = g[e].double().cpu().numpy()
+        rel2 = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        print("ciPLV loss backward: rel2", rel2, "max rel", err)
+        assert rel2 < 1e-3 and err < 5e-3
+
+
+def test_autograd_function(h32):
+    """connectivity() is a torch.autograd.Function whose backward is
+    plv_backward; its gradient matches FP64 autograd of plain torch ops."""
+    import paper_1710_08037_gb300 as plv
+    rng = np.random.default_rng(9)
+    N, T = 12, 128
+    x = rng.standard_normal((1, N, T)).astype(np.float32)
+    xd = torch.tensor(x, device="cuda", requires_grad=True)
+    p, ip, cp = plv.connectivity(xd, h32)
+    w = torch.tensor(rng.standard_normal((1, N, N)), device="cuda",
+                     dtype=torch.float32)
+    (p * w).sum().add((cp * w.transpose(1, 2)).sum()).backward()
+    ref = obw.torch_grad(x[0].astype(np.float64), w[0].double().cpu().numpy(),
+                         None, w[0].T.double().cpu().numpy())
+    got = xd.grad[0].double().cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 5e-4
+
+
+def test_backward_zero_grads_and_validation(h32):
+    from paper_1710_08037_gb300 import _lib
+    x = torch.randn(1, 8, 64, device="cuda")
+    C = torch.zeros(1, 8, 8, dtype=torch.complex64, device="cuda")
+    g = h32.plv_backward(x, C)
+    assert torch.all(g == 0)
+    rc = h32.lib.plv_backward(h32.h, None, x.data_ptr(), 0, 1, 8, 100, 100,
+                              C.data_ptr(), None, None, None, g.data_ptr())
+    assert rc == _lib.PLV_ERR_UNSUPPORTED
