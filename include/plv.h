@@ -178,6 +178,44 @@ plv_status plv_backward(plv_handle *h, void *stream, const void *x,
                         const void *C, const float *g_plv, const float *g_iplv,
                         const float *g_ciplv, float *grad_x);
 
+/* Size of the fixed scratch array behind plv_backward_noalloc: 64 MiB. */
+#define PLV_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/* plv_backward without any allocation and without a handle.  The paper has
+ * no counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc, for example:
+ *   - a plugin run inside another framework's execution engine that forbids
+ *     allocation during its enqueue step;
+ *   - a host whose device memory is already owned by a pooling allocator
+ *     that must not be bypassed;
+ *   - a latency-critical loop that must not pay for (or risk failing) an
+ *     allocation.
+ * Instead of handle scratch it uses one fixed device array of
+ * PLV_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits (plus the FFT twiddle tables, also static).
+ *
+ * Same arguments and results as plv_backward (minus the handle); it runs on
+ * the CURRENT device.  A problem whose scratch (batch*N*ld*20 + batch*N*N*8
+ * bytes, each of the four parts rounded up to 256 bytes; ld = plv_phasor_ld(T))
+ * exceeds the array is rejected with PLV_ERR_INVALID and a message naming
+ * the sizes; nothing is launched.  For example batch = 4, N = 128, T = 4096
+ * fits.
+ *
+ * The first call on each device sets that device up: it looks up the
+ * array's device address and uploads the twiddle tables (synchronous
+ * copies).  Make that first call outside any stream capture.
+ *
+ * All calls share the one array.  Each call writes every scratch element it
+ * reads, so no clearing is needed between calls.  Calls whose work overlaps
+ * on the GPU (different streams, or graphs replayed concurrently) race on
+ * the array and corrupt each other's results: serialise them.
+ * plv_last_error(NULL) returns the message of a failure. */
+plv_status plv_backward_noalloc(void *stream, const void *x, plv_dtype dtype,
+                                int batch, int N, int T, int64_t ldx,
+                                const void *C, const float *g_plv,
+                                const float *g_iplv, const float *g_ciplv,
+                                float *grad_x);
+
 /* Read (and clear) the handle's device status word after synchronising
  * `stream`.  *device_status receives PLV_OK or the recorded error. */
 plv_status plv_sync_status(plv_handle *h, void *stream, int *device_status);

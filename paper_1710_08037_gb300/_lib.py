@@ -55,6 +55,8 @@ SIGNATURES = {
     "plv_metrics": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "plv_backward": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i64, _vp, _vp, _vp,
                           _vp, _vp]),
+    "plv_backward_noalloc": (_i, [_vp, _vp, _i, _i, _i, _i, _i64, _vp, _vp,
+                                  _vp, _vp, _vp]),
     "plv_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
 }
 
