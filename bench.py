@@ -118,7 +118,6 @@ class ClockSampler:
 # launch by epochs (profiles/k_gram_tc_and_k_analytic_bandlimited-N4096-T4096-E4.md).
 # An entry is removed when the kernel changes after its capture.
 TRAFFIC = {
-    ("k_gram_tc", "bandlimited-N4096-T4096-E30", "bf16x3"): (1.943164e9 + 1.039759e9) * 30 / 4,
 }
 
 

@@ -98,12 +98,16 @@ plv_precision plv_get_precision(const plv_handle *h);
  * rounded up to a multiple of 32; the padding samples are zero. */
 int64_t plv_phasor_ld(int T);
 
-/* Bytes of the phasor operand buffer P for `batch` epochs of N x T (both
- * precisions use 8 bytes per padded sample):
- *   FP32:   float  P[batch][N][2][ld]        plane 0 = Re P, 1 = Im P
- *   BF16X3: bf16   P[batch][4][N][ld]        planes Re_hi, Re_lo, Im_hi, Im_lo
- *   FP16X3: half   P[batch][4][N][ld]        same planes, FP16 hi / lo
- * with ld = plv_phasor_ld(T).  Returns 0 for invalid sizes. */
+/* Bytes of the phasor operand buffer P for `batch` epochs of N x T (8 bytes
+ * per padded sample), ld = plv_phasor_ld(T):
+ *   FP32:   float P[batch][N][2][ld]: plane 0 = Re P, plane 1 = Im P.
+ *   BF16X3 / FP16X3: 16-bit hi / lo splits in blocks of 128 rows x 32
+ *   samples x 4 planes (Re_hi, Re_lo, Im_hi, Im_lo), 32 KB each, stored
+ *   in the order [batch][ceil(N/128)][ld/32]; inside a block [plane][row]
+ *   [32 samples], the four 16-byte chunks of each 64-byte row rotated by
+ *   XOR with ((row >> 1) & 3) (the tensor cores' 64-byte swizzle).  Rows
+ *   are padded with zeros to a multiple of 128.
+ * Returns 0 for invalid sizes. */
 size_t plv_phasor_bytes(const plv_handle *h, int batch, int N, int T);
 
 /* Make the handle's per-length tables for T samples (twiddles).  The first
@@ -118,7 +122,7 @@ plv_status plv_prepare(plv_handle *h, int T);
  *          converted to FP32 on load; the arithmetic is FP32).
  *   P    : plv_phasor_bytes(h, batch, N, T) bytes, written completely
  *          (including zero padding).
- * Supported T: powers of two, 32 <= T <= 16384 (others: PLV_ERR_UNSUPPORTED).
+ * Supported T: powers of two, 32 <= T <= 8192 (others: PLV_ERR_UNSUPPORTED).
  * batch = 0 or N = 0 is a no-op. */
 plv_status plv_analytic(plv_handle *h, void *stream, const void *x,
                         plv_dtype dtype, int batch, int N, int T, int64_t ldx,
@@ -149,6 +153,37 @@ plv_status plv_normalize(plv_handle *h, void *stream, const void *z,
 plv_status plv_gram(plv_handle *h, void *stream, const void *P, int batch,
                     int N, int T, unsigned out_mask, float *plv, float *iplv,
                     float *ciplv, void *C, double *diag_dev);
+
+/* One problem of a grouped Gram: phasors written by plv_analytic /
+ * plv_normalize of the same handle for (batch, N, T), and its outputs
+ * (layouts as in plv_gram; NULL outputs are skipped). */
+typedef struct {
+    const void *P;
+    int batch, N, T;
+    float *plv, *iplv, *ciplv;
+    void *C;          /* complex64 [batch][N][N] */
+    double *diag;     /* [batch] */
+} plv_problem;
+
+typedef struct plv_group plv_group;
+
+/* Plan a grouped Gram over `nprob` problems of uneven N and T (Section IV:
+ * many subjects, epochs and frequency bands): uploads the problem
+ * descriptors and the list of every (problem, epoch, upper-triangle tile),
+ * sorted longest first (by T), to the device.  Allocates: call outside
+ * stream capture.  out_mask selects outputs as in plv_gram.  The pointers in
+ * `probs` are captured: the plan runs on those buffers. */
+plv_status plv_group_create(plv_handle *h, const plv_problem *probs, int nprob,
+                            unsigned out_mask, plv_group **group);
+
+/* Run a plan: Eq. 7, 13, 14 for every problem.  BF16X3 / FP16X3 handles run
+ * ONE persistent tensor-core launch over the whole tile list (CTAs take
+ * tiles round-robin, longest first); an FP32 handle runs one Gram launch per
+ * problem.  Allocates nothing: can be captured in a CUDA graph. */
+plv_status plv_gram_grouped(plv_handle *h, void *stream, const plv_group *group);
+
+/* Free a plan (synchronises the device).  NULL is ignored. */
+plv_status plv_group_destroy(plv_group *group);
 
 /* Eq. 7, 13, 14 applied elementwise to a stored C (complex64 interleaved,
  * [batch][N][N]); the same arithmetic as the fused epilogue, including the

@@ -176,6 +176,42 @@ class Handle:
                                          _ptr(gs[2]), _ptr(grad_x)), self.h)
         return grad_x
 
+    def plv_group_create(self, problems, plv=True, iplv=True, ciplv=True,
+                         C=False, diag=False):
+        """Plan a grouped Gram.  `problems`: list of dicts with keys P,
+        batch, N, T and output tensors (plv, iplv, ciplv, C, diag); missing
+        outputs are allocated here.  Returns a Group (keeps the tensors)."""
+        mask = ((PLV_OUT_PLV if plv else 0) | (PLV_OUT_IPLV if iplv else 0) |
+                (PLV_OUT_CIPLV if ciplv else 0) | (PLV_OUT_C if C else 0))
+        arr = (_lib.PlvProblem * len(problems))()
+        keep = []
+        for k, q in enumerate(problems):
+            B, N = q["batch"], q["N"]
+            for key, want, shape, dt in (("plv", plv, (B, N, N), torch.float32),
+                                         ("iplv", iplv, (B, N, N), torch.float32),
+                                         ("ciplv", ciplv, (B, N, N), torch.float32),
+                                         ("C", C, (B, N, N), torch.complex64),
+                                         ("diag", diag, (B,), torch.float64)):
+                if want and key not in q:
+                    q[key] = torch.empty(shape, dtype=dt, device=self.device)
+            arr[k] = _lib.PlvProblem(
+                q["P"].data_ptr(), B, N, q["T"],
+                q["plv"].data_ptr() if plv else None,
+                q["iplv"].data_ptr() if iplv else None,
+                q["ciplv"].data_ptr() if ciplv else None,
+                q["C"].data_ptr() if C else None,
+                q["diag"].data_ptr() if diag else None)
+            keep.append(q)
+        g = ctypes.c_void_p()
+        _lib.check(self.lib.plv_group_create(self.h, arr, len(problems), mask,
+                                             ctypes.byref(g)), self.h)
+        return Group(self, g, keep)
+
+    def plv_gram_grouped(self, group):
+        _lib.check(self.lib.plv_gram_grouped(self.h, _stream(self.device),
+                                             group.g), self.h)
+        return group.problems
+
     def plv_sync_status(self) -> int:
         v = ctypes.c_int(0)
         _lib.check(self.lib.plv_sync_status(self.h, _stream(self.device),
@@ -190,6 +226,26 @@ class Handle:
         P = self.plv_analytic(x, P)
         res = self.plv_gram(P, E, N, T, C=C, diag=diag, out=out)
         return res
+
+
+class Group:
+    """A grouped-Gram plan (plv_group) and the tensors it runs on."""
+
+    def __init__(self, handle, g, problems):
+        self.handle = handle
+        self.g = g
+        self.problems = problems
+
+    def close(self):
+        if getattr(self, "g", None):
+            self.handle.lib.plv_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _Connectivity(torch.autograd.Function):

@@ -57,6 +57,9 @@ SIGNATURES = {
                           _vp, _vp]),
     "plv_backward_noalloc": (_i, [_vp, _vp, _i, _i, _i, _i, _i64, _vp, _vp,
                                   _vp, _vp, _vp]),
+    "plv_group_create": (_i, [_vp, _vp, _i, _u, ctypes.POINTER(_vp)]),
+    "plv_gram_grouped": (_i, [_vp, _vp, _vp]),
+    "plv_group_destroy": (_i, [_vp]),
     "plv_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
 }
 
@@ -98,3 +101,12 @@ def check(status: int, handle=None):
     if status != PLV_OK:
         msg = load().plv_last_error(handle)
         raise PlvError(status, msg.decode() if msg else "")
+
+
+class PlvProblem(ctypes.Structure):
+    """Mirror of plv_problem (include/plv.h)."""
+    _fields_ = [("P", ctypes.c_void_p), ("batch", ctypes.c_int),
+                ("N", ctypes.c_int), ("T", ctypes.c_int),
+                ("plv", ctypes.c_void_p), ("iplv", ctypes.c_void_p),
+                ("ciplv", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("diag", ctypes.c_void_p)]

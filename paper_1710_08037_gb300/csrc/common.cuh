@@ -20,13 +20,35 @@ namespace plv {
 // Gram's K tile); the padding holds zeros.
 constexpr int kPadT = 32;
 
-inline int64_t padded_len(int T) {
+__host__ __device__ inline int64_t padded_len(int T) {
     return ((int64_t)T + kPadT - 1) / kPadT * kPadT;
+}
+
+// Split-precision operand layout (BF16X3 / FP16X3): blocks of 128 rows x 32
+// samples x 4 planes (Re_hi, Re_lo, Im_hi, Im_lo) of 16-bit values, 32 KB
+// each, contiguous and already in the tensor-core shared-memory layout
+// (K-major, 64-byte rows, 64-byte swizzle: the 16-byte chunk c of row r sits
+// at chunk c ^ ((r >> 1) & 3)).  Block (e, rb, kb) starts at
+// ((e * NRB + rb) * NKB + kb) * 32 KB with NRB = ceil(N / 128) row blocks and
+// NKB = ld / 32 sample blocks.  Rows N .. NRB*128-1 and samples T .. ld-1
+// are zero.
+constexpr int kTileRows = 128;
+constexpr int kTileK = 32;
+constexpr int kBlockElems = 4 * kTileRows * kTileK;  // 16-bit elements per block
+__host__ __device__ inline int64_t row_blocks(int N) { return ((int64_t)N + kTileRows - 1) / kTileRows; }
+
+__host__ __device__ inline int64_t split_offset(int64_t e, int64_t n, int64_t t, int64_t NRB,
+                                                int64_t NKB) {
+    const int64_t rb = n >> 7, r = n & 127, kb = t >> 5, k = t & 31;
+    const int64_t blk = (e * NRB + rb) * NKB + kb;
+    const int64_t kc = ((((k >> 3) ^ ((r >> 1) & 3)) << 3) | (k & 7));
+    return blk * kBlockElems + r * kTileK + kc;  // plane 0; plane p at + p * 4096
 }
 
 // Smallest and largest power-of-two lengths the shared-memory FFT handles.
 constexpr int kMinLog2T = 5;
-constexpr int kMaxLog2T = 14;
+constexpr int kMaxLog2T = 14;        // twiddle tables
+constexpr int kMaxLog2Direct = 13;   // lengths the two-buffer FFT kernel fits
 
 // Device status codes written by kernels into the handle's status word.
 enum : int { kDevOk = 0, kDevTimeout = 5 };
@@ -46,6 +68,34 @@ struct Handle {
     std::mutex mu;
 };
 
+// Per-kernel launch set-up done once per device (the shared-memory opt-in
+// and the occupancy query are not stream operations, and doing them once
+// keeps later launches free of them, e.g. inside a graph capture).
+struct LaunchSetup {
+    int per_sm[64] = {0};  // 0: not set up yet on that device
+};
+template <typename Kern>
+inline cudaError_t setup_once(LaunchSetup &ls, Kern kern, int threads, size_t smem,
+                              int &per_sm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (ls.per_sm[dev] == 0) {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        ls.per_sm[dev] = n > 0 ? n : 1;
+    }
+    per_sm = ls.per_sm[dev];
+    return cudaSuccess;
+}
+
 // Per-thread last error message.
 void set_error(const char *fmt, ...);
 plv_status fail(plv_status s, const char *fmt, ...);
@@ -61,6 +111,8 @@ inline const float2 *twiddle_table(const Handle *h, int log2T) {
 cudaError_t launch_analytic_pow2(const Handle *h, cudaStream_t s,
                                  const void *x, plv_dtype dt, int64_t rows,
                                  int N, int log2T, int64_t ldx, void *P);
+// Zero the padding rows N .. NRB*128-1 of a split-precision phasor buffer.
+cudaError_t launch_zero_pad_rows(cudaStream_t s, void *P, int batch, int N, int T);
 // Backward preparation: FP32 phasors P[rows][2][ld] and rinv[rows][ld].
 cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
                             int64_t rows, int log2T, int64_t ldx, float *P, float *rinv);
@@ -85,6 +137,21 @@ cudaError_t launch_gram_fp32(const Handle *h, cudaStream_t s, const float *P,
 // K3: split-precision tensor-core Gram + fused read-outs (BF16X3 / FP16X3).
 cudaError_t launch_gram_tc(const Handle *h, cudaStream_t s, const void *P,
                            int batch, int N, int T, GramOut out);
+// One problem of a grouped tensor-core launch (device descriptor): phasors
+// in the tiled split layout, sizes and outputs.
+struct TcProblem {
+    const uint8_t *P;
+    int batch, N, nrb, nkb, tpe;  // epochs, rows, row blocks, 32-sample blocks, tiles/epoch
+    float invT;
+    double invT_d;
+    GramOut out;
+};
+TcProblem make_tc_problem(const void *P, int batch, int N, int T, GramOut out);
+// One persistent launch over a list of (problem, epoch, I, J) tiles.
+cudaError_t launch_gram_tc_group(const Handle *h, cudaStream_t s, const TcProblem *probs,
+                                 const int4 *items, int nitems);
+// Zero the diagonal-check outputs of every problem of a group.
+cudaError_t launch_zero_group_diag(cudaStream_t s, const TcProblem *probs, int nprob);
 // K6: read-outs from a stored C.
 cudaError_t launch_metrics(cudaStream_t s, const float2 *C, int batch, int N,
                            float *plv, float *iplv, float *ciplv);

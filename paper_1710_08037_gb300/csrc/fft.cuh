@@ -303,16 +303,10 @@ cudaError_t launch_hilbert_pairs(int num_sms, cudaStream_t st, const Task &task,
                                  const float2 *tw, int64_t rows) {
     using C = K1Cfg<L>;
     auto kern = k_hilbert_pairs<L, Task>;
-    if (C::SMEM > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(
-            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-    }
+    static LaunchSetup ls;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS,
-                                                                  C::SMEM);
+    cudaError_t e = setup_once(ls, kern, C::THREADS, C::SMEM, per_sm);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     const int64_t pairs = (rows + 1) / 2;
     const int64_t nbatch = (pairs + C::SEQ - 1) / C::SEQ;
     if (nbatch == 0) return cudaSuccess;

@@ -18,7 +18,9 @@ __device__ __forceinline__ float ldx_f(const Tin *p) {
     return (float)__ldg(p);
 }
 
-// Store one unit phasor of row r at sample m in the operand layout.
+// Store one unit phasor of row r (= e * N + n) at sample m in the operand
+// layout: FP32 planar rows, or the tiled split layout (common.cuh) with the
+// component split as hi = RN(p), lo = RN(p - hi).
 template <int PREC>
 __device__ __forceinline__ void store_phasor(void *P, int64_t r, int N,
                                              int64_t ld, int m, float2 p) {
@@ -26,26 +28,52 @@ __device__ __forceinline__ void store_phasor(void *P, int64_t r, int N,
         float *o = (float *)P + r * 2 * ld + m;
         o[0] = p.x;
         o[ld] = p.y;
-    } else if constexpr (PREC == PLV_PREC_FP16X3) {
-        const int64_t e = r / N, n = r - e * N;
-        __half *o = (__half *)P + ((e * 4) * N + n) * ld + m;
-        const int64_t ps = (int64_t)N * ld;  // plane stride
-        const __half rh = __float2half_rn(p.x);
-        const __half ih = __float2half_rn(p.y);
-        o[0] = rh;
-        o[ps] = __float2half_rn(p.x - __half2float(rh));
-        o[2 * ps] = ih;
-        o[3 * ps] = __float2half_rn(p.y - __half2float(ih));
     } else {
         const int64_t e = r / N, n = r - e * N;
-        __nv_bfloat16 *o = (__nv_bfloat16 *)P + ((e * 4) * N + n) * ld + m;
-        const int64_t ps = (int64_t)N * ld;  // plane stride
-        const __nv_bfloat16 rh = __float2bfloat16_rn(p.x);
-        const __nv_bfloat16 ih = __float2bfloat16_rn(p.y);
-        o[0] = rh;
-        o[ps] = __float2bfloat16_rn(p.x - __bfloat162float(rh));
-        o[2 * ps] = ih;
-        o[3 * ps] = __float2bfloat16_rn(p.y - __bfloat162float(ih));
+        const int64_t off = split_offset(e, n, m, row_blocks(N), ld / kTileK);
+        constexpr int64_t ps = kTileRows * kTileK;  // plane stride in a block
+        if constexpr (PREC == PLV_PREC_FP16X3) {
+            __half *o = (__half *)P + off;
+            const __half rh = __float2half_rn(p.x);
+            const __half ih = __float2half_rn(p.y);
+            o[0] = rh;
+            o[ps] = __float2half_rn(p.x - __half2float(rh));
+            o[2 * ps] = ih;
+            o[3 * ps] = __float2half_rn(p.y - __half2float(ih));
+        } else {
+            __nv_bfloat16 *o = (__nv_bfloat16 *)P + off;
+            const __nv_bfloat16 rh = __float2bfloat16_rn(p.x);
+            const __nv_bfloat16 ih = __float2bfloat16_rn(p.y);
+            o[0] = rh;
+            o[ps] = __float2bfloat16_rn(p.x - __bfloat162float(rh));
+            o[2 * ps] = ih;
+            o[3 * ps] = __float2bfloat16_rn(p.y - __bfloat162float(ih));
+        }
+    }
+}
+
+// Zero the rows N .. NRB*128-1 of every epoch's last row block, all planes
+// and samples: one thread per 16-byte chunk.
+__global__ void k_zero_pad_rows(uint4 *P, int batch, int N, int64_t NRB, int64_t NKB) {
+    const int pad0 = N & 127;  // first padding row inside the last block
+    const int npad = 128 - pad0;
+    const int64_t chunks_per_row = kTileK * 2 / 16;  // 4 chunks of 16 bytes
+    const int64_t per_block = 4 * (int64_t)npad * chunks_per_row;
+    const int64_t total = (int64_t)batch * NKB * per_block;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = q % chunks_per_row;
+        int64_t rest = q / chunks_per_row;
+        const int64_t rr = rest % npad;
+        rest /= npad;
+        const int64_t plane = rest % 4;
+        rest /= 4;
+        const int64_t kb = rest % NKB;
+        const int64_t e = rest / NKB;
+        const int64_t blk = (e * NRB + (NRB - 1)) * NKB + kb;
+        const int64_t el = blk * kBlockElems + plane * (kTileRows * kTileK) +
+                           (pad0 + rr) * kTileK + c * 8;
+        P[el / 8] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -122,6 +150,16 @@ __global__ void k_normalize(const Tc *__restrict__ z, int64_t rows, int N,
 }
 
 }  // namespace
+
+cudaError_t launch_zero_pad_rows(cudaStream_t s, void *P, int batch, int N, int T) {
+    if ((N & 127) == 0 || batch == 0) return cudaSuccess;
+    const int64_t NKB = padded_len(T) / kTileK;
+    const int64_t total = (int64_t)batch * NKB * 4 * (128 - (N & 127)) * 4;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_zero_pad_rows<<<(unsigned)blocks, 256, 0, s>>>((uint4 *)P, batch, N, row_blocks(N), NKB);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
                             int64_t rows, int log2T, int64_t ldx, float *P, float *rinv) {

@@ -20,9 +20,10 @@
 // in registers (round to nearest), as a two-level summation.
 //
 // Kernel structure (one CTA per SM, persistent over the tile list):
-//   warp 0      TMA producer: per stage, one 3-D box {32 samples, 128 rows,
-//               4 planes} per operand side (64-byte swizzle) into a
-//               3-stage shared-memory ring;
+//   warp 0      producer: per stage, one 32 KB bulk copy (cp.async.bulk)
+//               per operand side -- the operand layout stores each block of
+//               128 rows x 32 samples x 4 planes contiguously and already
+//               64-byte swizzled -- into a 3-stage shared-memory ring;
 //   warp 1      TMEM allocator and MMA issuer (one thread): tcgen05.mma
 //               128x128x16, two TMEM regions of [128 Re + 128 Im] FP32
 //               columns (512 columns) alternating per K chunk;
@@ -34,11 +35,14 @@
 // Only tiles (I, J) with I <= J of each epoch are computed; on a diagonal
 // tile the B operand is the A operand already in shared memory.
 //
+// Work list.  A launch covers one problem (every epoch's upper-triangle
+// tiles, enumerated in the kernel) or a group of problems of different N
+// and T (an explicit list of (problem, epoch, I, J) items, longest first).
+// CTAs take items round-robin; all three roles walk the same sequence.
+//
 // Every wait on an mbarrier is bounded in time; on expiry the CTA records
 // PLV_ERR_TIMEOUT in the device status word, stops issuing work, lets the
 // copies and MMAs it issued land, frees its TMEM and returns.
-#include <cuda.h>
-
 #include "epilogue.cuh"
 
 namespace plv {
@@ -115,13 +119,14 @@ __device__ __noinline__ bool wait_bar(uint32_t bar, uint32_t parity,
     }
 }
 
-// ---- TMA ----------------------------------------------------------------------
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map,
-                                            uint32_t bar, int x, int y, int z) {
+// ---- bulk copy ---------------------------------------------------------------
+// 1-D bulk copy global -> shared, completion counted on an mbarrier (16-byte
+// aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"((uint64_t)src), "r"(bytes), "r"(bar)
         : "memory");
 }
 
@@ -202,19 +207,30 @@ __device__ __forceinline__ void tile_of(int t, int &I, int &J) {
 }
 
 struct TcArgs {
-    int N;
-    int nkb;              // K blocks of 32 samples
-    int tiles_per_epoch;  // nt (nt + 1) / 2
-    int total_tiles;
-    float invT;
-    double invT_d;
-    GramOut out;
+    TcProblem single;         // the problem when items == nullptr
+    const TcProblem *probs;   // group: problem descriptors
+    const int4 *items;        // group: (problem, epoch, I, J), longest first
+    int total_items;
     int *status;
 };
 
+__device__ __forceinline__ const TcProblem &item_of(const TcArgs &a, int t, int &e, int &I,
+                                                    int &J) {
+    if (a.items) {
+        const int4 it = a.items[t];
+        e = it.y;
+        I = it.z;
+        J = it.w;
+        return a.probs[it.x];
+    }
+    e = t / a.single.tpe;
+    tile_of(t - e * a.single.tpe, I, J);
+    return a.single;
+}
+
 template <uint32_t FMT>
 __global__ void __launch_bounds__(NTHREADS, 1)
-k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
+k_gram_tc(const __grid_constant__ TcArgs args) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // stages, 1024-aligned
@@ -243,7 +259,6 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmap) : "memory");
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
@@ -254,7 +269,6 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int tpe = args.tiles_per_epoch;
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
@@ -262,19 +276,20 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
             uint32_t phase = 0;
             uint32_t pending = 0;        // stages with a copy issued
             uint32_t pend_parity = 0;    // FULL parity each pending copy completes
-            for (int t = blockIdx.x; t < args.total_tiles && !*abort_flag; t += gridDim.x) {
-                const int e = t / tpe;
-                int I, J;
-                tile_of(t - e * tpe, I, J);
+            for (int t = blockIdx.x; t < args.total_items && !*abort_flag; t += gridDim.x) {
+                int e, I, J;
+                const TcProblem &pb = item_of(args, t, e, I, J);
                 const bool diag = I == J;
-                for (int kb = 0; kb < args.nkb; ++kb) {
+                const uint8_t *pa = pb.P + (size_t)((int64_t)e * pb.nrb + I) * pb.nkb * SIDE_BYTES;
+                const uint8_t *pj = pb.P + (size_t)((int64_t)e * pb.nrb + J) * pb.nkb * SIDE_BYTES;
+                for (int kb = 0; kb < pb.nkb; ++kb) {
                     if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status)) break;
                     const uint32_t sa = base + stage * STAGE_BYTES;
                     mbar_expect_tx(FULL(stage), diag ? SIDE_BYTES : 2 * SIDE_BYTES);
-                    tma_load_3d(sa, &tmap, FULL(stage), kb * KB, I * TM, 4 * e);
+                    bulk_g2s(sa, pa + (size_t)kb * SIDE_BYTES, SIDE_BYTES, FULL(stage));
                     if (!diag)
-                        tma_load_3d(sa + SIDE_BYTES, &tmap, FULL(stage), kb * KB, J * TN,
-                                    4 * e);
+                        bulk_g2s(sa + SIDE_BYTES, pj + (size_t)kb * SIDE_BYTES, SIDE_BYTES,
+                                 FULL(stage));
                     pending |= 1u << stage;
                     pend_parity = (pend_parity & ~(1u << stage)) | (phase << stage);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
@@ -303,13 +318,13 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
             bool issued = false;
             uint32_t last_bar = 0, last_parity = 0;
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < args.total_tiles && !*abort_flag;
+            for (int t = blockIdx.x; ok && t < args.total_items && !*abort_flag;
                  t += gridDim.x) {
-                const int e = t / tpe;
-                int I, J;
-                tile_of(t - e * tpe, I, J);
+                int e, I, J;
+                const TcProblem &pb = item_of(args, t, e, I, J);
                 const bool diag = I == J;
-                for (int kb0 = 0; ok && kb0 < args.nkb; kb0 += CH) {
+                const int nkb = pb.nkb;
+                for (int kb0 = 0; ok && kb0 < nkb; kb0 += CH) {
                     if (!wait_bar(TEMPTY(buf), buf_phase ^ 1u, abort_flag, args.status)) {
                         ok = false;
                         break;
@@ -317,7 +332,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
                     tc_fence_after();
                     const uint32_t d_re = tmem + buf * ACC_COLS;
                     const uint32_t d_im = d_re + TN;
-                    const int kb1 = kb0 + CH < args.nkb ? kb0 + CH : args.nkb;
+                    const int kb1 = kb0 + CH < nkb ? kb0 + CH : nkb;
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!wait_bar(FULL(stage), phase, abort_flag, args.status)) {
                             ok = false;
@@ -379,16 +394,15 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
         const int row = q * 32 + lane;         // tile row owned by this thread
         int buf = 0;
         uint32_t buf_phase = 0;
-        const int N = args.N;
         bool ok = true;
-        for (int t = blockIdx.x; ok && t < args.total_tiles; t += gridDim.x) {
-            const int e = t / tpe;
-            int I, J;
-            tile_of(t - e * tpe, I, J);
+        for (int t = blockIdx.x; ok && t < args.total_items; t += gridDim.x) {
+            int e, I, J;
+            const TcProblem &pb = item_of(args, t, e, I, J);
+            const int N = pb.N;
             float sre[32], sim[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
-            for (int kb0 = 0; kb0 < args.nkb; kb0 += CH) {
+            for (int kb0 = 0; kb0 < pb.nkb; kb0 += CH) {
                 if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status)) {
                     ok = false;
                     break;
@@ -415,9 +429,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
             if (!ok) break;
             const int i = I * TM + row;
             const int j0 = J * TN + cq * 32;
-            store_tile_row(args.out, (int64_t)e * N * N, N, i, j0, I == J, sre, sim,
-                           args.invT, args.invT_d, args.out.diag ? args.out.diag + e
-                                                                 : nullptr);
+            store_tile_row(pb.out, (int64_t)e * N * N, N, i, j0, I == J, sre, sim, pb.invT,
+                           pb.invT_d, pb.out.diag ? pb.out.diag + e : nullptr);
         }
     }
 
@@ -430,64 +443,71 @@ k_gram_tc(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
     }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                  CUtensorMapFloatOOBfill);
+}  // namespace
 
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    });
-    return fn;
+TcProblem make_tc_problem(const void *P, int batch, int N, int T, GramOut out) {
+    TcProblem p;
+    p.P = (const uint8_t *)P;
+    p.batch = batch;
+    p.N = N;
+    p.nrb = (int)row_blocks(N);
+    p.nkb = (int)(padded_len(T) / KB);
+    p.tpe = p.nrb * (p.nrb + 1) / 2;
+    p.invT = 1.0f / (float)T;
+    p.invT_d = 1.0 / (double)T;
+    p.out = out;
+    return p;
 }
 
-}  // namespace
+static cudaError_t launch_tc(const Handle *h, cudaStream_t s, const TcArgs &a) {
+    if (a.total_items <= 0) return cudaSuccess;
+    const int grid = a.total_items < h->num_sms ? a.total_items : h->num_sms;
+    const bool fp16 = h->prec == PLV_PREC_FP16X3;
+    auto kern = fp16 ? k_gram_tc<0u> : k_gram_tc<1u>;
+    static LaunchSetup ls16, ls_bf;
+    int per_sm = 0;
+    cudaError_t e = setup_once(fp16 ? ls16 : ls_bf, kern, NTHREADS, SMEM_BYTES, per_sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gram_tc(const Handle *h, cudaStream_t s, const void *P, int batch,
                            int N, int T, GramOut out) {
-    const int64_t ld = padded_len(T);
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
-    CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)N, (cuuint64_t)4 * batch};
-    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)N * ld * 2};
-    const cuuint32_t box[3] = {KB, TM, 4};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const bool fp16 = h->prec == PLV_PREC_FP16X3;
-    CUresult r = enc(&map,
-                     fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                     3, const_cast<void *>(P), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    const int nt = (N + TM - 1) / TM;
     TcArgs a;
-    a.N = N;
-    a.nkb = (int)(ld / KB);
-    a.tiles_per_epoch = nt * (nt + 1) / 2;
-    const int64_t total = (int64_t)a.tiles_per_epoch * batch;
+    a.single = make_tc_problem(P, batch, N, T, out);
+    a.probs = nullptr;
+    a.items = nullptr;
+    const int64_t total = (int64_t)a.single.tpe * batch;
     if (total > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    a.total_tiles = (int)total;
-    a.invT = 1.0f / (float)T;
-    a.invT_d = 1.0 / (double)T;
-    a.out = out;
+    a.total_items = (int)total;
     a.status = h->status;
-    const int grid = (int)(total < h->num_sms ? total : h->num_sms);
-    auto kern = fp16 ? k_gram_tc<0u> : k_gram_tc<1u>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, NTHREADS, SMEM_BYTES, s>>>(map, a);
+    return launch_tc(h, s, a);
+}
+
+static __global__ void k_zero_group_diag(const TcProblem *probs, int nprob) {
+    for (int p = blockIdx.x; p < nprob; p += gridDim.x) {
+        double *d = probs[p].out.diag;
+        if (!d) continue;
+        for (int e = threadIdx.x; e < probs[p].batch; e += blockDim.x) d[e] = 0.0;
+    }
+}
+
+cudaError_t launch_zero_group_diag(cudaStream_t s, const TcProblem *probs, int nprob) {
+    if (nprob <= 0) return cudaSuccess;
+    k_zero_group_diag<<<nprob < 1024 ? nprob : 1024, 128, 0, s>>>(probs, nprob);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc_group(const Handle *h, cudaStream_t s, const TcProblem *probs,
+                                 const int4 *items, int nitems) {
+    TcArgs a;
+    a.single = TcProblem{};
+    a.probs = probs;
+    a.items = items;
+    a.total_items = nitems;
+    a.status = h->status;
+    return launch_tc(h, s, a);
 }
 
 }  // namespace plv

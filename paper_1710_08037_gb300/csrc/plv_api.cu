@@ -4,6 +4,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -180,19 +181,21 @@ plv_precision plv_get_precision(const plv_handle *hp) {
 
 int64_t plv_phasor_ld(int T) { return T > 0 ? padded_len(T) : 0; }
 
-size_t plv_phasor_bytes(const plv_handle *, int batch, int N, int T) {
+size_t plv_phasor_bytes(const plv_handle *hp, int batch, int N, int T) {
     if (batch < 0 || N < 0 || T <= 0) return 0;
-    return (size_t)batch * (size_t)N * (size_t)padded_len(T) * 8u;
+    const bool split = hp && hp->h.prec != PLV_PREC_FP32;
+    const size_t rows = split ? (size_t)row_blocks(N) * kTileRows : (size_t)N;
+    return (size_t)batch * rows * (size_t)padded_len(T) * 8u;
 }
 
 plv_status plv_prepare(plv_handle *hp, int T) {
     if (!hp) return fail(PLV_ERR_INVALID, "plv_prepare: handle is NULL");
     if (T <= 0) return fail(PLV_ERR_INVALID, "plv_prepare: T = %d", T);
     const int L = log2_exact(T);
-    if (L < kMinLog2T || L > kMaxLog2T)
+    if (L < kMinLog2T || L > kMaxLog2Direct)
         return fail(PLV_ERR_UNSUPPORTED,
                     "plv_prepare: T = %d (this build's FFT takes powers of two "
-                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2T);
+                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2Direct);
     return PLV_OK;  // power-of-two tables are made by plv_create
 }
 
@@ -208,16 +211,21 @@ plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
     if (batch == 0 || N == 0) return PLV_OK;
     if (!x || !P) return fail(PLV_ERR_INVALID, "plv_analytic: NULL data pointer");
     const int L = log2_exact(T);
-    if (L < kMinLog2T || L > kMaxLog2T)
+    if (L < kMinLog2T || L > kMaxLog2Direct)
         return fail(PLV_ERR_UNSUPPORTED,
                     "plv_analytic: T = %d (this build's FFT takes powers of two "
-                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2T);
+                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2Direct);
     const size_t esz = dtype == PLV_F32 ? 4 : 8;
     if (((uintptr_t)x % esz) != 0)
         return fail(PLV_ERR_INVALID, "plv_analytic: x is not %zu-byte aligned", esz);
     if (((uintptr_t)P % 16) != 0)
         return fail(PLV_ERR_INVALID, "plv_analytic: P is not 16-byte aligned");
     PLV_GUARD(&hp->h);
+    if (hp->h.prec != PLV_PREC_FP32) {
+        plv_status st = check_cuda(launch_zero_pad_rows((cudaStream_t)stream, P, batch, N, T),
+                                   "plv_analytic: pad rows");
+        if (st != PLV_OK) return st;
+    }
     return check_cuda(launch_analytic_pow2(&hp->h, (cudaStream_t)stream, x, dtype,
                                            (int64_t)batch * N, N, L, ldx, P),
                       "plv_analytic launch");
@@ -237,6 +245,11 @@ plv_status plv_normalize(plv_handle *hp, void *stream, const void *z,
     if (((uintptr_t)z % (dtype == PLV_F32 ? 8 : 16)) != 0 || ((uintptr_t)P % 16) != 0)
         return fail(PLV_ERR_INVALID, "plv_normalize: misaligned pointer");
     PLV_GUARD(&hp->h);
+    if (hp->h.prec != PLV_PREC_FP32) {
+        plv_status st = check_cuda(launch_zero_pad_rows((cudaStream_t)stream, P, batch, N, T),
+                                   "plv_normalize: pad rows");
+        if (st != PLV_OK) return st;
+    }
     return check_cuda(launch_normalize(&hp->h, (cudaStream_t)stream, z, dtype,
                                        (int64_t)batch * N, N, T, ldz, P),
                       "plv_normalize launch");
@@ -280,6 +293,143 @@ plv_status plv_gram(plv_handle *hp, void *stream, const void *P, int batch,
     return check_cuda(launch_gram_tc(&hp->h, s, P, batch, N, T, o), "plv_gram launch");
 }
 
+}  // extern "C"
+
+struct plv_group {
+    int device = 0;
+    plv_precision prec = PLV_PREC_FP32;
+    std::vector<plv_problem> host;   // validated problems (FP32 path)
+    unsigned mask = 0;
+    plv::TcProblem *probs = nullptr;  // device descriptors (split paths)
+    int4 *items = nullptr;            // device tile list, longest first
+    int nprob = 0, nitems = 0;
+    bool any_diag = false;
+};
+
+extern "C" {
+
+plv_status plv_group_create(plv_handle *hp, const plv_problem *probs, int nprob,
+                            unsigned out_mask, plv_group **out) {
+    if (!hp || !out) return fail(PLV_ERR_INVALID, "plv_group_create: NULL argument");
+    *out = nullptr;
+    if (nprob < 0 || (nprob > 0 && !probs))
+        return fail(PLV_ERR_INVALID, "plv_group_create: bad problem list");
+    if (out_mask & ~15u) return fail(PLV_ERR_INVALID, "plv_group_create: unknown output bits");
+    Handle &h = hp->h;
+    plv_group *g = new (std::nothrow) plv_group();
+    if (!g) return fail(PLV_ERR_ALLOC, "plv_group_create: out of host memory");
+    g->device = h.device;
+    g->prec = h.prec;
+    g->mask = out_mask;
+    std::vector<TcProblem> dp;
+    std::vector<int4> items;
+    for (int p = 0; p < nprob; ++p) {
+        plv_problem q = probs[p];
+        if (q.batch < 0 || q.N < 0 || q.T <= 0) {
+            delete g;
+            return fail(PLV_ERR_INVALID, "plv_group_create: problem %d has bad sizes", p);
+        }
+        if (q.batch == 0 || q.N == 0) continue;
+        if (!q.P || ((uintptr_t)q.P % 16) != 0) {
+            delete g;
+            return fail(PLV_ERR_INVALID, "plv_group_create: problem %d phasors NULL or misaligned", p);
+        }
+        if (!(out_mask & PLV_OUT_PLV)) q.plv = nullptr;
+        if (!(out_mask & PLV_OUT_IPLV)) q.iplv = nullptr;
+        if (!(out_mask & PLV_OUT_CIPLV)) q.ciplv = nullptr;
+        if (!(out_mask & PLV_OUT_C)) q.C = nullptr;
+        if ((q.C && ((uintptr_t)q.C % 8)) || (q.plv && ((uintptr_t)q.plv % 4)) ||
+            (q.iplv && ((uintptr_t)q.iplv % 4)) || (q.ciplv && ((uintptr_t)q.ciplv % 4))) {
+            delete g;
+            return fail(PLV_ERR_INVALID, "plv_group_create: problem %d output misaligned", p);
+        }
+        if (q.diag) g->any_diag = true;
+        g->host.push_back(q);
+        GramOut o;
+        o.plv = q.plv;
+        o.iplv = q.iplv;
+        o.ciplv = q.ciplv;
+        o.C = (float2 *)q.C;
+        o.diag = q.diag;
+        o.vec_ok = (q.N % 4 == 0) && !((uintptr_t)o.plv % 16) && !((uintptr_t)o.iplv % 16) &&
+                   !((uintptr_t)o.ciplv % 16) && !((uintptr_t)o.C % 16);
+        const TcProblem tp = make_tc_problem(q.P, q.batch, q.N, q.T, o);
+        const int pid = (int)dp.size();
+        dp.push_back(tp);
+        for (int e = 0; e < q.batch; ++e)
+            for (int J = 0; J < tp.nrb; ++J)
+                for (int I = 0; I <= J; ++I) items.push_back(make_int4(pid, e, I, J));
+    }
+    if (items.size() > 0x7fffffffu) {
+        delete g;
+        return fail(PLV_ERR_UNSUPPORTED, "plv_group_create: too many tiles");
+    }
+    // longest first: a tile's cost is proportional to its K blocks
+    std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
+        return dp[a.x].nkb > dp[b.x].nkb;
+    });
+    g->nprob = (int)dp.size();
+    g->nitems = (int)items.size();
+    if (h.prec != PLV_PREC_FP32 && g->nprob > 0) {
+        DeviceGuard guard(h.device);
+        plv_status st = check_cuda(cudaMalloc(&g->probs, sizeof(TcProblem) * dp.size()),
+                                   "plv_group_create: descriptors");
+        if (st == PLV_OK)
+            st = check_cuda(cudaMalloc(&g->items, sizeof(int4) * items.size()),
+                            "plv_group_create: tile list");
+        if (st == PLV_OK)
+            st = check_cuda(cudaMemcpy(g->probs, dp.data(), sizeof(TcProblem) * dp.size(),
+                                       cudaMemcpyHostToDevice),
+                            "plv_group_create: upload descriptors");
+        if (st == PLV_OK)
+            st = check_cuda(cudaMemcpy(g->items, items.data(), sizeof(int4) * items.size(),
+                                       cudaMemcpyHostToDevice),
+                            "plv_group_create: upload tiles");
+        if (st != PLV_OK) {
+            plv_group_destroy(g);
+            return st;
+        }
+    }
+    *out = g;
+    return PLV_OK;
+}
+
+plv_status plv_gram_grouped(plv_handle *hp, void *stream, const plv_group *g) {
+    if (!hp || !g) return fail(PLV_ERR_INVALID, "plv_gram_grouped: NULL argument");
+    if (g->device != hp->h.device || g->prec != hp->h.prec)
+        return fail(PLV_ERR_INVALID, "plv_gram_grouped: plan made for another device or precision");
+    PLV_GUARD(&hp->h);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (hp->h.prec == PLV_PREC_FP32) {
+        for (const plv_problem &q : g->host) {
+            plv_status st = plv_gram(hp, stream, q.P, q.batch, q.N, q.T, g->mask, q.plv, q.iplv,
+                                     q.ciplv, q.C, q.diag);
+            if (st != PLV_OK) return st;
+        }
+        return PLV_OK;
+    }
+    if (g->nitems == 0) return PLV_OK;
+    if (g->any_diag) {
+        plv_status st = check_cuda(launch_zero_group_diag(s, g->probs, g->nprob),
+                                   "plv_gram_grouped: clear diag");
+        if (st != PLV_OK) return st;
+    }
+    return check_cuda(launch_gram_tc_group(&hp->h, s, g->probs, g->items, g->nitems),
+                      "plv_gram_grouped launch");
+}
+
+plv_status plv_group_destroy(plv_group *g) {
+    if (!g) return PLV_OK;
+    {
+        DeviceGuard guard(g->device);
+        if (g->probs || g->items) cudaDeviceSynchronize();
+        if (g->probs) cudaFree(g->probs);
+        if (g->items) cudaFree(g->items);
+    }
+    delete g;
+    return PLV_OK;
+}
+
 plv_status plv_metrics(plv_handle *hp, void *stream, const void *C, int batch,
                        int N, float *plv, float *iplv, float *ciplv) {
     if (!hp) return fail(PLV_ERR_INVALID, "plv_metrics: handle is NULL");
@@ -306,10 +456,10 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
     if (batch == 0 || N == 0) return PLV_OK;
     if (!grad_x) return fail(PLV_ERR_INVALID, "plv_backward: grad_x is NULL");
     const int L = log2_exact(T);
-    if (L < kMinLog2T || L > kMaxLog2T)
+    if (L < kMinLog2T || L > kMaxLog2Direct)
         return fail(PLV_ERR_UNSUPPORTED,
                     "plv_backward: T = %d (this build's FFT takes powers of two "
-                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2T);
+                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2Direct);
     PLV_GUARD(&hp->h);
     Handle &h = hp->h;
     cudaStream_t s = (cudaStream_t)stream;

@@ -105,10 +105,10 @@ extern "C" plv_status plv_backward_noalloc(void *stream, const void *x, plv_dtyp
     if ((T & (T - 1)) == 0)
         for (L = 0; (1 << L) < T; ++L) {
         }
-    if (L < kMinLog2T || L > kMaxLog2T)
+    if (L < kMinLog2T || L > kMaxLog2Direct)
         return fail(PLV_ERR_UNSUPPORTED,
                     "plv_backward_noalloc: T = %d (powers of two from %d to %d)", T,
-                    1 << kMinLog2T, 1 << kMaxLog2T);
+                    1 << kMinLog2T, 1 << kMaxLog2Direct);
     const size_t need = noalloc_scratch_bytes(batch, N, T);
     if (need > (size_t)PLV_NOALLOC_SCRATCH_BYTES)
         return fail(PLV_ERR_INVALID,

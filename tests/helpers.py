@@ -20,11 +20,19 @@ def unpack_phasors(P, precision, B, N, T):
     if precision == "fp32":
         a = P[: B * N * 2 * ld].view(B, N, 2, ld).double().cpu().numpy()
         return a[:, :, 0, :T] + 1j * a[:, :, 1, :T]
+    # tiled split layout: blocks [B][NRB][NKB][4 planes][128 rows][32], the
+    # 16-byte chunk c of row r stored at chunk c ^ ((r >> 1) & 3)
     dt = torch.bfloat16 if precision == "bf16x3" else torch.float16
-    b = P.view(dt)[: B * 4 * N * ld].view(B, 4, N, ld)
-    b = b.double().cpu().numpy()
-    return (b[:, 0, :, :T] + b[:, 1, :, :T]) + 1j * (b[:, 2, :, :T] +
-                                                     b[:, 3, :, :T])
+    nrb, nkb = (N + 127) // 128, ld // 32
+    b = P.view(dt)[: B * nrb * nkb * 4 * 128 * 32].double().cpu().numpy()
+    b = b.reshape(B, nrb, nkb, 4, 128, 4, 8)
+    r = np.arange(128)
+    chunk = np.arange(4)
+    src = chunk[None, :] ^ ((r[:, None] >> 1) & 3)          # (128, 4)
+    b = b[:, :, :, :, r[:, None], src, :]                   # unswizzle
+    b = b.transpose(0, 3, 1, 4, 2, 5, 6).reshape(B, 4, nrb * 128, ld)
+    b = b[:, :, :N, :T]
+    return (b[:, 0] + b[:, 1]) + 1j * (b[:, 2] + b[:, 3])
 
 
 def ciplv_bound(c, eps):
