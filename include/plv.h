@@ -110,9 +110,11 @@ int64_t plv_phasor_ld(int T);
  * Returns 0 for invalid sizes. */
 size_t plv_phasor_bytes(const plv_handle *h, int batch, int N, int T);
 
-/* Make the handle's per-length tables for T samples (twiddles).  The first
- * plv_analytic / plv_backward call for a new T does this implicitly; call it
- * beforehand when those calls are to be captured in a CUDA graph. */
+/* Make the handle's per-length tables for T samples: for lengths outside the
+ * direct FFT, the any-length transform's twiddles and Hilbert-kernel
+ * spectrum (allocates).  The first plv_analytic call for a new T does this
+ * implicitly; call it beforehand when that call is to be captured in a CUDA
+ * graph. */
 plv_status plv_prepare(plv_handle *h, int T);
 
 /* Eq. 3 + Eq. 4, fused (Section II.A): analytic signal of every row of x by
@@ -122,7 +124,11 @@ plv_status plv_prepare(plv_handle *h, int T);
  *          converted to FP32 on load; the arithmetic is FP32).
  *   P    : plv_phasor_bytes(h, batch, N, T) bytes, written completely
  *          (including zero padding).
- * Supported T: powers of two, 32 <= T <= 8192 (others: PLV_ERR_UNSUPPORTED).
+ * Supported T: 2 <= T <= 12288.  Powers of two from 32 to 8192 take the
+ * direct radix-16 FFT of length T; every other length takes the circular
+ * convolution with the periodic Hilbert kernel through an FFT of length
+ * M >= 2T - 1 (M = 2^a or 3 * 2^a), whose tables are made on first use of a
+ * T (allocates; see plv_prepare).  Others: PLV_ERR_UNSUPPORTED.
  * batch = 0 or N = 0 is a no-op. */
 plv_status plv_analytic(plv_handle *h, void *stream, const void *x,
                         plv_dtype dtype, int batch, int N, int T, int64_t ldx,

@@ -53,6 +53,18 @@ constexpr int kMaxLog2Direct = 13;   // lengths the two-buffer FFT kernel fits
 // Device status codes written by kernels into the handle's status word.
 enum : int { kDevOk = 0, kDevTimeout = 5 };
 
+// Plan of the any-length Hilbert transform (fft.cuh): FFT length M and its
+// decimation-in-frequency radix order, twiddles exp(-2 pi i m / M), and the
+// Hilbert kernel's spectrum factor S / M in that transform's output order.
+struct ConvPlan {
+    int M;
+    int nstages;
+    int radix[8];
+    const float2 *tw;
+    const float *S;
+};
+constexpr int kMaxConvM = 24576;  // 3 * 2^13: T up to 12288
+
 struct Handle {
     int device = 0;
     plv_precision prec = PLV_PREC_FP32;
@@ -65,6 +77,9 @@ struct Handle {
     int *status = nullptr;  // device status word
     void *ws = nullptr;     // scratch for the backward pass (grows on demand)
     size_t ws_bytes = 0;
+    std::map<int, ConvPlan> conv;      // by T (lengths that are not handled directly)
+    std::map<int, float2 *> conv_tw;   // twiddle tables by M
+    std::map<int, float *> conv_S;     // kernel spectra by T
     std::mutex mu;
 };
 
@@ -95,6 +110,14 @@ inline cudaError_t setup_once(LaunchSetup &ls, Kern kern, int threads, size_t sm
     per_sm = ls.per_sm[dev];
     return cudaSuccess;
 }
+
+// The any-length plan for T (built and cached on first use: allocates).
+plv_status get_conv_plan(Handle &h, int T, const ConvPlan **plan);
+void free_conv_plans(Handle &h);
+// K1 for lengths the direct FFT does not take (any T up to kMaxConvM / 2).
+cudaError_t launch_analytic_conv(const Handle *h, cudaStream_t s, const void *x,
+                                 plv_dtype dt, int64_t rows, int N, int T, int64_t ldx,
+                                 void *P, const ConvPlan &plan);
 
 // Per-thread last error message.
 void set_error(const char *fmt, ...);

@@ -1,0 +1,140 @@
+// conv_plan.cu -- host side of the any-length Hilbert transform: choice of
+// the FFT length M >= 2T - 1 (2^a or 3 * 2^a), its radix order, and the
+// spectrum of the periodic discrete Hilbert kernel, computed in FP64 with the
+// same in-place decimation-in-frequency algorithm the device runs, so it
+// lands in the device's output order.  Tables are cached per handle.
+#include <math.h>
+
+#include <complex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace plv {
+namespace {
+
+typedef std::complex<double> cd;
+
+int choose_M(int T) {
+    const int need = 2 * T - 1;
+    int best = 0;
+    for (int p = 32; p <= kMaxConvM; p *= 2) {
+        if (p >= need && (best == 0 || p < best)) best = p;
+        if (3 * p >= need && 3 * p <= kMaxConvM && (best == 0 || 3 * p < best)) best = 3 * p;
+    }
+    return best;
+}
+
+// radix order: 3 first for 3 * 2^a, then 16s, then the remaining power of two
+std::vector<int> schedule(int M) {
+    std::vector<int> r;
+    int m = M;
+    if (m % 3 == 0) {
+        r.push_back(3);
+        m /= 3;
+    }
+    int a = 0;
+    while ((1 << a) < m) ++a;
+    for (int k = 0; k < a / 4; ++k) r.push_back(16);
+    if (a % 4) r.push_back(1 << (a % 4));
+    return r;
+}
+
+// In-place decimation-in-frequency FFT with the device's loop structure.
+void host_dif(std::vector<cd> &x, int M, const std::vector<int> &radix) {
+    int span = M;
+    std::vector<cd> v(16), V(16);
+    for (int R : radix) {
+        const int sub = span / R;
+        for (int b = 0; b < M / R; ++b) {
+            const int g = b / sub, j = b - g * sub;
+            const int base = g * span + j;
+            for (int r = 0; r < R; ++r) v[r] = x[base + r * sub];
+            for (int q = 0; q < R; ++q) {
+                cd acc = 0.0;
+                for (int r = 0; r < R; ++r)
+                    acc += v[r] * std::polar(1.0, -2.0 * M_PI * (double)(r * q % R) / R);
+                V[q] = acc * std::polar(1.0, -2.0 * M_PI * (double)q * j / span);
+            }
+            for (int q = 0; q < R; ++q) x[base + q * sub] = V[q];
+        }
+        span = sub;
+    }
+}
+
+}  // namespace
+
+plv_status get_conv_plan(Handle &h, int T, const ConvPlan **out) {
+    auto it = h.conv.find(T);
+    if (it != h.conv.end()) {
+        *out = &it->second;
+        return PLV_OK;
+    }
+    const int M = choose_M(T);
+    if (M == 0 || T < 2)
+        return fail(PLV_ERR_UNSUPPORTED, "T = %d: lengths up to %d are supported", T,
+                    kMaxConvM / 2);
+    const std::vector<int> radix = schedule(M);
+    // periodic Hilbert kernel k_T[n] = (2/T) sum_{k=1}^{K} sin(2 pi k n / T),
+    // K = ceil(T/2) - 1, summed in closed form
+    const int K = (T + 1) / 2 - 1;
+    std::vector<double> kt(T, 0.0);
+    for (int n = 1; n < T; ++n) {
+        const double th = 2.0 * M_PI * n / T;
+        const double den = sin(th / 2.0);
+        kt[n] = (2.0 / T) * sin(K * th / 2.0) * sin((K + 1) * th / 2.0) / den;
+    }
+    std::vector<cd> kc(M, 0.0);
+    for (int m = 0; m < T; ++m) kc[m] = kt[m];
+    for (int j = 1; j < T; ++j) kc[M - j] = kt[T - j];
+    host_dif(kc, M, radix);
+    // K = FFT(k) is imaginary: K = -i S, S = -Im K; fold in 1/M
+    std::vector<float> S(M);
+    for (int p = 0; p < M; ++p) S[p] = (float)(-kc[p].imag() / M);
+    if (!h.conv_tw.count(M)) {
+        std::vector<float2> tw(M);
+        for (int m = 0; m < M; ++m) {
+            const double a = 2.0 * M_PI * m / M;
+            tw[m] = make_float2((float)cos(a), (float)-sin(a));
+        }
+        float2 *d = nullptr;
+        cudaError_t e = cudaMalloc(&d, sizeof(float2) * M);
+        if (e != cudaSuccess) return check_cuda(e, "any-length plan: twiddles");
+        e = cudaMemcpy(d, tw.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return check_cuda(e, "any-length plan: twiddles upload");
+        }
+        h.conv_tw[M] = d;
+        h.workspace_used += sizeof(float2) * M;
+    }
+    float *dS = nullptr;
+    cudaError_t e = cudaMalloc(&dS, sizeof(float) * M);
+    if (e != cudaSuccess) return check_cuda(e, "any-length plan: spectrum");
+    e = cudaMemcpy(dS, S.data(), sizeof(float) * M, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dS);
+        return check_cuda(e, "any-length plan: spectrum upload");
+    }
+    h.conv_S[T] = dS;
+    h.workspace_used += sizeof(float) * M;
+    ConvPlan p;
+    p.M = M;
+    p.nstages = (int)radix.size();
+    for (int k = 0; k < 8; ++k) p.radix[k] = k < p.nstages ? radix[k] : 0;
+    p.tw = h.conv_tw[M];
+    p.S = dS;
+    h.conv[T] = p;
+    *out = &h.conv[T];
+    return PLV_OK;
+}
+
+void free_conv_plans(Handle &h) {
+    for (auto &kv : h.conv_tw) cudaFree(kv.second);
+    for (auto &kv : h.conv_S) cudaFree(kv.second);
+    h.conv_tw.clear();
+    h.conv_S.clear();
+    h.conv.clear();
+}
+
+}  // namespace plv

@@ -335,5 +335,178 @@ cudaError_t launch_hilbert_pow2(int num_sms, cudaStream_t st, int log2T, const T
     }
 }
 
+// ---------------------------------------------------------------------------
+// Any-length engine.  The periodic Hilbert transform of length T is the
+// circular convolution y = x (*)_T k_T with the real, odd kernel
+//     k_T[n] = (2/T) sum_{k=1}^{ceil(T/2)-1} sin(2 pi k n / T)
+// (the inverse DFT of -i sgn).  A circular convolution of length T equals
+// the first T outputs of a circular convolution of length M >= 2T - 1 of the
+// zero-padded row with the kernel placed at [0, T) and its periodic
+// continuation at [M - T + 1, M).  So for any T:
+//     y = IFFT_M( K (.) FFT_M(c_pad) ),  K = FFT_M(k_circ) = -i S  (S real).
+// FFT_M is an in-place decimation-in-frequency transform (digit-reversed
+// output), K is stored in that order (and divided by M), and the inverse is
+// the matching in-place decimation-in-time transform (digit-reversed input,
+// natural output), so no reordering pass is needed.  M = 2^a or 3 * 2^a.
+// One sequence (row pair) per CTA; every thread loops over butterflies with
+// only R values in registers, so the shared buffer is single.
+
+constexpr int kConvThreads = 512;
+
+__device__ __forceinline__ void dft3(float2 (&a)[3]) {
+    const float h = 0.86602540378443864676f;  // sqrt(3) / 2
+    const float2 t1 = cadd(a[1], a[2]);
+    const float2 t2 = make_float2(fmaf(-0.5f, t1.x, a[0].x), fmaf(-0.5f, t1.y, a[0].y));
+    const float2 d = csub(a[1], a[2]);
+    const float2 t3 = make_float2(h * d.y, -h * d.x);  // -i h (a1 - a2)
+    a[0] = cadd(a[0], t1);
+    a[1] = cadd(t2, t3);
+    a[2] = csub(t2, t3);
+}
+
+template <int R>
+__device__ __forceinline__ void dft_any(float2 (&a)[R]) {
+    if constexpr (R == 3) dft3(a);
+    else Dft<R>::run(a);
+}
+
+// One radix-R butterfly of a decimation-in-frequency stage (span = R sub):
+// V = DFT_R(x[base + r sub]); x[base + q sub] = V[q] w_span^(q j).
+// With INV it is the matching decimation-in-time inverse butterfly:
+// v[r] = x[base + r sub] conj(w_span)^(r j); x[base + q sub] = IDFT_R(v)[q],
+// done as conj(DFT_R(conj(v))).
+template <int R, bool INV>
+__device__ __forceinline__ void conv_bfly(float2 *s, int base, int sub, int tb,
+                                          const float2 *__restrict__ tw) {
+    float2 a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        a[r] = s[padi(base + r * sub)];
+        if (INV) a[r].y = -a[r].y;
+    }
+    if (INV && tb != 0) {
+        // conj(x conj(w^r)) = conj(x) w^r
+        if constexpr (R == 16) {
+            apply_twiddles16(tw, tb, a);
+        } else {
+#pragma unroll
+            for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&tw[r * tb]));
+        }
+    }
+    dft_any<R>(a);
+    if (!INV && tb != 0) {
+        if constexpr (R == 16) {
+            apply_twiddles16(tw, tb, a);
+        } else {
+#pragma unroll
+            for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&tw[r * tb]));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float2 v = a[r];
+        if (INV) v.y = -v.y;
+        s[padi(base + r * sub)] = v;
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void conv_stage(float2 *s, int M, int R, int span,
+                                           const float2 *__restrict__ tw) {
+    const int sub = span / R;
+    const int tstep = M / span;  // w_span = w_M^tstep
+    const int nb = M / R;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int g = b / sub, j = b - g * sub;
+        const int base = g * span + j;
+        const int tb = tstep * j;
+        switch (R) {
+            case 16: conv_bfly<16, INV>(s, base, sub, tb, tw); break;
+            case 8: conv_bfly<8, INV>(s, base, sub, tb, tw); break;
+            case 4: conv_bfly<4, INV>(s, base, sub, tb, tw); break;
+            case 3: conv_bfly<3, INV>(s, base, sub, tb, tw); break;
+            default: conv_bfly<2, INV>(s, base, sub, tb, tw); break;
+        }
+    }
+    __syncthreads();
+}
+
+// Same Task interface as k_hilbert_pairs, plus
+//   void pad(int64_t r0, bool v0, int64_t r1, bool v1, int m)
+// for the padding samples T <= m < ld of the output rows.
+template <class Task>
+__global__ void __launch_bounds__(kConvThreads, 2)
+k_hilbert_conv(const Task task, const ConvPlan plan, int T, int64_t ld, int64_t rows) {
+    extern __shared__ __align__(16) float2 smem[];
+    __shared__ float s_pow;
+    const int M = plan.M;
+    const int64_t npairs = (rows + 1) / 2;
+    for (int64_t pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const int64_t r0 = 2 * pr, r1 = 2 * pr + 1;
+        const bool v0 = r0 < rows, v1 = r1 < rows;
+        __syncthreads();  // the previous pair is done with smem and s_pow
+        if (threadIdx.x == 0) s_pow = 0.f;
+        float pw = 0.f;
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            const float2 c = m < T ? task.load(r0, v0, r1, v1, m) : make_float2(0.f, 0.f);
+            pw = fmaf(c.x, c.x, fmaf(c.y, c.y, pw));
+            smem[padi(m)] = c;
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) pw += __shfl_xor_sync(0xffffffffu, pw, off);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s_pow, pw);
+        // forward transform (decimation in frequency)
+        int span = M;
+        for (int st = 0; st < plan.nstages; ++st) {
+            conv_stage<false>(smem, M, plan.radix[st], span, plan.tw);
+            span /= plan.radix[st];
+        }
+        // times K = -i S (already divided by M)
+        for (int p = threadIdx.x; p < M; p += blockDim.x) {
+            const float2 v = smem[padi(p)];
+            const float S = __ldg(&plan.S[p]);
+            smem[padi(p)] = make_float2(S * v.y, -S * v.x);
+        }
+        __syncthreads();
+        // inverse transform (decimation in time, stages in reverse)
+        span = 1;
+        for (int st = plan.nstages - 1; st >= 0; --st) {
+            span *= plan.radix[st];
+            conv_stage<true>(smem, M, plan.radix[st], span, plan.tw);
+        }
+        const float floor2 = 0x1p-40f * (s_pow / (float)T);
+        for (int m = threadIdx.x; m < ld; m += blockDim.x) {
+            if (m < T) {
+                const float2 y = smem[padi(m)];
+                task.finish(r0, v0, r1, v1, m, y.x, y.y, floor2);
+            } else {
+                task.pad(r0, v0, r1, v1, m);
+            }
+        }
+    }
+}
+
+template <class Task>
+cudaError_t launch_hilbert_conv(int num_sms, cudaStream_t st, const Task &task,
+                                const ConvPlan &plan, int T, int64_t ld, int64_t rows) {
+    auto kern = k_hilbert_conv<Task>;
+    static LaunchSetup ls;
+    constexpr size_t kMaxSmem = (size_t)(24576 + 24576 / 32) * sizeof(float2);
+    int unused = 0;
+    cudaError_t e = setup_once(ls, kern, kConvThreads, kMaxSmem, unused);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)(plan.M + plan.M / 32) * sizeof(float2);
+    int per_sm = (int)(225 * 1024 / (smem + 1024));
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t npairs = (rows + 1) / 2;
+    if (npairs == 0) return cudaSuccess;
+    int64_t grid = (int64_t)per_sm * num_sms * 2;
+    if (grid > npairs) grid = npairs;
+    kern<<<(unsigned)grid, kConvThreads, smem, st>>>(task, plan, T, ld, rows);
+    return cudaGetLastError();
+}
+
 }  // namespace fft
 }  // namespace plv

@@ -95,6 +95,11 @@ struct FwdTask {
         if (v0) store_phasor<PREC>(P, r0, N, ld, m, unit_phasor(ldx_f(x + r0 * ldx + m), h0, floor2));
         if (v1) store_phasor<PREC>(P, r1, N, ld, m, unit_phasor(ldx_f(x + r1 * ldx + m), h1, floor2));
     }
+    // padding samples T <= m < ld are zero
+    __device__ void pad(int64_t r0, bool v0, int64_t r1, bool v1, int m) const {
+        if (v0) store_phasor<PREC>(P, r0, N, ld, m, make_float2(0.f, 0.f));
+        if (v1) store_phasor<PREC>(P, r1, N, ld, m, make_float2(0.f, 0.f));
+    }
 };
 
 // Backward preparation: the same analytic signal, stored as FP32 phasors
@@ -124,6 +129,15 @@ struct PrepTask {
                            float h1, float floor2) const {
         if (v0) one(r0, m, h0, floor2);
         if (v1) one(r1, m, h1, floor2);
+    }
+    __device__ void pad(int64_t r0, bool v0, int64_t r1, bool v1, int m) const {
+        for (int h = 0; h < 2; ++h) {
+            const int64_t r = h ? r1 : r0;
+            if (!(h ? v1 : v0)) continue;
+            P[r * 2 * ld + m] = 0.f;
+            P[r * 2 * ld + ld + m] = 0.f;
+            rinv[r * ld + m] = 0.f;
+        }
     }
 };
 
@@ -159,6 +173,26 @@ cudaError_t launch_zero_pad_rows(cudaStream_t s, void *P, int batch, int N, int 
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_zero_pad_rows<<<(unsigned)blocks, 256, 0, s>>>((uint4 *)P, batch, N, row_blocks(N), NKB);
     return cudaGetLastError();
+}
+
+cudaError_t launch_analytic_conv(const Handle *h, cudaStream_t s, const void *x,
+                                 plv_dtype dt, int64_t rows, int N, int T, int64_t ldx,
+                                 void *P, const ConvPlan &plan) {
+    const int64_t ld = padded_len(T);
+    const int ns = h->num_sms;
+    if (h->prec == PLV_PREC_FP32) {
+        if (dt == PLV_F32)
+            return launch_hilbert_conv(ns, s, FwdTask<float, PLV_PREC_FP32>{(const float *)x, ldx, P, N, ld}, plan, T, ld, rows);
+        return launch_hilbert_conv(ns, s, FwdTask<double, PLV_PREC_FP32>{(const double *)x, ldx, P, N, ld}, plan, T, ld, rows);
+    }
+    if (h->prec == PLV_PREC_FP16X3) {
+        if (dt == PLV_F32)
+            return launch_hilbert_conv(ns, s, FwdTask<float, PLV_PREC_FP16X3>{(const float *)x, ldx, P, N, ld}, plan, T, ld, rows);
+        return launch_hilbert_conv(ns, s, FwdTask<double, PLV_PREC_FP16X3>{(const double *)x, ldx, P, N, ld}, plan, T, ld, rows);
+    }
+    if (dt == PLV_F32)
+        return launch_hilbert_conv(ns, s, FwdTask<float, PLV_PREC_BF16X3>{(const float *)x, ldx, P, N, ld}, plan, T, ld, rows);
+    return launch_hilbert_conv(ns, s, FwdTask<double, PLV_PREC_BF16X3>{(const double *)x, ldx, P, N, ld}, plan, T, ld, rows);
 }
 
 cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,

@@ -168,6 +168,7 @@ plv_status plv_destroy(plv_handle *hp) {
         if (h.twiddles) cudaFree(h.twiddles);
         if (h.status) cudaFree(h.status);
         if (h.ws) cudaFree(h.ws);
+        free_conv_plans(h);
     }
     delete hp;
     return PLV_OK;
@@ -192,11 +193,11 @@ plv_status plv_prepare(plv_handle *hp, int T) {
     if (!hp) return fail(PLV_ERR_INVALID, "plv_prepare: handle is NULL");
     if (T <= 0) return fail(PLV_ERR_INVALID, "plv_prepare: T = %d", T);
     const int L = log2_exact(T);
-    if (L < kMinLog2T || L > kMaxLog2Direct)
-        return fail(PLV_ERR_UNSUPPORTED,
-                    "plv_prepare: T = %d (this build's FFT takes powers of two "
-                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2Direct);
-    return PLV_OK;  // power-of-two tables are made by plv_create
+    if (L >= kMinLog2T && L <= kMaxLog2Direct) return PLV_OK;  // tables made by plv_create
+    PLV_GUARD(&hp->h);
+    std::lock_guard<std::mutex> lock(hp->h.mu);
+    const ConvPlan *plan = nullptr;
+    return get_conv_plan(hp->h, T, &plan);
 }
 
 plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
@@ -211,10 +212,10 @@ plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
     if (batch == 0 || N == 0) return PLV_OK;
     if (!x || !P) return fail(PLV_ERR_INVALID, "plv_analytic: NULL data pointer");
     const int L = log2_exact(T);
-    if (L < kMinLog2T || L > kMaxLog2Direct)
-        return fail(PLV_ERR_UNSUPPORTED,
-                    "plv_analytic: T = %d (this build's FFT takes powers of two "
-                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2Direct);
+    const bool direct = L >= kMinLog2T && L <= kMaxLog2Direct;
+    if (!direct && (T < 2 || 2 * T - 1 > kMaxConvM))
+        return fail(PLV_ERR_UNSUPPORTED, "plv_analytic: T = %d (supported: 2 <= T <= %d)", T,
+                    kMaxConvM / 2);
     const size_t esz = dtype == PLV_F32 ? 4 : 8;
     if (((uintptr_t)x % esz) != 0)
         return fail(PLV_ERR_INVALID, "plv_analytic: x is not %zu-byte aligned", esz);
@@ -226,8 +227,26 @@ plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
                                    "plv_analytic: pad rows");
         if (st != PLV_OK) return st;
     }
-    return check_cuda(launch_analytic_pow2(&hp->h, (cudaStream_t)stream, x, dtype,
-                                           (int64_t)batch * N, N, L, ldx, P),
+    if (direct)
+        return check_cuda(launch_analytic_pow2(&hp->h, (cudaStream_t)stream, x, dtype,
+                                               (int64_t)batch * N, N, L, ldx, P),
+                          "plv_analytic launch");
+    const ConvPlan *plan = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(hp->h.mu);
+        if (!hp->h.conv.count(T)) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) == cudaSuccess &&
+                cs != cudaStreamCaptureStatusNone)
+                return fail(PLV_ERR_INVALID,
+                            "plv_analytic: tables for T = %d must be made before capture "
+                            "(call plv_prepare)", T);
+        }
+        plv_status st = get_conv_plan(hp->h, T, &plan);
+        if (st != PLV_OK) return st;
+    }
+    return check_cuda(launch_analytic_conv(&hp->h, (cudaStream_t)stream, x, dtype,
+                                           (int64_t)batch * N, N, T, ldx, P, *plan),
                       "plv_analytic launch");
 }
 

@@ -50,6 +50,42 @@ def test_analytic_phasors_on_bin_tones(handles, prec, T):
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("T", [2, 3, 33, 100, 500, 997, 1000, 3001, 4097, 8191,
+                               9999, 10000, 12288])
+def test_analytic_any_length_vs_oracle(handles, prec, T):
+    """Eq. 3-4 for lengths that are not powers of two (the circular
+    convolution with the periodic Hilbert kernel): against the oracle's
+    direct DFT, in z, with zero padding samples."""
+    h = handles[prec]
+    rng = np.random.default_rng(T)
+    B, N = 1, 3
+    x = rng.standard_normal((B, N, T))
+    P = h.plv_analytic(torch.tensor(x, device="cuda", dtype=torch.float32))
+    got = unpack_phasors(P, prec, B, N, T)
+    z = oracle.analytic(x.astype(np.float32).astype(np.float64))
+    ref = z / np.abs(z)
+    rms = np.sqrt(np.mean(np.abs(z) ** 2))
+    err_z = np.abs(got - ref) * np.abs(z)
+    assert err_z.max() < max(2e-5, PHASOR_TOL[prec]) * rms, err_z.max() / rms
+    ld = ((T + 31) // 32) * 32
+    if prec == "fp32" and ld > T:
+        pad = P[: B * N * 2 * ld].view(B, N, 2, ld)[..., T:]
+        assert torch.all(pad == 0)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_end_to_end_any_length(handles, prec):
+    """Whole path at T = 1000 and T = 2500 (ragged N) against the oracle."""
+    h = handles[prec]
+    for (N, T) in ((70, 1000), (129, 2500)):
+        x = synth.bandlimited(1, N, T, seed=T, device="cuda")
+        res = _to_np(h.connectivity(x, C=True))
+        ref = oracle.connectivity(x[0].double().cpu().numpy())
+        gpu = {k: res[k][0] for k in ("plv", "iplv", "ciplv")}
+        compare(gpu, ref, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
 def test_analytic_phasors_random_vs_oracle(handles, prec):
     """Eq. 3-4 on white noise against the oracle's direct DFT: phasor error
     scales like (FFT error)/|z|, so compare where |z| is not tiny."""
@@ -159,10 +195,10 @@ def test_invalid_arguments_are_rejected(handles):
     import paper_1710_08037_gb300 as plv
     from paper_1710_08037_gb300 import _lib
     h = handles["fp32"]
-    x = torch.randn(1, 4, 100, device="cuda")
     with pytest.raises(plv.PlvError) as ei:
-        h.plv_analytic(x)  # T = 100: not a power of two
+        h.plv_analytic(torch.randn(1, 2, 20000, device="cuda"))  # T too long
     assert ei.value.status == _lib.PLV_ERR_UNSUPPORTED
+    x = torch.randn(1, 4, 100, device="cuda")
     P = h.empty_phasors(1, 4, 64)
     rc = h.lib.plv_gram(h.h, None, None, 1, 4, 64, 1, None, None, None, None,
                         None)
