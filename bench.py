@@ -42,6 +42,10 @@ WORKLOADS = {
     "bandlimited-N4096-T4096-E4": (4, 4096, 4096, 1002),
 }
 DEFAULT_WORKLOAD = "bandlimited-N4096-T4096-E30"
+# uneven batch: 256 subjects, N ~ U{68..2000}, T ~ U{500..10000} per subject,
+# 5 frequency bands each (1280 problems of one epoch), fs = 1000 Hz
+GROUPED = "grouped-256subj-5bands-N68to2000-T500to10000"
+BANDS = [(4.0, 8.0), (8.0, 12.0), (13.0, 30.0), (30.0, 45.0), (55.0, 80.0)]
 
 
 def _peaks():
@@ -334,6 +338,125 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def grouped_problems(seed=1004, nsub=256):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for sj in range(nsub):
+        N = int(rng.integers(68, 2001))
+        T = int(rng.integers(500, 10001))
+        for b, band in enumerate(BANDS):
+            out.append((N, T, band, seed * 10000 + sj * 5 + b))
+    return out
+
+
+def run_grouped(args):
+    """The uneven batch in one persistent grouped-Gram launch: per step, the
+    phasor kernel of every problem (one CUDA graph) and the grouped Gram (a
+    second graph), inputs resident in HBM."""
+    import torch
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    h = plv.Handle(precision=args.precision, device=local)
+    specs = grouped_problems(seed=1004 + rank, nsub=args.subjects)
+    t_gen = time.perf_counter()
+    probs = []
+    for (N, T, band, sd) in specs:
+        x = synth.bandlimited(1, N, T, seed=sd, band=band, device=dev)
+        h.prepare(T)
+        probs.append({"x": x, "P": h.empty_phasors(1, N, T), "batch": 1,
+                      "N": N, "T": T})
+    t_gen = time.perf_counter() - t_gen
+    grp = h.plv_group_create(probs)
+    s = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+
+    def k1_all():
+        for q in probs:
+            h.plv_analytic(q["x"], q["P"])
+
+    with torch.cuda.stream(s):
+        k1_all()
+        h.plv_gram_grouped(grp)
+    torch.cuda.synchronize(dev)
+    g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g1, stream=s):
+            k1_all()
+        with torch.cuda.graph(g2, stream=s):
+            h.plv_gram_grouped(grp)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            g1.replay()
+            g2.replay()
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        per = [[ev(), ev(), ev()] for _ in range(args.steps)]
+        for p in per:
+            p[0].record(s)
+            g1.replay()
+            p[1].record(s)
+            g2.replay()
+            p[2].record(s)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+    ms = sum(p[0].elapsed_time(p[2]) for p in per)
+    k1_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
+    gram_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / args.steps
+    units = float(sum(N * N * T for (N, T, _, _) in specs))
+    value = units * world / (ms_step / 1e3)
+    flops = sum(gram_flops(N, T, 1, args.precision) for (N, T, _, _) in specs)
+    peaks, peak_kind = _peaks()
+    peak = float(peaks["bf16_tflops"])
+    roof = {"bound": "tensor", "kernel": "k_gram_tc (grouped, one launch)",
+            "achieved": flops / (gram_ms / 1e3) / 1e12, "peak": peak,
+            "unit": "TFLOP/s", "peak_source": f"{peak_kind} bf16 dense (burst)",
+            "traffic": None, "launch_ms": gram_ms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    k1b = sum(N * T * 12 for (N, T, _, _) in specs)
+    device_status = h.plv_sync_status()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": GROUPED, "problems": len(specs),
+                       "sum_N2T": units, "precision": args.precision,
+                       "graphs": "phasor kernels of all problems in one CUDA "
+                                 "graph, grouped Gram in another",
+                       "generation_s": t_gen},
+            "roofline": roof,
+            "k1": {"launches": len(specs), "ms": k1_ms,
+                   "algorithmic_GBps": k1b / (k1_ms / 1e3) / 1e9},
+            "gpu_launches": (len(specs) + 1) * args.steps,
+            "clocks": clk, "device_status": device_status}
+        print(json.dumps(line), flush=True)
+    grp.close()
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(E, N, T, seed, nsub):
     """The FP64 oracle as it stands, on a bounded sample of the same
     workload: one epoch, a random subset S of ``nsub`` channels; direct-DFT
@@ -405,8 +528,10 @@ def main():
                     default="bf16x3")
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the split one")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS),
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED],
                     default=DEFAULT_WORKLOAD)
+    ap.add_argument("--subjects", type=int, default=256,
+                    help="subjects of the grouped workload")
     ap.add_argument("--sustained", action="store_true",
                     help="roofline against the sustained tensor peak")
     ap.add_argument("--no-e2e", action="store_true")
@@ -418,6 +543,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == GROUPED:
+        run_grouped(args)
     else:
         run_ours(args)
 

@@ -138,12 +138,13 @@ cudaError_t launch_analytic_pow2(const Handle *h, cudaStream_t s,
 cudaError_t launch_zero_pad_rows(cudaStream_t s, void *P, int batch, int N, int T);
 // Backward preparation: FP32 phasors P[rows][2][ld] and rinv[rows][ld].
 cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
-                            int64_t rows, int log2T, int64_t ldx, float *P, float *rinv);
+                            int64_t rows, int log2T, int64_t ldx, float *P, float *rinv,
+                            int T, const ConvPlan *plan);
 // K5: S = G + G^H, Gamma = S P / T, grad = Re Gamma_z - H{Im Gamma_z}.
 cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
                             int log2T, const float2 *C, const float *g1, const float *g2,
                             const float *g3, const float *P, const float *rinv, float *S,
-                            float *Gm, float *grad);
+                            float *Gm, float *grad, const ConvPlan *plan);
 // Eq. 4 on a given analytic signal.
 cudaError_t launch_normalize(const Handle *h, cudaStream_t s, const void *z,
                              plv_dtype dt, int64_t rows, int N, int T,

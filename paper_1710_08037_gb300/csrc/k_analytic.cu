@@ -196,7 +196,14 @@ cudaError_t launch_analytic_conv(const Handle *h, cudaStream_t s, const void *x,
 }
 
 cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
-                            int64_t rows, int log2T, int64_t ldx, float *P, float *rinv) {
+                            int64_t rows, int log2T, int64_t ldx, float *P, float *rinv,
+                            int T, const ConvPlan *plan) {
+    if (plan) {
+        const int64_t ld = padded_len(T);
+        if (dt == PLV_F32)
+            return launch_hilbert_conv(h->num_sms, s, PrepTask<float>{(const float *)x, ldx, P, rinv, ld}, *plan, T, ld, rows);
+        return launch_hilbert_conv(h->num_sms, s, PrepTask<double>{(const double *)x, ldx, P, rinv, ld}, *plan, T, ld, rows);
+    }
     const float2 *tw = twiddle_table(h, log2T);
     const int64_t ld = (int64_t)1 << log2T;
     if (dt == PLV_F32) {

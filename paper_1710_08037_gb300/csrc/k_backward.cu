@@ -214,6 +214,7 @@ struct BwdTask {
         if (v1) b = s_of(r1, m, pr, pi) * pr;
         return make_float2(a, b);
     }
+    __device__ void pad(int64_t, bool, int64_t, bool, int) const {}  // grad has no padding
     __device__ void finish(int64_t r0, bool v0, int64_t r1, bool v1, int m, float h0,
                            float h1, float) const {
         float pr, pi;
@@ -233,7 +234,7 @@ struct BwdTask {
 cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
                             int log2T, const float2 *C, const float *g1, const float *g2,
                             const float *g3, const float *P, const float *rinv, float *S,
-                            float *Gm, float *grad) {
+                            float *Gm, float *grad, const ConvPlan *plan) {
     const int64_t ld = padded_len(T);
     dim3 sg((N + 31) / 32, (N + 31) / 32, batch);
     k_bwd_s<<<sg, 256, 0, st>>>(C, g1, g2, g3, N, S);
@@ -244,6 +245,7 @@ cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     BwdTask task{P, Gm, rinv, grad, ld, T};
+    if (plan) return launch_hilbert_conv(h->num_sms, st, task, *plan, T, ld, (int64_t)batch * N);
     return launch_hilbert_pow2(h->num_sms, st, log2T, task, twiddle_table(h, log2T),
                                (int64_t)batch * N);
 }

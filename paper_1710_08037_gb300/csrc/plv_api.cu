@@ -475,10 +475,10 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
     if (batch == 0 || N == 0) return PLV_OK;
     if (!grad_x) return fail(PLV_ERR_INVALID, "plv_backward: grad_x is NULL");
     const int L = log2_exact(T);
-    if (L < kMinLog2T || L > kMaxLog2Direct)
-        return fail(PLV_ERR_UNSUPPORTED,
-                    "plv_backward: T = %d (this build's FFT takes powers of two "
-                    "from %d to %d)", T, 1 << kMinLog2T, 1 << kMaxLog2Direct);
+    const bool direct = L >= kMinLog2T && L <= kMaxLog2Direct;
+    if (!direct && (T < 2 || 2 * T - 1 > kMaxConvM))
+        return fail(PLV_ERR_UNSUPPORTED, "plv_backward: T = %d (supported: 2 <= T <= %d)", T,
+                    kMaxConvM / 2);
     PLV_GUARD(&hp->h);
     Handle &h = hp->h;
     cudaStream_t s = (cudaStream_t)stream;
@@ -497,14 +497,26 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
     std::lock_guard<std::mutex> lock(h.mu);
     plv_status st = ensure_workspace(h, s, bP + bR + bG + bS);
     if (st != PLV_OK) return st;
+    const ConvPlan *plan = nullptr;
+    if (!direct) {
+        if (!h.conv.count(T)) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+                return fail(PLV_ERR_INVALID,
+                            "plv_backward: tables for T = %d must be made before capture "
+                            "(call plv_prepare)", T);
+        }
+        st = get_conv_plan(h, T, &plan);
+        if (st != PLV_OK) return st;
+    }
     char *w = (char *)h.ws;
     float *P = (float *)w, *rinv = (float *)(w + bP), *Gm = (float *)(w + bP + bR),
           *S = (float *)(w + bP + bR + bG);
-    st = check_cuda(launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv),
+    st = check_cuda(launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv, T, plan),
                     "plv_backward: recompute");
     if (st != PLV_OK) return st;
     return check_cuda(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,
-                                      g_ciplv, P, rinv, S, Gm, grad_x),
+                                      g_ciplv, P, rinv, S, Gm, grad_x, plan),
                       "plv_backward launch");
 }
 

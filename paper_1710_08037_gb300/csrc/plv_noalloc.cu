@@ -152,10 +152,11 @@ extern "C" plv_status plv_backward_noalloc(void *stream, const void *x, plv_dtyp
     unsigned char *w = st->scratch;
     float *P = (float *)w, *rinv = (float *)(w + bP), *Gm = (float *)(w + bP + bR),
           *S = (float *)(w + bP + bR + bG);
-    plv_status r = check_cuda(launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv),
-                              "plv_backward_noalloc: recompute");
+    plv_status r = check_cuda(
+        launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv, T, nullptr),
+        "plv_backward_noalloc: recompute");
     if (r != PLV_OK) return r;
     return check_cuda(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,
-                                      g_ciplv, P, rinv, S, Gm, grad_x),
+                                      g_ciplv, P, rinv, S, Gm, grad_x, nullptr),
                       "plv_backward_noalloc launch");
 }

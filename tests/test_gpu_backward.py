@@ -46,7 +46,7 @@ def _gpu_grad(h, x, gs, prec_forward="fp32"):
 
 @pytest.mark.parametrize("which", [("plv",), ("iplv",), ("ciplv",),
                                    ("plv", "iplv", "ciplv")])
-@pytest.mark.parametrize("N,T", [(16, 256), (67, 128)])
+@pytest.mark.parametrize("N,T", [(16, 256), (67, 128), (20, 300)])
 def test_backward_vs_torch_fp64(h32, which, N, T):
     rng = np.random.default_rng(N * 7 + T + len(which))
     B = 2
@@ -127,6 +127,7 @@ def test_backward_zero_grads_and_validation(h32):
     C = torch.zeros(1, 8, 8, dtype=torch.complex64, device="cuda")
     g = h32.plv_backward(x, C)
     assert torch.all(g == 0)
-    rc = h32.lib.plv_backward(h32.h, None, x.data_ptr(), 0, 1, 8, 100, 100,
-                              C.data_ptr(), None, None, None, g.data_ptr())
+    xl = torch.randn(1, 8, 20000, device="cuda")
+    rc = h32.lib.plv_backward(h32.h, None, xl.data_ptr(), 0, 1, 8, 20000, 20000,
+                              C.data_ptr(), C.data_ptr(), None, None, g.data_ptr())
     assert rc == _lib.PLV_ERR_UNSUPPORTED
