@@ -35,26 +35,6 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
 }
 
-// Multiply a[r] by the twiddle tw[r * base], r = 1..15, from four table
-// loads (r = 1, 2, 4, 8) and products of those, at most three products deep;
-// only w^1..w^8 are held at once.
-__device__ __forceinline__ void apply_twiddles16(const float2 *__restrict__ tw, int base,
-                                                 float2 (&a)[16]) {
-    float2 w[9];
-    w[1] = __ldg(&tw[base]);
-    w[2] = __ldg(&tw[2 * base]);
-    w[4] = __ldg(&tw[4 * base]);
-    w[8] = __ldg(&tw[8 * base]);
-    w[3] = cmul(w[2], w[1]);
-    w[5] = cmul(w[4], w[1]);
-    w[6] = cmul(w[4], w[2]);
-    w[7] = cmul(w[4], w[3]);
-#pragma unroll
-    for (int r = 1; r <= 8; ++r) a[r] = cmul(a[r], w[r]);
-#pragma unroll
-    for (int r = 1; r < 8; ++r) a[8 + r] = cmul(a[8 + r], cmul(w[8], w[r]));
-}
-
 // a * exp(-i pi m / 8), m in 0..7 (folds to a constant path after unrolling)
 __device__ __forceinline__ float2 rot16(float2 a, int m) {
     const float c1 = 0.92387953251128675613f;  // cos(pi/8)
@@ -142,13 +122,9 @@ __device__ __forceinline__ void stockham(const float2 *src, float2 *dst,
             }
         }
         if constexpr (NS > 1) {
-            if constexpr (R == 16) {
-                apply_twiddles16(tw, k * (T / (NS * R)), a);
-            } else {
 #pragma unroll
-                for (int r = 1; r < R; ++r)
-                    a[r] = cmul(a[r], __ldg(&tw[r * k * (T / (NS * R))]));
-            }
+            for (int r = 1; r < R; ++r)
+                a[r] = cmul(a[r], __ldg(&tw[r * k * (T / (NS * R))]));
         }
         Dft<R>::run(a);
         const int base = (j - k) * R + k;
@@ -238,10 +214,11 @@ struct K1Cfg {
 
 // The Hilbert transform of real rows, two rows per complex FFT, for any
 // Task providing
-//   float2 load(int64_t r0, bool v0, int64_t r1, bool v1, int m):
+//   Rows rows(int64_t r0, bool v0, int64_t r1, bool v1):
+//       per-pair state (row addresses), computed once per pair;
+//   float2 load(const Rows &, int m):
 //       the complex sample c[m] = u0[m] + i u1[m] of rows r0, r1;
-//   void finish(int64_t r0, bool v0, int64_t r1, bool v1, int m,
-//               float h0, float h1, float floor2):
+//   void finish(const Rows &, int m, float h0, float h1, float floor2):
 //       consumes H{u0}[m], H{u1}[m]; floor2 is 2^-40 of the pair's mean
 //       |c|^2 (the rounding floor of the transform).
 // With c = u0 + i u1: w = IFFT(-i sgn(k) FFT(c)) = H{u0} + i H{u1}, computed
@@ -270,7 +247,8 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
         __syncthreads();
         if (lt == 0) s_pow[sq] = 0.f;  // ordered before the adds by pass 0's barrier
         float pw;
-        auto load = [&](int m) { return task.load(r0, v0, r1, v1, m); };
+        const auto rs = task.rows(r0, v0, r1, v1);
+        auto load = [&](int m) { return task.load(rs, m); };
         stockham<T, radix_of(L, 0), 1, kFromX>(nullptr, buf[1], tw, lt, load, &pw);
         // sum of |c|^2 over the sequence (its lanes are an aligned group of Q
         // threads, or whole warps when Q >= 32)
@@ -293,7 +271,7 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
         for (int u = 0; u < 16; ++u) {
             const int m = lt + u * C::Q;
             const float2 w = w_out[padi(m)];
-            task.finish(r0, v0, r1, v1, m, w.x * invT, -w.y * invT, floor2);
+            task.finish(rs, m, w.x * invT, -w.y * invT, floor2);
         }
     }
 }
@@ -370,119 +348,176 @@ __device__ __forceinline__ void dft_any(float2 (&a)[R]) {
     else Dft<R>::run(a);
 }
 
-// One radix-R butterfly of a decimation-in-frequency stage (span = R sub):
-// V = DFT_R(x[base + r sub]); x[base + q sub] = V[q] w_span^(q j).
-// With INV it is the matching decimation-in-time inverse butterfly:
-// v[r] = x[base + r sub] conj(w_span)^(r j); x[base + q sub] = IDFT_R(v)[q],
-// done as conj(DFT_R(conj(v))).
+// Load R values (stride sub) of one butterfly; with INV conjugate them.
 template <int R, bool INV>
-__device__ __forceinline__ void conv_bfly(float2 *s, int base, int sub, int tb,
-                                          const float2 *__restrict__ tw) {
-    float2 a[R];
+__device__ __forceinline__ void bfly_load(const float2 *s, int base, int sub, float2 (&a)[R]) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         a[r] = s[padi(base + r * sub)];
         if (INV) a[r].y = -a[r].y;
     }
-    if (INV && tb != 0) {
-        // conj(x conj(w^r)) = conj(x) w^r
-        if constexpr (R == 16) {
-            apply_twiddles16(tw, tb, a);
-        } else {
+}
+template <int R>
+__device__ __forceinline__ void twiddle_r(float2 (&a)[R], int tb, const float2 *__restrict__ tw) {
+    if (tb != 0) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&tw[r * tb]));
-        }
-    }
-    dft_any<R>(a);
-    if (!INV && tb != 0) {
-        if constexpr (R == 16) {
-            apply_twiddles16(tw, tb, a);
-        } else {
-#pragma unroll
-            for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&tw[r * tb]));
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        float2 v = a[r];
-        if (INV) v.y = -v.y;
-        s[padi(base + r * sub)] = v;
+        for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&tw[r * tb]));
     }
 }
+// Decimation-in-frequency butterfly on registers (span = R sub, position j
+// in the sub-block): V = DFT_R(v); V[q] *= w_span^(q j).
+template <int R>
+__device__ __forceinline__ void dif_core(float2 (&a)[R], int tb, const float2 *tw) {
+    dft_any<R>(a);
+    twiddle_r<R>(a, tb, tw);
+}
+// Matching decimation-in-time inverse on conjugated registers: conj(v) has
+// been loaded; v[r] conj(w)^(r j) then IDFT_R is conj(DFT_R(conj(v) w^(r j))).
+template <int R>
+__device__ __forceinline__ void dit_core_conj(float2 (&a)[R], int tb, const float2 *tw) {
+    twiddle_r<R>(a, tb, tw);
+    dft_any<R>(a);
+}
 
-template <bool INV>
-__device__ __forceinline__ void conv_stage(float2 *s, int M, int R, int span,
-                                           const float2 *__restrict__ tw) {
-    const int sub = span / R;
+// Stage kinds of the any-length transform.
+enum ConvStage { kDifSmem = 0, kDitSmem = 1, kDifFirst = 2, kMidFused = 3, kDitLast = 4 };
+
+// One stage over all butterflies.  span = R sub with sub = 1 << lsub.
+//   kDifFirst: inputs c[m] = task.load (0 for m >= T) straight from global
+//              memory, sums |c|^2 into *pw;
+//   kDifSmem / kDitSmem: shared memory in place;
+//   kMidFused: the last forward stage, the multiply by K = -i S / M and the
+//              first inverse stage, all in registers (same butterflies, sub = 1);
+//   kDitLast:  the last inverse stage; outputs m < T go to task.finish, the
+//              padding T <= m < ld to task.pad.
+template <int R, int KIND, class Task>
+__device__ __forceinline__ void conv_stage_r(float2 *s, int M, int lsub, const ConvPlan &plan,
+                                             const Task &task, const typename Task::Rows &rs,
+                                             int T, int64_t ld, float *pw, float floor2) {
+    const int sub = 1 << lsub;
+    const int span = R * sub;
     const int tstep = M / span;  // w_span = w_M^tstep
     const int nb = M / R;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int g = b / sub, j = b - g * sub;
+        const int g = b >> lsub, j = b & (sub - 1);
         const int base = g * span + j;
         const int tb = tstep * j;
-        switch (R) {
-            case 16: conv_bfly<16, INV>(s, base, sub, tb, tw); break;
-            case 8: conv_bfly<8, INV>(s, base, sub, tb, tw); break;
-            case 4: conv_bfly<4, INV>(s, base, sub, tb, tw); break;
-            case 3: conv_bfly<3, INV>(s, base, sub, tb, tw); break;
-            default: conv_bfly<2, INV>(s, base, sub, tb, tw); break;
+        float2 a[R];
+        if constexpr (KIND == kDifFirst) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int m = base + r * sub;
+                a[r] = m < T ? task.load(rs, m) : make_float2(0.f, 0.f);
+                *pw = fmaf(a[r].x, a[r].x, fmaf(a[r].y, a[r].y, *pw));
+            }
+            dif_core<R>(a, tb, plan.tw);
+        } else if constexpr (KIND == kDifSmem) {
+            bfly_load<R, false>(s, base, sub, a);
+            dif_core<R>(a, tb, plan.tw);
+        } else if constexpr (KIND == kMidFused) {
+            bfly_load<R, false>(s, base, sub, a);
+            dif_core<R>(a, tb, plan.tw);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                // times -i S, then conjugate for the inverse: conj(-i S v) = (S y, S x)
+                const float S = __ldg(&plan.S[base + q * sub]);
+                a[q] = make_float2(S * a[q].y, S * a[q].x);
+            }
+            dit_core_conj<R>(a, tb, plan.tw);
+        } else {  // kDitSmem, kDitLast
+            bfly_load<R, true>(s, base, sub, a);
+            dit_core_conj<R>(a, tb, plan.tw);
+        }
+        if constexpr (KIND == kDitLast) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int m = base + q * sub;
+                if (m < T) task.finish(rs, m, a[q].x, -a[q].y, floor2);
+                else if (m < ld) task.pad(rs, m);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                float2 v = a[q];
+                if (KIND == kDitSmem || KIND == kMidFused) v.y = -v.y;
+                s[padi(base + q * sub)] = v;
+            }
         }
     }
-    __syncthreads();
 }
 
+template <int KIND, class Task>
+__device__ __forceinline__ void conv_stage(float2 *s, int M, int R, int lsub,
+                                           const ConvPlan &plan, const Task &task,
+                                           const typename Task::Rows &rs, int T, int64_t ld,
+                                           float *pw, float floor2) {
+    switch (R) {
+        case 16: conv_stage_r<16, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
+        case 8: conv_stage_r<8, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
+        case 4: conv_stage_r<4, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
+        case 3: conv_stage_r<3, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
+        default: conv_stage_r<2, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
+    }
+}
+
+__device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
+
 // Same Task interface as k_hilbert_pairs, plus
-//   void pad(int64_t r0, bool v0, int64_t r1, bool v1, int m)
-// for the padding samples T <= m < ld of the output rows.
+//   void pad(const Rows &, int m)
+// for the padding samples T <= m < ld of the output rows.  Stages: the first
+// forward stage reads global memory, the last forward and first inverse
+// stages run fused in registers, the last inverse stage writes the outputs.
 template <class Task>
-__global__ void __launch_bounds__(kConvThreads, 2)
+__global__ void __launch_bounds__(kConvThreads, 1)
 k_hilbert_conv(const Task task, const ConvPlan plan, int T, int64_t ld, int64_t rows) {
     extern __shared__ __align__(16) float2 smem[];
     __shared__ float s_pow;
     const int M = plan.M;
+    const int ns = plan.nstages;
     const int64_t npairs = (rows + 1) / 2;
+    if (threadIdx.x == 0) s_pow = 0.f;
     for (int64_t pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
         const int64_t r0 = 2 * pr, r1 = 2 * pr + 1;
         const bool v0 = r0 < rows, v1 = r1 < rows;
-        __syncthreads();  // the previous pair is done with smem and s_pow
-        if (threadIdx.x == 0) s_pow = 0.f;
-        float pw = 0.f;
-        for (int m = threadIdx.x; m < M; m += blockDim.x) {
-            const float2 c = m < T ? task.load(r0, v0, r1, v1, m) : make_float2(0.f, 0.f);
-            pw = fmaf(c.x, c.x, fmaf(c.y, c.y, pw));
-            smem[padi(m)] = c;
-        }
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) pw += __shfl_xor_sync(0xffffffffu, pw, off);
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s_pow, pw);
-        // forward transform (decimation in frequency)
+        __syncthreads();  // the previous pair is done with smem; s_pow is 0
+        const auto rs = task.rows(r0, v0, r1, v1);
+        // forward stages; span of stage st is M / (radix[0] ... radix[st-1])
         int span = M;
-        for (int st = 0; st < plan.nstages; ++st) {
-            conv_stage<false>(smem, M, plan.radix[st], span, plan.tw);
-            span /= plan.radix[st];
-        }
-        // times K = -i S (already divided by M)
-        for (int p = threadIdx.x; p < M; p += blockDim.x) {
-            const float2 v = smem[padi(p)];
-            const float S = __ldg(&plan.S[p]);
-            smem[padi(p)] = make_float2(S * v.y, -S * v.x);
-        }
-        __syncthreads();
-        // inverse transform (decimation in time, stages in reverse)
-        span = 1;
-        for (int st = plan.nstages - 1; st >= 0; --st) {
-            span *= plan.radix[st];
-            conv_stage<true>(smem, M, plan.radix[st], span, plan.tw);
-        }
-        const float floor2 = 0x1p-40f * (s_pow / (float)T);
-        for (int m = threadIdx.x; m < ld; m += blockDim.x) {
-            if (m < T) {
-                const float2 y = smem[padi(m)];
-                task.finish(r0, v0, r1, v1, m, y.x, y.y, floor2);
-            } else {
-                task.pad(r0, v0, r1, v1, m);
+        float pw = 0.f, floor2 = 0.f;
+        for (int st = 0; st < ns - 1; ++st) {
+            const int R = plan.radix[st];
+            const int lsub = ilog2(span / R);
+            if (st == 0)
+                conv_stage<kDifFirst>(smem, M, R, lsub, plan, task, rs, T, ld, &pw, 0.f);
+            else
+                conv_stage<kDifSmem>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, 0.f);
+            if (st == 0) {
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1)
+                    pw += __shfl_xor_sync(0xffffffffu, pw, off);
+                if ((threadIdx.x & 31) == 0) atomicAdd(&s_pow, pw);
             }
+            __syncthreads();
+            if (st == 0) floor2 = 0x1p-40f * (s_pow / (float)T);
+            span /= R;
+        }
+        // last forward stage (sub = 1), spectrum, first inverse stage
+        conv_stage<kMidFused>(smem, M, plan.radix[ns - 1], 0, plan, task, rs, T, ld, nullptr,
+                              0.f);
+        __syncthreads();
+        if (threadIdx.x == 0) s_pow = 0.f;  // every thread has read it (before the barrier)
+        // remaining inverse stages; the last writes the outputs
+        span = plan.radix[ns - 1];
+        for (int st = ns - 2; st >= 0; --st) {
+            const int R = plan.radix[st];
+            const int lsub = ilog2(span);
+            if (st > 0) {
+                conv_stage<kDitSmem>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, 0.f);
+                __syncthreads();
+            } else {
+                conv_stage<kDitLast>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, floor2);
+            }
+            span *= R;
         }
     }
 }

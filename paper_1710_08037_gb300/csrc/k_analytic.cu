@@ -18,19 +18,42 @@ __device__ __forceinline__ float ldx_f(const Tin *p) {
     return (float)__ldg(p);
 }
 
-// Store one unit phasor of row r (= e * N + n) at sample m in the operand
-// layout: FP32 planar rows, or the tiled split layout (common.cuh) with the
-// component split as hi = RN(p), lo = RN(p - hi).
+// Where row r (= e * N + n) of the operand layout starts: the FP32 planar
+// row (float index), or, for the tiled split layout, the row's element base
+// within its row block plus its swizzle key.
 template <int PREC>
-__device__ __forceinline__ void store_phasor(void *P, int64_t r, int N,
-                                             int64_t ld, int m, float2 p) {
+struct RowAddr {
+    int64_t base;
+    int sw;
+};
+template <int PREC>
+__device__ __forceinline__ RowAddr<PREC> row_addr(int64_t r, int N, int64_t ld) {
+    RowAddr<PREC> a;
     if constexpr (PREC == PLV_PREC_FP32) {
-        float *o = (float *)P + r * 2 * ld + m;
+        a.base = r * 2 * ld;
+        a.sw = 0;
+    } else {
+        const int64_t e = r / N, n = r - e * N;
+        const int64_t rb = n >> 7, rr = n & 127;
+        a.base = (e * row_blocks(N) + rb) * (ld / kTileK) * kBlockElems + rr * kTileK;
+        a.sw = (int)((rr >> 1) & 3);
+    }
+    return a;
+}
+
+// Store one unit phasor at sample m of a row: FP32 planar, or the tiled split
+// layout (common.cuh) with each component split as hi = RN(p), lo = RN(p - hi).
+template <int PREC>
+__device__ __forceinline__ void store_phasor(void *P, const RowAddr<PREC> &ra, int64_t ld,
+                                             int m, float2 p) {
+    if constexpr (PREC == PLV_PREC_FP32) {
+        float *o = (float *)P + ra.base + m;
         o[0] = p.x;
         o[ld] = p.y;
     } else {
-        const int64_t e = r / N, n = r - e * N;
-        const int64_t off = split_offset(e, n, m, row_blocks(N), ld / kTileK);
+        const int k = m & 31;
+        const int64_t off = ra.base + (int64_t)(m >> 5) * kBlockElems +
+                            ((((k >> 3) ^ ra.sw) << 3) | (k & 7));
         constexpr int64_t ps = kTileRows * kTileK;  // plane stride in a block
         if constexpr (PREC == PLV_PREC_FP16X3) {
             __half *o = (__half *)P + off;
@@ -86,19 +109,29 @@ struct FwdTask {
     void *P;
     int N;
     int64_t ld;
-    __device__ float2 load(int64_t r0, bool v0, int64_t r1, bool v1, int m) const {
-        return make_float2(v0 ? ldx_f(x + r0 * ldx + m) : 0.f,
-                           v1 ? ldx_f(x + r1 * ldx + m) : 0.f);
+    struct Rows {
+        const Tin *x0, *x1;  // nullptr for a row past the end
+        RowAddr<PREC> a0, a1;
+    };
+    __device__ Rows rows(int64_t r0, bool v0, int64_t r1, bool v1) const {
+        Rows rs;
+        rs.x0 = v0 ? x + r0 * ldx : nullptr;
+        rs.x1 = v1 ? x + r1 * ldx : nullptr;
+        rs.a0 = row_addr<PREC>(v0 ? r0 : 0, N, ld);
+        rs.a1 = row_addr<PREC>(v1 ? r1 : 0, N, ld);
+        return rs;
     }
-    __device__ void finish(int64_t r0, bool v0, int64_t r1, bool v1, int m, float h0,
-                           float h1, float floor2) const {
-        if (v0) store_phasor<PREC>(P, r0, N, ld, m, unit_phasor(ldx_f(x + r0 * ldx + m), h0, floor2));
-        if (v1) store_phasor<PREC>(P, r1, N, ld, m, unit_phasor(ldx_f(x + r1 * ldx + m), h1, floor2));
+    __device__ float2 load(const Rows &rs, int m) const {
+        return make_float2(rs.x0 ? ldx_f(rs.x0 + m) : 0.f, rs.x1 ? ldx_f(rs.x1 + m) : 0.f);
+    }
+    __device__ void finish(const Rows &rs, int m, float h0, float h1, float floor2) const {
+        if (rs.x0) store_phasor<PREC>(P, rs.a0, ld, m, unit_phasor(ldx_f(rs.x0 + m), h0, floor2));
+        if (rs.x1) store_phasor<PREC>(P, rs.a1, ld, m, unit_phasor(ldx_f(rs.x1 + m), h1, floor2));
     }
     // padding samples T <= m < ld are zero
-    __device__ void pad(int64_t r0, bool v0, int64_t r1, bool v1, int m) const {
-        if (v0) store_phasor<PREC>(P, r0, N, ld, m, make_float2(0.f, 0.f));
-        if (v1) store_phasor<PREC>(P, r1, N, ld, m, make_float2(0.f, 0.f));
+    __device__ void pad(const Rows &rs, int m) const {
+        if (rs.x0) store_phasor<PREC>(P, rs.a0, ld, m, make_float2(0.f, 0.f));
+        if (rs.x1) store_phasor<PREC>(P, rs.a1, ld, m, make_float2(0.f, 0.f));
     }
 };
 
@@ -112,32 +145,38 @@ struct PrepTask {
     float *P;
     float *rinv;
     int64_t ld;
-    __device__ void one(int64_t r, int m, float h, float floor2) const {
-        const float a = ldx_f(x + r * ldx + m);
+    struct Rows {
+        const Tin *x0, *x1;
+        float *p0, *p1, *q0, *q1;  // phasor rows, reciprocal-amplitude rows
+    };
+    __device__ Rows rows(int64_t r0, bool v0, int64_t r1, bool v1) const {
+        Rows rs;
+        rs.x0 = v0 ? x + r0 * ldx : nullptr;
+        rs.x1 = v1 ? x + r1 * ldx : nullptr;
+        rs.p0 = P + (v0 ? r0 : 0) * 2 * ld;
+        rs.p1 = P + (v1 ? r1 : 0) * 2 * ld;
+        rs.q0 = rinv + (v0 ? r0 : 0) * ld;
+        rs.q1 = rinv + (v1 ? r1 : 0) * ld;
+        return rs;
+    }
+    __device__ void one(const Tin *xr, float *pr, float *qr, int m, float h,
+                        float floor2) const {
         float ri;
-        const float2 p = unit_phasor_inv(a, h, floor2, ri);
-        float *o = P + r * 2 * ld + m;
-        o[0] = p.x;
-        o[ld] = p.y;
-        rinv[r * ld + m] = ri;
+        const float2 p = unit_phasor_inv(ldx_f(xr + m), h, floor2, ri);
+        pr[m] = p.x;
+        pr[ld + m] = p.y;
+        qr[m] = ri;
     }
-    __device__ float2 load(int64_t r0, bool v0, int64_t r1, bool v1, int m) const {
-        return make_float2(v0 ? ldx_f(x + r0 * ldx + m) : 0.f,
-                           v1 ? ldx_f(x + r1 * ldx + m) : 0.f);
+    __device__ float2 load(const Rows &rs, int m) const {
+        return make_float2(rs.x0 ? ldx_f(rs.x0 + m) : 0.f, rs.x1 ? ldx_f(rs.x1 + m) : 0.f);
     }
-    __device__ void finish(int64_t r0, bool v0, int64_t r1, bool v1, int m, float h0,
-                           float h1, float floor2) const {
-        if (v0) one(r0, m, h0, floor2);
-        if (v1) one(r1, m, h1, floor2);
+    __device__ void finish(const Rows &rs, int m, float h0, float h1, float floor2) const {
+        if (rs.x0) one(rs.x0, rs.p0, rs.q0, m, h0, floor2);
+        if (rs.x1) one(rs.x1, rs.p1, rs.q1, m, h1, floor2);
     }
-    __device__ void pad(int64_t r0, bool v0, int64_t r1, bool v1, int m) const {
-        for (int h = 0; h < 2; ++h) {
-            const int64_t r = h ? r1 : r0;
-            if (!(h ? v1 : v0)) continue;
-            P[r * 2 * ld + m] = 0.f;
-            P[r * 2 * ld + ld + m] = 0.f;
-            rinv[r * ld + m] = 0.f;
-        }
+    __device__ void pad(const Rows &rs, int m) const {
+        if (rs.x0) { rs.p0[m] = 0.f; rs.p0[ld + m] = 0.f; rs.q0[m] = 0.f; }
+        if (rs.x1) { rs.p1[m] = 0.f; rs.p1[ld + m] = 0.f; rs.q1[m] = 0.f; }
     }
 };
 
@@ -160,7 +199,7 @@ __global__ void k_normalize(const Tc *__restrict__ z, int64_t rows, int N,
         const Tc v = z[r * ldz + m];
         p = unit_phasor((float)v.x, (float)v.y);
     }
-    store_phasor<PREC>(P, r, N, ld, (int)m, p);
+    store_phasor<PREC>(P, row_addr<PREC>(r, N, ld), ld, (int)m, p);
 }
 
 }  // namespace

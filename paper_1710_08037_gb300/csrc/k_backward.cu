@@ -200,31 +200,41 @@ struct BwdTask {
     float *grad;        // [rows][T]
     int64_t ld;
     int T;
-    __device__ float s_of(int64_t r, int m, float &pr, float &pi) const {
-        const float *p = P + r * 2 * ld + m;
-        const float *g = Gm + r * 2 * ld + m;
-        pr = p[0];
-        pi = p[ld];
-        const float gr = g[0], gi = g[ld];
-        return fmaf(pr, gi, -pi * gr) * rinv[r * ld + m];
+    struct Row {
+        const float *p, *g, *q;
+        float *o;
+    };
+    struct Rows {
+        Row a, b;
+        bool v0, v1;
+    };
+    __device__ Row row(int64_t r) const {
+        return Row{P + r * 2 * ld, Gm + r * 2 * ld, rinv + r * ld, grad + r * T};
     }
-    __device__ float2 load(int64_t r0, bool v0, int64_t r1, bool v1, int m) const {
+    __device__ Rows rows(int64_t r0, bool v0, int64_t r1, bool v1) const {
+        return Rows{row(v0 ? r0 : 0), row(v1 ? r1 : 0), v0, v1};
+    }
+    __device__ float s_of(const Row &w, int m, float &pr, float &pi) const {
+        pr = w.p[m];
+        pi = w.p[ld + m];
+        return fmaf(pr, w.g[ld + m], -pi * w.g[m]) * w.q[m];
+    }
+    __device__ float2 load(const Rows &rs, int m) const {
         float pr, pi, a = 0.f, b = 0.f;
-        if (v0) a = s_of(r0, m, pr, pi) * pr;
-        if (v1) b = s_of(r1, m, pr, pi) * pr;
+        if (rs.v0) a = s_of(rs.a, m, pr, pi) * pr;
+        if (rs.v1) b = s_of(rs.b, m, pr, pi) * pr;
         return make_float2(a, b);
     }
-    __device__ void pad(int64_t, bool, int64_t, bool, int) const {}  // grad has no padding
-    __device__ void finish(int64_t r0, bool v0, int64_t r1, bool v1, int m, float h0,
-                           float h1, float) const {
+    __device__ void pad(const Rows &, int) const {}  // grad has no padding
+    __device__ void finish(const Rows &rs, int m, float h0, float h1, float) const {
         float pr, pi;
-        if (v0) {
-            const float s = s_of(r0, m, pr, pi);
-            grad[r0 * T + m] = -pi * s - h0;
+        if (rs.v0) {
+            const float s = s_of(rs.a, m, pr, pi);
+            rs.a.o[m] = -pi * s - h0;
         }
-        if (v1) {
-            const float s = s_of(r1, m, pr, pi);
-            grad[r1 * T + m] = -pi * s - h1;
+        if (rs.v1) {
+            const float s = s_of(rs.b, m, pr, pi);
+            rs.b.o[m] = -pi * s - h1;
         }
     }
 };
