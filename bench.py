@@ -119,9 +119,10 @@ class ClockSampler:
 # DRAM traffic per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel build,
 # workload and precision.  Captured on the 4-epoch case and scaled to the
-# launch by epochs (profiles/k_gram_tc_and_k_analytic_bandlimited-N4096-T4096-E4.md).
+# launch by epochs (profiles/k_gram_tc_and_k_hilbert_pairs_bandlimited-N4096-T4096-E4.md).
 # An entry is removed when the kernel changes after its capture.
 TRAFFIC = {
+    ("k_gram_tc", "bandlimited-N4096-T4096-E30", "bf16x3"): (1.902304e9 + 1.010694e9) * 30 / 4,
 }
 
 

@@ -14,7 +14,8 @@
 //
 // Accumulation.  The tensor core's FP32 accumulation into TMEM does not
 // round to nearest, and its error grows with the number of K blocks added
-// into one accumulator.  So the K loop runs in chunks of CH_SAMPLES samples:
+// into one accumulator.  So the K loop runs in chunks (256 samples for BF16,
+// 128 for FP16):
 // each chunk accumulates into a fresh TMEM region (two regions, ping-pong),
 // and the epilogue warps drain every finished chunk into FP32 running sums
 // in registers (round to nearest), as a two-level summation.
@@ -59,7 +60,14 @@ constexpr int NEPI_WARPS = 16;               // 4 lane quarters x 4 column quart
 constexpr int NTHREADS = 64 + 32 * NEPI_WARPS;
 constexpr int TMEM_COLS = 512;
 constexpr int ACC_COLS = 256;                 // Re (128) + Im (128)
-constexpr int CH = 4;                         // stages per K chunk (128 samples)
+// Stages per K chunk, by split: BF16x3 drains every 256 samples, FP16x3 every
+// 128.  Longer chunks leave the MMAs more slack over the tile-end stores but
+// add accumulation error in proportion (about 5.6e-6 against 2.8e-6 at worst,
+// for a coherent pair); the FP16 split is the accuracy-first mode.
+template <uint32_t FMT>
+struct Chunk {
+    static constexpr int CH = FMT == 1u ? 8 : 4;
+};
 constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s bound on any wait
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align*/ + 256;
 
@@ -324,7 +332,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                 const TcProblem &pb = item_of(args, t, e, I, J);
                 const bool diag = I == J;
                 const int nkb = pb.nkb;
-                for (int kb0 = 0; ok && kb0 < nkb; kb0 += CH) {
+                for (int kb0 = 0; ok && kb0 < nkb; kb0 += Chunk<FMT>::CH) {
                     if (!wait_bar(TEMPTY(buf), buf_phase ^ 1u, abort_flag, args.status)) {
                         ok = false;
                         break;
@@ -332,7 +340,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     tc_fence_after();
                     const uint32_t d_re = tmem + buf * ACC_COLS;
                     const uint32_t d_im = d_re + TN;
-                    const int kb1 = kb0 + CH < nkb ? kb0 + CH : nkb;
+                    const int kb1 = kb0 + Chunk<FMT>::CH < nkb ? kb0 + Chunk<FMT>::CH : nkb;
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!wait_bar(FULL(stage), phase, abort_flag, args.status)) {
                             ok = false;
@@ -402,7 +410,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             float sre[32], sim[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
-            for (int kb0 = 0; kb0 < pb.nkb; kb0 += CH) {
+            for (int kb0 = 0; kb0 < pb.nkb; kb0 += Chunk<FMT>::CH) {
                 if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status)) {
                     ok = false;
                     break;
