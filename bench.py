@@ -45,6 +45,9 @@ DEFAULT_WORKLOAD = "bandlimited-N4096-T4096-E30"
 # uneven batch: 256 subjects, N ~ U{68..2000}, T ~ U{500..10000} per subject,
 # 5 frequency bands each (1280 problems of one epoch), fs = 1000 Hz
 GROUPED = "grouped-256subj-5bands-N68to2000-T500to10000"
+# differentiable loss: 16 recordings, N = 1024, T = 4096, loss = sum of ciPLV
+# over a seeded 10 % pair mask; forward + hand-written backward per step
+BACKWARD = "backward-ciplv-loss-B16-N1024-T4096"
 BANDS = [(4.0, 8.0), (8.0, 12.0), (13.0, 30.0), (30.0, 45.0), (55.0, 80.0)]
 
 
@@ -206,33 +209,50 @@ def run_ours(args):
     value = units * world / (ms_step / 1e3)
     device_status = h.plv_sync_status()
 
-    # end to end through the C ABI: host x -> device, path, outputs -> host
+    # end to end through the C ABI: host x -> device, path, outputs -> host.
+    # The epochs go in chunks on two streams, so one chunk's copies overlap
+    # another chunk's kernels (every byte still crosses inside the timed
+    # region, every step).
     e2e = None
     if not args.no_e2e:
         xh = x.cpu().pin_memory()
         oh = {k: torch.empty((E, N, N), dtype=torch.float32).pin_memory()
               for k in out}
         xd = torch.empty_like(x)
+        nch = max(1, min(E, args.e2e_chunks))
+        bounds = [(E * c // nch, E * (c + 1) // nch) for c in range(nch)]
+        streams = [torch.cuda.Stream(dev) for _ in range(2)]
+        Ps = [h.empty_phasors(max(b - a for a, b in bounds), N, T) for _ in streams]
 
         def e2e_step():
-            xd.copy_(xh, non_blocking=True)
-            h.plv_analytic(xd, P)
-            h.plv_gram(P, E, N, T, out=out)
-            for k in out:
-                oh[k].copy_(out[k], non_blocking=True)
+            for c, (a, b) in enumerate(bounds):
+                k = c % 2
+                with torch.cuda.stream(streams[k]):
+                    xd[a:b].copy_(xh[a:b], non_blocking=True)
+                    h.plv_analytic(xd[a:b], Ps[k])
+                    h.plv_gram(Ps[k], b - a, N, T,
+                               out={kk: v[a:b] for kk, v in out.items()})
+                    for kk in out:
+                        oh[kk][a:b].copy_(out[kk][a:b], non_blocking=True)
+            for st_ in streams:
+                s.wait_stream(st_)
 
         for _ in range(max(1, min(args.warmup, 2))):
             e2e_step()
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
-        a, b = ev(), ev()
-        a.record(s)
+        a_, b_ = ev(), ev()
+        a_.record(s)
+        for st_ in streams:
+            st_.wait_stream(s)
         for _ in range(args.steps):
             e2e_step()
-        b.record(s)
+            for st_ in streams:
+                st_.wait_stream(s)
+        b_.record(s)
         torch.cuda.synchronize(dev)
-        ems = a.elapsed_time(b)
+        ems = a_.elapsed_time(b_)
         if dist:
             tt = torch.tensor([ems], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -240,7 +260,8 @@ def run_ours(args):
         e2e = {"value": units * world / (ems / args.steps / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(x.numel() * x.element_size()),
                "d2h_bytes_per_step": int(sum(v.numel() * 4 for v in out.values())),
-               "ms_per_step": ems / args.steps}
+               "ms_per_step": ems / args.steps,
+               "pipeline": f"{nch} epoch chunks on 2 streams"}
 
     # the plain FP32 path on the same input: time and agreement
     fp32 = None
@@ -458,6 +479,101 @@ def run_grouped(args):
         dist.destroy_process_group()
 
 
+def run_backward(args):
+    """Forward (analytic signal, Gram with C) and backward (recompute,
+    S = G + G^H, Gamma = S P / T, adjoint Hilbert) of the masked ciPLV loss."""
+    import torch
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    B, N, T = 16, 1024, 4096
+    hf = plv.Handle(precision=args.precision, device=local)
+    hb = plv.Handle(precision="fp32", device=local)
+    x = synth.bandlimited(B, N, T, seed=1005 + rank, device=dev)
+    mask = synth.random_pair_mask(N, 0.10, seed=1005, device=dev)
+    g3 = mask.to(torch.float32).expand(B, N, N).contiguous()
+    P = hf.empty_phasors(B, N, T)
+    out = {k: torch.empty((B, N, N), dtype=torch.float32, device=dev)
+           for k in ("ciplv",)}
+    out["C"] = torch.empty((B, N, N), dtype=torch.complex64, device=dev)
+    grad = torch.empty((B, N, T), dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(e=None):
+        if e:
+            e[0].record(s)
+        hf.plv_analytic(x, P)
+        hf.plv_gram(P, B, N, T, plv=False, iplv=False, ciplv=True, C=True,
+                    out=out)
+        if e:
+            e[1].record(s)
+        hb.plv_backward(x, out["C"], None, None, g3, grad_x=grad)
+        if e:
+            e[2].record(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    per = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    for p in per:
+        step(p)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = sum(p[0].elapsed_time(p[2]) for p in per)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    fwd_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
+    bwd_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
+    ms_step = ms / args.steps
+    units = float(N) * N * T * B
+    value = units * world / (ms_step / 1e3)
+    ld = (T + 31) // 32 * 32
+    gemm_flops = 8.0 * N * N * ld * B
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"forward {args.precision}, backward f32",
+            "data": "synthetic",
+            "config": {"workload": BACKWARD, "B": B, "N": N, "T": T,
+                       "loss": "sum of ciPLV over a seeded 10% mask of ordered "
+                               "pairs", "recompute": "analytic signal "
+                       "recomputed in the backward pass"},
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "backward_gemm": {"flops_per_launch": gemm_flops,
+                              "note": "Gamma = S P / T, FP32 on the CUDA "
+                                      "cores; the roofline is the FP32 ALU "
+                                      "peak (%s)" % peak_kind,
+                              "peak_tflops": peak},
+            "gpu_launches": 6 * args.steps, "clocks": clk,
+            "device_status": hb.plv_sync_status()}
+        print(json.dumps(line), flush=True)
+    hf.close()
+    hb.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(E, N, T, seed, nsub):
     """The FP64 oracle as it stands, on a bounded sample of the same
     workload: one epoch, a random subset S of ``nsub`` channels; direct-DFT
@@ -529,7 +645,7 @@ def main():
                     default="bf16x3")
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the split one")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED, BACKWARD],
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--subjects", type=int, default=256,
                     help="subjects of the grouped workload")
@@ -538,6 +654,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=384)
+    ap.add_argument("--e2e-chunks", type=int, default=6)
     ap.add_argument("--ref-sample", type=int, default=192)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -546,6 +663,8 @@ def main():
         run_reference(args)
     elif args.workload == GROUPED:
         run_grouped(args)
+    elif args.workload == BACKWARD:
+        run_backward(args)
     else:
         run_ours(args)
 
