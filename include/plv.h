@@ -160,25 +160,34 @@ plv_status plv_gram(plv_handle *h, void *stream, const void *P, int batch,
                     int N, int T, unsigned out_mask, float *plv, float *iplv,
                     float *ciplv, void *C, double *diag_dev);
 
-/* One problem of a grouped Gram: phasors written by plv_analytic /
- * plv_normalize of the same handle for (batch, N, T), and its outputs
- * (layouts as in plv_gram; NULL outputs are skipped). */
+/* One problem of a grouped plan: its phasors P for (batch, N, T) in the
+ * handle's operand layout, its Gram outputs (layouts as in plv_gram; NULL
+ * outputs are skipped) and, optionally, its real input x for
+ * plv_analytic_grouped.  With x NULL the phasors are written by the caller
+ * (plv_analytic / plv_normalize of the same handle). */
 typedef struct {
-    const void *P;
+    void *P;
     int batch, N, T;
     float *plv, *iplv, *ciplv;
     void *C;          /* complex64 [batch][N][N] */
     double *diag;     /* [batch] */
+    const void *x;    /* real [batch][N][ldx] or NULL */
+    int64_t ldx;      /* row stride of x in elements, >= T */
+    plv_dtype dtype;  /* PLV_F32 or PLV_F64; one dtype for every x of a plan */
 } plv_problem;
 
 typedef struct plv_group plv_group;
 
-/* Plan a grouped Gram over `nprob` problems of uneven N and T (Section IV:
+/* Plan a grouped run over `nprob` problems of uneven N and T (Section IV:
  * many subjects, epochs and frequency bands): uploads the problem
  * descriptors and the list of every (problem, epoch, upper-triangle tile),
- * sorted longest first (by T), to the device.  Allocates: call outside
- * stream capture.  out_mask selects outputs as in plv_gram.  The pointers in
- * `probs` are captured: the plan runs on those buffers. */
+ * sorted longest first (by T), to the device; for the problems with an
+ * input x also the list of every (problem, row pair) of the analytic-signal
+ * engine, and, for the split precisions, zeroes the padding rows of their P
+ * once (no call writes them later).  Allocates and synchronises the device:
+ * call outside stream capture.  out_mask selects outputs as in plv_gram.
+ * The pointers in `probs` are captured: the plan runs on those buffers.  The
+ * plan uses tables owned by the handle and must not outlive it. */
 plv_status plv_group_create(plv_handle *h, const plv_problem *probs, int nprob,
                             unsigned out_mask, plv_group **group);
 
@@ -187,6 +196,16 @@ plv_status plv_group_create(plv_handle *h, const plv_problem *probs, int nprob,
  * tiles round-robin, longest first); an FP32 handle runs one Gram launch per
  * problem.  Allocates nothing: can be captured in a CUDA graph. */
 plv_status plv_gram_grouped(plv_handle *h, void *stream, const plv_group *group);
+
+/* Eq. 3 and 4 for every problem of a plan that has an input x: the
+ * analytic signal by the any-length engine of plv_analytic (also for
+ * power-of-two T, whose results may then differ from plv_analytic's in the
+ * last bits) fused with the unit-phasor normalisation, written to the
+ * problem's P.  One persistent launch per thread class of the engine (at most
+ * four), each over all (problem, row pair) of the class, longest transform
+ * first.  Allocates nothing: can be captured in a CUDA graph.  Fails with
+ * PLV_ERR_INVALID if the plan has no input. */
+plv_status plv_analytic_grouped(plv_handle *h, void *stream, const plv_group *group);
 
 /* Free a plan (synchronises the device).  NULL is ignored. */
 plv_status plv_group_destroy(plv_group *group);

@@ -178,9 +178,11 @@ class Handle:
 
     def plv_group_create(self, problems, plv=True, iplv=True, ciplv=True,
                          C=False, diag=False):
-        """Plan a grouped Gram.  `problems`: list of dicts with keys P,
-        batch, N, T and output tensors (plv, iplv, ciplv, C, diag); missing
-        outputs are allocated here.  Returns a Group (keeps the tensors)."""
+        """Plan a grouped run.  `problems`: list of dicts with keys P,
+        batch, N, T, optionally the input x (batch, N, T) for
+        plv_analytic_grouped, and output tensors (plv, iplv, ciplv, C, diag);
+        missing outputs are allocated here.  Returns a Group (keeps the
+        tensors)."""
         mask = ((PLV_OUT_PLV if plv else 0) | (PLV_OUT_IPLV if iplv else 0) |
                 (PLV_OUT_CIPLV if ciplv else 0) | (PLV_OUT_C if C else 0))
         arr = (_lib.PlvProblem * len(problems))()
@@ -194,18 +196,35 @@ class Handle:
                                          ("diag", diag, (B,), torch.float64)):
                 if want and key not in q:
                     q[key] = torch.empty(shape, dtype=dt, device=self.device)
+            x = q.get("x")
+            xptr, ldx, xdt = None, 0, 0
+            if x is not None:
+                assert x.is_cuda and x.dim() == 3 and x.shape == (B, N, q["T"])
+                if not (x.stride(-1) == 1 and
+                        (N == 1 or x.stride(0) == N * x.stride(1))):
+                    x = q["x"] = x.contiguous()
+                xptr = x.data_ptr()
+                ldx = x.stride(1) if N > 1 else max(x.stride(0), q["T"])
+                xdt = _dtype_code(x)
             arr[k] = _lib.PlvProblem(
                 q["P"].data_ptr(), B, N, q["T"],
                 q["plv"].data_ptr() if plv else None,
                 q["iplv"].data_ptr() if iplv else None,
                 q["ciplv"].data_ptr() if ciplv else None,
                 q["C"].data_ptr() if C else None,
-                q["diag"].data_ptr() if diag else None)
+                q["diag"].data_ptr() if diag else None,
+                xptr, ldx, xdt)
             keep.append(q)
         g = ctypes.c_void_p()
         _lib.check(self.lib.plv_group_create(self.h, arr, len(problems), mask,
                                              ctypes.byref(g)), self.h)
         return Group(self, g, keep)
+
+    def plv_analytic_grouped(self, group):
+        """Eq. 3 + 4 for every problem of the plan that has an input x."""
+        _lib.check(self.lib.plv_analytic_grouped(self.h, _stream(self.device),
+                                                 group.g), self.h)
+        return group.problems
 
     def plv_gram_grouped(self, group):
         _lib.check(self.lib.plv_gram_grouped(self.h, _stream(self.device),

@@ -59,6 +59,7 @@ SIGNATURES = {
                                   _vp, _vp, _vp]),
     "plv_group_create": (_i, [_vp, _vp, _i, _u, ctypes.POINTER(_vp)]),
     "plv_gram_grouped": (_i, [_vp, _vp, _vp]),
+    "plv_analytic_grouped": (_i, [_vp, _vp, _vp]),
     "plv_group_destroy": (_i, [_vp]),
     "plv_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
 }
@@ -109,4 +110,5 @@ class PlvProblem(ctypes.Structure):
                 ("N", ctypes.c_int), ("T", ctypes.c_int),
                 ("plv", ctypes.c_void_p), ("iplv", ctypes.c_void_p),
                 ("ciplv", ctypes.c_void_p), ("C", ctypes.c_void_p),
-                ("diag", ctypes.c_void_p)]
+                ("diag", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("ldx", ctypes.c_int64), ("dtype", ctypes.c_int)]

@@ -1,6 +1,7 @@
 """Build the CUDA library in-tree: csrc/*.cu -> _build/libplv.so (sm_103a).
 
-Each translation unit is compiled in parallel by nvcc, then linked into one
+Each translation unit (and each variant of a multiply-compiled one) is
+compiled in parallel by nvcc, then linked into one
 shared library exporting the C ABI of include/plv.h.  No cmake, no torch
 extension machinery: the library has no torch types in it.
 """
@@ -32,12 +33,27 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+# Sources compiled more than once, with different -D flags (object suffix,
+# flags): k_fwd.cu holds the K1 launchers of one (input type, task kind).
+VARIANTS = {
+    "k_fwd.cu": [(f"_{t}_{k}", [f"-DPLV_K1_F64={f64}", f"-DPLV_K1_KIND={k}"])
+                 for f64, t in ((0, "f32"), (1, "f64")) for k in range(4)],
+}
+
+
+def _units():
+    """(source, object, extra flags) of every compiler run."""
+    out = []
+    for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
+        name = os.path.basename(src)[:-3]
+        for suffix, flags in VARIANTS.get(os.path.basename(src), [("", [])]):
+            out.append((src, os.path.join(BUILD, name + suffix + ".o"), flags))
+    return out
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu"))) + sorted(
+        glob.glob(os.path.join(CSRC, "*.cuh"))) + [
         os.path.join(ROOT, "include", "plv.h"), __file__]
 
 
@@ -54,11 +70,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    srcs = _sources()
+    units = _units()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *NVFLAGS, *extra, "-c", src, "-o", obj]
+    def compile_one(unit):
+        src, obj, flags = unit
+        cmd = [nvcc, *NVFLAGS, *flags, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,8 +84,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    workers = max(1, min(len(units), os.cpu_count() or 8, 16))
+    # longest first: the K1 variants, then the rest
+    order = sorted(units, key=lambda u: 0 if u[2] else 1)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(compile_one, order))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -64,6 +64,15 @@ struct ConvPlan {
     const float *S;
 };
 constexpr int kMaxConvM = 24576;  // 3 * 2^13: T up to 12288
+// Threads per CTA of the any-length engine for transform length M: as many
+// CTAs per SM as the shared buffer allows (each CTA is its own barrier
+// domain), with the SM's 512 threads of 128 registers split among them.
+__host__ __device__ constexpr int conv_threads(int M) {
+    return M <= 3072 ? 64 : M <= 6144 ? 128 : M <= 12288 ? 256 : 512;
+}
+__host__ __device__ constexpr size_t conv_smem(int M) {
+    return (size_t)(M + M / 32) * sizeof(float2);
+}
 
 struct Handle {
     int device = 0;
@@ -118,6 +127,29 @@ void free_conv_plans(Handle &h);
 cudaError_t launch_analytic_conv(const Handle *h, cudaStream_t s, const void *x,
                                  plv_dtype dt, int64_t rows, int N, int T, int64_t ldx,
                                  void *P, const ConvPlan &plan);
+
+// One problem of a grouped K1 launch (device descriptor; words copied to
+// shared memory by the kernel, so the size is a multiple of 4 bytes).
+struct K1Desc {
+    const void *x;
+    void *P;
+    int64_t ldx, ld, rows;  // x row stride, phasor row length, batch * N
+    int N, T;
+    ConvPlan plan;
+};
+// Thread-count classes of the any-length engine (fft::conv_threads).
+constexpr int kConvClasses = 4;
+// A grouped K1 plan: every (problem, row pair) of the group, in class order
+// (64, 128, 256, 512 threads) and within a class by decreasing M.
+struct K1Group {
+    const K1Desc *descs;     // device
+    const int2 *items;       // device: (problem, row pair)
+    int64_t begin[kConvClasses], count[kConvClasses];
+    int max_M[kConvClasses];
+};
+// K1 of every problem of a group: one persistent launch per non-empty class.
+cudaError_t launch_analytic_group(const Handle *h, cudaStream_t s, plv_dtype dt,
+                                  const K1Group &g);
 
 // Per-thread last error message.
 void set_error(const char *fmt, ...);

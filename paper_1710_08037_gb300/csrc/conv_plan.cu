@@ -25,19 +25,46 @@ int choose_M(int T) {
     return best;
 }
 
-// radix order: 3 first for 3 * 2^a, then 16s, then the remaining power of two
+// Radix order of the transform: 3 first for M = 3 * 2^a (every later span is
+// then a power of two), then radix-16 stages and one remainder radix
+// 2^(a mod 4).  The remainder goes where it leaves the fewest twiddle loads
+// on the device: a stage whose sub-block length (span / R) exceeds the CTA's
+// thread count loads its R - 1 twiddles per butterfly, a later one loads
+// them once per thread; the last forward stage has none.
 std::vector<int> schedule(int M) {
-    std::vector<int> r;
+    std::vector<int> head;
     int m = M;
     if (m % 3 == 0) {
-        r.push_back(3);
+        head.push_back(3);
         m /= 3;
     }
     int a = 0;
     while ((1 << a) < m) ++a;
-    for (int k = 0; k < a / 4; ++k) r.push_back(16);
-    if (a % 4) r.push_back(1 << (a % 4));
-    return r;
+    const int n16 = a / 4, rem = 1 << (a % 4);
+    const int threads = conv_threads(M);
+    std::vector<int> best;
+    double best_cost = 0.0;
+    for (int pos = 0; pos <= n16; ++pos) {
+        std::vector<int> r = head;
+        for (int k = 0; k < n16; ++k) {
+            if (k == pos && rem > 1) r.push_back(rem);
+            r.push_back(16);
+        }
+        if (pos == n16 && rem > 1) r.push_back(rem);
+        double cost = 0.0;
+        int span = M;
+        for (size_t st = 0; st < r.size(); ++st) {
+            const int sub = span / r[st];
+            if (st + 1 < r.size() && sub > threads) cost += (double)(r[st] - 1) / r[st];
+            span = sub;
+        }
+        if (best.empty() || cost < best_cost) {
+            best = r;
+            best_cost = cost;
+        }
+        if (rem == 1) break;  // no remainder to place
+    }
+    return best;
 }
 
 // In-place decimation-in-frequency FFT with the device's loop structure.

@@ -308,7 +308,6 @@ cudaError_t launch_hilbert_pow2(int num_sms, cudaStream_t st, int log2T, const T
         case 11: return launch_hilbert_pairs<11>(num_sms, st, task, tw, rows);
         case 12: return launch_hilbert_pairs<12>(num_sms, st, task, tw, rows);
         case 13: return launch_hilbert_pairs<13>(num_sms, st, task, tw, rows);
-        case 14: return launch_hilbert_pairs<14>(num_sms, st, task, tw, rows);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -328,8 +327,6 @@ cudaError_t launch_hilbert_pow2(int num_sms, cudaStream_t st, int log2T, const T
 // natural output), so no reordering pass is needed.  M = 2^a or 3 * 2^a.
 // One sequence (row pair) per CTA; every thread loops over butterflies with
 // only R values in registers, so the shared buffer is single.
-
-constexpr int kConvThreads = 512;
 
 __device__ __forceinline__ void dft3(float2 (&a)[3]) {
     const float h = 0.86602540378443864676f;  // sqrt(3) / 2
@@ -357,39 +354,109 @@ __device__ __forceinline__ void bfly_load(const float2 *s, int base, int sub, fl
         if (INV) a[r].y = -a[r].y;
     }
 }
-template <int R>
-__device__ __forceinline__ void twiddle_r(float2 (&a)[R], int tb, const float2 *__restrict__ tw) {
-    if (tb != 0) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&tw[r * tb]));
-    }
-}
-// Decimation-in-frequency butterfly on registers (span = R sub, position j
-// in the sub-block): V = DFT_R(v); V[q] *= w_span^(q j).
-template <int R>
-__device__ __forceinline__ void dif_core(float2 (&a)[R], int tb, const float2 *tw) {
-    dft_any<R>(a);
-    twiddle_r<R>(a, tb, tw);
-}
-// Matching decimation-in-time inverse on conjugated registers: conj(v) has
-// been loaded; v[r] conj(w)^(r j) then IDFT_R is conj(DFT_R(conj(v) w^(r j))).
-template <int R>
-__device__ __forceinline__ void dit_core_conj(float2 (&a)[R], int tb, const float2 *tw) {
-    twiddle_r<R>(a, tb, tw);
-    dft_any<R>(a);
-}
-
 // Stage kinds of the any-length transform.
 enum ConvStage { kDifSmem = 0, kDitSmem = 1, kDifFirst = 2, kMidFused = 3, kDitLast = 4 };
 
-// One stage over all butterflies.  span = R sub with sub = 1 << lsub.
+// The R - 1 twiddles w[r] = tw[r tb] of one butterfly position (w[0] = 1).
+template <int R>
+__device__ __forceinline__ void load_twiddles(float2 (&w)[R], int tb,
+                                              const float2 *__restrict__ tw) {
+    w[0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r] = __ldg(&tw[r * tb]);
+}
+template <int R>
+__device__ __forceinline__ void apply_twiddles(float2 (&a)[R], const float2 (&w)[R]) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[r]);
+}
+template <int R>
+__device__ __forceinline__ void apply_twiddles_mem(float2 (&a)[R], int tb,
+                                                  const float2 *__restrict__ tw) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) a[r] = cmul(a[r], __ldg(&tw[r * tb]));
+}
+
+// One butterfly of a stage: base = g span + j, twiddles w of position j.
 //   kDifFirst: inputs c[m] = task.load (0 for m >= T) straight from global
 //              memory, sums |c|^2 into *pw;
 //   kDifSmem / kDitSmem: shared memory in place;
 //   kMidFused: the last forward stage, the multiply by K = -i S / M and the
-//              first inverse stage, all in registers (same butterflies, sub = 1);
+//              first inverse stage, all in registers (same butterflies, sub = 1,
+//              so j = 0 and no twiddles);
 //   kDitLast:  the last inverse stage; outputs m < T go to task.finish, the
 //              padding T <= m < ld to task.pad.
+template <int R, int KIND, bool HOIST, class Task>
+__device__ __forceinline__ void conv_butterfly(float2 *s, int base, int sub, int tb,
+                                               const float2 (&w)[R], const ConvPlan &plan,
+                                               const Task &task,
+                                               const typename Task::Rows &rs, int T,
+                                               int64_t ld, float *pw, float floor2) {
+    float2 a[R];
+    if constexpr (KIND == kDifFirst) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int m = base + r * sub;
+            a[r] = m < T ? task.load(rs, m) : make_float2(0.f, 0.f);
+            *pw = fmaf(a[r].x, a[r].x, fmaf(a[r].y, a[r].y, *pw));
+        }
+        dft_any<R>(a);
+        if constexpr (HOIST) apply_twiddles<R>(a, w);
+        else if (tb != 0) apply_twiddles_mem<R>(a, tb, plan.tw);
+    } else if constexpr (KIND == kDifSmem) {
+        bfly_load<R, false>(s, base, sub, a);
+        dft_any<R>(a);
+        if constexpr (HOIST) apply_twiddles<R>(a, w);
+        else if (tb != 0) apply_twiddles_mem<R>(a, tb, plan.tw);
+    } else if constexpr (KIND == kMidFused) {
+        bfly_load<R, false>(s, base, sub, a);
+        dft_any<R>(a);
+        // times -i S, then conjugate for the inverse: conj(-i S v) = (S y, S x)
+        float S[R];
+        if constexpr (R % 4 == 0) {
+            // base = g R: 16-byte aligned runs of four
+#pragma unroll
+            for (int q = 0; q < R; q += 4) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(plan.S + base + q));
+                S[q] = v.x;
+                S[q + 1] = v.y;
+                S[q + 2] = v.z;
+                S[q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) S[q] = __ldg(&plan.S[base + q * sub]);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = make_float2(S[q] * a[q].y, S[q] * a[q].x);
+        dft_any<R>(a);
+    } else {  // kDitSmem, kDitLast
+        bfly_load<R, true>(s, base, sub, a);
+        if constexpr (HOIST) apply_twiddles<R>(a, w);
+        else if (tb != 0) apply_twiddles_mem<R>(a, tb, plan.tw);
+        dft_any<R>(a);
+    }
+    if constexpr (KIND == kDitLast) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int m = base + q * sub;
+            if (m < T) task.finish(rs, m, a[q].x, -a[q].y, floor2);
+            else if (m < ld) task.pad(rs, m);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            float2 v = a[q];
+            if (KIND == kDitSmem || KIND == kMidFused) v.y = -v.y;
+            s[padi(base + q * sub)] = v;
+        }
+    }
+}
+
+// One stage over all butterflies.  span = R sub with sub = 1 << lsub;
+// butterfly b is (g, j) = (b >> lsub, b & (sub - 1)), twiddle step
+// tb = (M / span) j.  When sub <= blockDim (both powers of two), j is the
+// same for every butterfly of a thread, so its twiddles are loaded once.
 template <int R, int KIND, class Task>
 __device__ __forceinline__ void conv_stage_r(float2 *s, int M, int lsub, const ConvPlan &plan,
                                              const Task &task, const typename Task::Rows &rs,
@@ -398,50 +465,22 @@ __device__ __forceinline__ void conv_stage_r(float2 *s, int M, int lsub, const C
     const int span = R * sub;
     const int tstep = M / span;  // w_span = w_M^tstep
     const int nb = M / R;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int g = b >> lsub, j = b & (sub - 1);
-        const int base = g * span + j;
-        const int tb = tstep * j;
-        float2 a[R];
-        if constexpr (KIND == kDifFirst) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int m = base + r * sub;
-                a[r] = m < T ? task.load(rs, m) : make_float2(0.f, 0.f);
-                *pw = fmaf(a[r].x, a[r].x, fmaf(a[r].y, a[r].y, *pw));
-            }
-            dif_core<R>(a, tb, plan.tw);
-        } else if constexpr (KIND == kDifSmem) {
-            bfly_load<R, false>(s, base, sub, a);
-            dif_core<R>(a, tb, plan.tw);
-        } else if constexpr (KIND == kMidFused) {
-            bfly_load<R, false>(s, base, sub, a);
-            dif_core<R>(a, tb, plan.tw);
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                // times -i S, then conjugate for the inverse: conj(-i S v) = (S y, S x)
-                const float S = __ldg(&plan.S[base + q * sub]);
-                a[q] = make_float2(S * a[q].y, S * a[q].x);
-            }
-            dit_core_conj<R>(a, tb, plan.tw);
-        } else {  // kDitSmem, kDitLast
-            bfly_load<R, true>(s, base, sub, a);
-            dit_core_conj<R>(a, tb, plan.tw);
+    if (KIND == kMidFused || sub <= (int)blockDim.x) {
+        const int tb = KIND == kMidFused ? 0 : tstep * ((int)threadIdx.x & (sub - 1));
+        float2 w[R];
+        if (KIND != kMidFused) load_twiddles<R>(w, tb, plan.tw);
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int g = b >> lsub, j = b & (sub - 1);
+            conv_butterfly<R, KIND, KIND != kMidFused>(s, g * span + j, sub, tb, w, plan, task,
+                                                       rs, T, ld, pw, floor2);
         }
-        if constexpr (KIND == kDitLast) {
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int m = base + q * sub;
-                if (m < T) task.finish(rs, m, a[q].x, -a[q].y, floor2);
-                else if (m < ld) task.pad(rs, m);
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                float2 v = a[q];
-                if (KIND == kDitSmem || KIND == kMidFused) v.y = -v.y;
-                s[padi(base + q * sub)] = v;
-            }
+    } else {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int g = b >> lsub, j = b & (sub - 1);
+            const int tb = tstep * j;
+            float2 w[R];  // not read: twiddles come from memory per butterfly
+            conv_butterfly<R, KIND, false>(s, g * span + j, sub, tb, w, plan, task, rs, T, ld,
+                                           pw, floor2);
         }
     }
 }
@@ -462,85 +501,103 @@ __device__ __forceinline__ void conv_stage(float2 *s, int M, int R, int lsub,
 
 __device__ __forceinline__ int ilog2(int v) { return 31 - __clz(v); }
 
-// Same Task interface as k_hilbert_pairs, plus
+
+// One row pair (rows 2 pr, 2 pr + 1 of `rows`) through the any-length
+// engine.  Same Task interface as k_hilbert_pairs, plus
 //   void pad(const Rows &, int m)
 // for the padding samples T <= m < ld of the output rows.  Stages: the first
 // forward stage reads global memory, the last forward and first inverse
 // stages run fused in registers, the last inverse stage writes the outputs.
+// Entry and exit: *s_pow is 0; the caller's threads all take part.
 template <class Task>
-__global__ void __launch_bounds__(kConvThreads, 1)
+__device__ __forceinline__ void conv_pair(const Task &task, const ConvPlan &plan, int T,
+                                          int64_t ld, int64_t rows, int64_t pr, float2 *smem,
+                                          float *s_pow) {
+    const int M = plan.M;
+    const int ns = plan.nstages;
+    const int64_t r0 = 2 * pr, r1 = 2 * pr + 1;
+    const bool v0 = r0 < rows, v1 = r1 < rows;
+    __syncthreads();  // the previous pair is done with smem; s_pow is 0
+    const auto rs = task.rows(r0, v0, r1, v1);
+    // forward stages; span of stage st is M / (radix[0] ... radix[st-1])
+    int span = M;
+    float pw = 0.f, floor2 = 0.f;
+    for (int st = 0; st < ns - 1; ++st) {
+        const int R = plan.radix[st];
+        const int lsub = ilog2(span / R);
+        if (st == 0)
+            conv_stage<kDifFirst>(smem, M, R, lsub, plan, task, rs, T, ld, &pw, 0.f);
+        else
+            conv_stage<kDifSmem>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, 0.f);
+        if (st == 0) {
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1)
+                pw += __shfl_xor_sync(0xffffffffu, pw, off);
+            if ((threadIdx.x & 31) == 0) atomicAdd(s_pow, pw);
+        }
+        __syncthreads();
+        if (st == 0) floor2 = 0x1p-40f * (*s_pow / (float)T);
+        span /= R;
+    }
+    // last forward stage (sub = 1), spectrum, first inverse stage
+    conv_stage<kMidFused>(smem, M, plan.radix[ns - 1], 0, plan, task, rs, T, ld, nullptr, 0.f);
+    __syncthreads();
+    if (threadIdx.x == 0) *s_pow = 0.f;  // every thread has read it (before the barrier)
+    // remaining inverse stages; the last writes the outputs
+    span = plan.radix[ns - 1];
+    for (int st = ns - 2; st >= 0; --st) {
+        const int R = plan.radix[st];
+        const int lsub = ilog2(span);
+        if (st > 0) {
+            conv_stage<kDitSmem>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, 0.f);
+            __syncthreads();
+        } else {
+            conv_stage<kDitLast>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, floor2);
+        }
+        span *= R;
+    }
+}
+
+// Persistent over the row pairs of one problem.
+template <class Task, int THREADS>
+__global__ void __launch_bounds__(THREADS, 512 / THREADS)
 k_hilbert_conv(const Task task, const ConvPlan plan, int T, int64_t ld, int64_t rows) {
     extern __shared__ __align__(16) float2 smem[];
     __shared__ float s_pow;
-    const int M = plan.M;
-    const int ns = plan.nstages;
     const int64_t npairs = (rows + 1) / 2;
     if (threadIdx.x == 0) s_pow = 0.f;
-    for (int64_t pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
-        const int64_t r0 = 2 * pr, r1 = 2 * pr + 1;
-        const bool v0 = r0 < rows, v1 = r1 < rows;
-        __syncthreads();  // the previous pair is done with smem; s_pow is 0
-        const auto rs = task.rows(r0, v0, r1, v1);
-        // forward stages; span of stage st is M / (radix[0] ... radix[st-1])
-        int span = M;
-        float pw = 0.f, floor2 = 0.f;
-        for (int st = 0; st < ns - 1; ++st) {
-            const int R = plan.radix[st];
-            const int lsub = ilog2(span / R);
-            if (st == 0)
-                conv_stage<kDifFirst>(smem, M, R, lsub, plan, task, rs, T, ld, &pw, 0.f);
-            else
-                conv_stage<kDifSmem>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, 0.f);
-            if (st == 0) {
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1)
-                    pw += __shfl_xor_sync(0xffffffffu, pw, off);
-                if ((threadIdx.x & 31) == 0) atomicAdd(&s_pow, pw);
-            }
-            __syncthreads();
-            if (st == 0) floor2 = 0x1p-40f * (s_pow / (float)T);
-            span /= R;
-        }
-        // last forward stage (sub = 1), spectrum, first inverse stage
-        conv_stage<kMidFused>(smem, M, plan.radix[ns - 1], 0, plan, task, rs, T, ld, nullptr,
-                              0.f);
-        __syncthreads();
-        if (threadIdx.x == 0) s_pow = 0.f;  // every thread has read it (before the barrier)
-        // remaining inverse stages; the last writes the outputs
-        span = plan.radix[ns - 1];
-        for (int st = ns - 2; st >= 0; --st) {
-            const int R = plan.radix[st];
-            const int lsub = ilog2(span);
-            if (st > 0) {
-                conv_stage<kDitSmem>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, 0.f);
-                __syncthreads();
-            } else {
-                conv_stage<kDitLast>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, floor2);
-            }
-            span *= R;
-        }
-    }
+    for (int64_t pr = blockIdx.x; pr < npairs; pr += gridDim.x)
+        conv_pair(task, plan, T, ld, rows, pr, smem, &s_pow);
+}
+
+template <class Task, int THREADS>
+cudaError_t launch_hilbert_conv_t(int num_sms, cudaStream_t st, const Task &task,
+                                  const ConvPlan &plan, int T, int64_t ld, int64_t rows) {
+    auto kern = k_hilbert_conv<Task, THREADS>;
+    static LaunchSetup ls;
+    // the largest transform of this thread count
+    constexpr int kMaxM = THREADS == 64 ? 3072 : THREADS == 128 ? 6144
+                        : THREADS == 256 ? 12288 : kMaxConvM;
+    int per_sm = 0;
+    cudaError_t e = setup_once(ls, kern, THREADS, conv_smem(kMaxM), per_sm);
+    if (e != cudaSuccess) return e;
+    const int64_t npairs = (rows + 1) / 2;
+    if (npairs == 0) return cudaSuccess;
+    int64_t grid = (int64_t)per_sm * num_sms;
+    if (grid > npairs) grid = npairs;
+    kern<<<(unsigned)grid, THREADS, conv_smem(plan.M), st>>>(task, plan, T, ld, rows);
+    return cudaGetLastError();
 }
 
 template <class Task>
 cudaError_t launch_hilbert_conv(int num_sms, cudaStream_t st, const Task &task,
                                 const ConvPlan &plan, int T, int64_t ld, int64_t rows) {
-    auto kern = k_hilbert_conv<Task>;
-    static LaunchSetup ls;
-    constexpr size_t kMaxSmem = (size_t)(24576 + 24576 / 32) * sizeof(float2);
-    int unused = 0;
-    cudaError_t e = setup_once(ls, kern, kConvThreads, kMaxSmem, unused);
-    if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)(plan.M + plan.M / 32) * sizeof(float2);
-    int per_sm = (int)(225 * 1024 / (smem + 1024));
-    if (per_sm > 4) per_sm = 4;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t npairs = (rows + 1) / 2;
-    if (npairs == 0) return cudaSuccess;
-    int64_t grid = (int64_t)per_sm * num_sms * 2;
-    if (grid > npairs) grid = npairs;
-    kern<<<(unsigned)grid, kConvThreads, smem, st>>>(task, plan, T, ld, rows);
-    return cudaGetLastError();
+    switch (conv_threads(plan.M)) {
+        case 64: return launch_hilbert_conv_t<Task, 64>(num_sms, st, task, plan, T, ld, rows);
+        case 128: return launch_hilbert_conv_t<Task, 128>(num_sms, st, task, plan, T, ld, rows);
+        case 256: return launch_hilbert_conv_t<Task, 256>(num_sms, st, task, plan, T, ld, rows);
+        default: return launch_hilbert_conv_t<Task, 512>(num_sms, st, task, plan, T, ld, rows);
+    }
 }
 
 }  // namespace fft

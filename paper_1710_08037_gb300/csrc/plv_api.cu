@@ -323,7 +323,122 @@ struct plv_group {
     int4 *items = nullptr;            // device tile list, longest first
     int nprob = 0, nitems = 0;
     bool any_diag = false;
+    // analytic-signal plan (problems with an input x)
+    bool has_k1 = false;
+    plv_dtype k1_dtype = PLV_F32;
+    plv::K1Desc *k1_descs = nullptr;  // device
+    int2 *k1_items = nullptr;         // device
+    plv::K1Group k1{};
 };
+
+namespace {
+
+// Thread class of the any-length engine for transform length M: 64, 128,
+// 256, 512 threads (conv_threads).
+int conv_class(int M) {
+    const int t = conv_threads(M);
+    return t == 64 ? 0 : t == 128 ? 1 : t == 256 ? 2 : 3;
+}
+
+// The analytic-signal part of a plan: descriptors, (problem, pair) items by
+// class and decreasing M, padding rows zeroed.  Called with the handle's
+// device current.
+plv_status plan_k1(Handle &h, const plv_problem *probs, int nprob, plv_group *g) {
+    std::vector<K1Desc> descs;
+    bool first = true;
+    for (int p = 0; p < nprob; ++p) {
+        const plv_problem &q = probs[p];
+        if (!q.x || q.batch == 0 || q.N == 0) continue;
+        if (q.dtype != PLV_F32 && q.dtype != PLV_F64)
+            return fail(PLV_ERR_INVALID, "plv_group_create: problem %d unknown dtype", p);
+        if (first) g->k1_dtype = q.dtype;
+        first = false;
+        if (q.dtype != g->k1_dtype)
+            return fail(PLV_ERR_UNSUPPORTED,
+                        "plv_group_create: problem %d: every input of a plan has one dtype", p);
+        if (q.ldx < q.T)
+            return fail(PLV_ERR_INVALID, "plv_group_create: problem %d ldx < T", p);
+        if (q.T < 2 || 2 * q.T - 1 > kMaxConvM)
+            return fail(PLV_ERR_UNSUPPORTED, "plv_group_create: problem %d T = %d (2..%d)", p,
+                        q.T, kMaxConvM / 2);
+        if (((uintptr_t)q.x % (q.dtype == PLV_F32 ? 4 : 8)) != 0)
+            return fail(PLV_ERR_INVALID, "plv_group_create: problem %d x misaligned", p);
+        const int64_t pairs = ((int64_t)q.batch * q.N + 1) / 2;
+        if (pairs > 0x7fffffffLL)
+            return fail(PLV_ERR_UNSUPPORTED, "plv_group_create: problem %d too many rows", p);
+        const ConvPlan *plan = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(h.mu);
+            plv_status st = get_conv_plan(h, q.T, &plan);
+            if (st != PLV_OK) return st;
+        }
+        K1Desc d;
+        d.x = q.x;
+        d.P = q.P;
+        d.ldx = q.ldx;
+        d.ld = padded_len(q.T);
+        d.rows = (int64_t)q.batch * q.N;
+        d.N = q.N;
+        d.T = q.T;
+        d.plan = *plan;
+        descs.push_back(d);
+    }
+    if (descs.empty()) return PLV_OK;
+    // items: by class, then decreasing M, then problem order
+    std::vector<int> order(descs.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const int ca = conv_class(descs[a].plan.M), cb = conv_class(descs[b].plan.M);
+        if (ca != cb) return ca < cb;
+        return descs[a].plan.M > descs[b].plan.M;
+    });
+    std::vector<int2> items;
+    K1Group kg{};
+    for (int c = 0; c < kConvClasses; ++c) {
+        kg.begin[c] = (int64_t)items.size();
+        kg.max_M[c] = 0;
+        for (int i : order) {
+            if (conv_class(descs[i].plan.M) != c) continue;
+            kg.max_M[c] = std::max(kg.max_M[c], descs[i].plan.M);
+            const int64_t pairs = (descs[i].rows + 1) / 2;
+            for (int64_t pr = 0; pr < pairs; ++pr) items.push_back(make_int2(i, (int)pr));
+        }
+        kg.count[c] = (int64_t)items.size() - kg.begin[c];
+    }
+    plv_status st = check_cuda(cudaMalloc(&g->k1_descs, sizeof(K1Desc) * descs.size()),
+                               "plv_group_create: analytic descriptors");
+    if (st == PLV_OK)
+        st = check_cuda(cudaMalloc(&g->k1_items, sizeof(int2) * items.size()),
+                        "plv_group_create: analytic items");
+    if (st == PLV_OK)
+        st = check_cuda(cudaMemcpy(g->k1_descs, descs.data(), sizeof(K1Desc) * descs.size(),
+                                   cudaMemcpyHostToDevice),
+                        "plv_group_create: upload analytic descriptors");
+    if (st == PLV_OK)
+        st = check_cuda(cudaMemcpy(g->k1_items, items.data(), sizeof(int2) * items.size(),
+                                   cudaMemcpyHostToDevice),
+                        "plv_group_create: upload analytic items");
+    if (st != PLV_OK) return st;
+    // the split layout's padding rows: zero once, nothing writes them later
+    if (h.prec != PLV_PREC_FP32) {
+        for (int p = 0; p < nprob && st == PLV_OK; ++p) {
+            const plv_problem &q = probs[p];
+            if (!q.x || q.batch == 0 || q.N == 0) continue;
+            st = check_cuda(launch_zero_pad_rows(0, q.P, q.batch, q.N, q.T),
+                            "plv_group_create: padding rows");
+        }
+        if (st == PLV_OK)
+            st = check_cuda(cudaDeviceSynchronize(), "plv_group_create: padding rows");
+        if (st != PLV_OK) return st;
+    }
+    kg.descs = g->k1_descs;
+    kg.items = g->k1_items;
+    g->k1 = kg;
+    g->has_k1 = true;
+    return PLV_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -383,6 +498,14 @@ plv_status plv_group_create(plv_handle *hp, const plv_problem *probs, int nprob,
         delete g;
         return fail(PLV_ERR_UNSUPPORTED, "plv_group_create: too many tiles");
     }
+    {
+        DeviceGuard guard(h.device);
+        plv_status st = plan_k1(h, probs, nprob, g);
+        if (st != PLV_OK) {
+            plv_group_destroy(g);
+            return st;
+        }
+    }
     // longest first: a tile's cost is proportional to its K blocks
     std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
         return dp[a.x].nkb > dp[b.x].nkb;
@@ -437,13 +560,26 @@ plv_status plv_gram_grouped(plv_handle *hp, void *stream, const plv_group *g) {
                       "plv_gram_grouped launch");
 }
 
+plv_status plv_analytic_grouped(plv_handle *hp, void *stream, const plv_group *g) {
+    if (!hp || !g) return fail(PLV_ERR_INVALID, "plv_analytic_grouped: NULL argument");
+    if (g->device != hp->h.device || g->prec != hp->h.prec)
+        return fail(PLV_ERR_INVALID,
+                    "plv_analytic_grouped: plan made for another device or precision");
+    if (!g->has_k1) return fail(PLV_ERR_INVALID, "plv_analytic_grouped: the plan has no input");
+    PLV_GUARD(&hp->h);
+    return check_cuda(launch_analytic_group(&hp->h, (cudaStream_t)stream, g->k1_dtype, g->k1),
+                      "plv_analytic_grouped launch");
+}
+
 plv_status plv_group_destroy(plv_group *g) {
     if (!g) return PLV_OK;
     {
         DeviceGuard guard(g->device);
-        if (g->probs || g->items) cudaDeviceSynchronize();
+        if (g->probs || g->items || g->k1_descs || g->k1_items) cudaDeviceSynchronize();
         if (g->probs) cudaFree(g->probs);
         if (g->items) cudaFree(g->items);
+        if (g->k1_descs) cudaFree(g->k1_descs);
+        if (g->k1_items) cudaFree(g->k1_items);
     }
     delete g;
     return PLV_OK;

@@ -64,3 +64,31 @@ def test_null_handle_is_rejected_without_a_device(lib):
     assert b"NULL" in lib.plv_last_error(None)
     rc = lib.plv_create(None, 0, 0, ctypes.c_size_t(0))
     assert rc == _lib.PLV_ERR_INVALID
+
+
+def test_problem_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of plv_problem has the C compiler's size and field
+    offsets for the struct declared in include/plv.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1710_08037_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+    names = [f[0] for f in _lib.PlvProblem._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "plv.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu\\n", sizeof(plv_problem));\n' +
+        "".join(f'  printf("%zu\\n", offsetof(plv_problem, {n}));\n' for n in names) +
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = [ctypes.sizeof(_lib.PlvProblem)] + [
+        getattr(_lib.PlvProblem, n).offset for n in names]
+    assert got == want
