@@ -125,7 +125,9 @@ class ClockSampler:
 # launch by epochs (profiles/k_gram_tc_and_k_hilbert_pairs_bandlimited-N4096-T4096-E4.md).
 # An entry is removed when the kernel changes after its capture.
 TRAFFIC = {
-    ("k_gram_tc", "bandlimited-N4096-T4096-E30", "bf16x3"): (1.902304e9 + 1.010694e9) * 30 / 4,
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_gram_tc launch
+    # on bandlimited-N4096-T4096-E4, scaled by epochs (traffic grows with them)
+    ("k_gram_tc", "bandlimited-N4096-T4096-E30", "bf16x3"): (1.945232e9 + 1.038737e9) * 30 / 4,
 }
 
 

@@ -64,11 +64,26 @@ struct ConvPlan {
     const float *S;
 };
 constexpr int kMaxConvM = 24576;  // 3 * 2^13: T up to 12288
-// Threads per CTA of the any-length engine for transform length M: as many
-// CTAs per SM as the shared buffer allows (each CTA is its own barrier
-// domain), with the SM's 512 threads of 128 registers split among them.
+// Thread classes of the any-length engine: CTAs of kConvThreads[c] threads
+// take transform lengths M <= kConvMaxM[c].  As many CTAs per SM as the
+// shared buffer allows (each CTA is its own barrier domain), with the SM's
+// register file split among them at kConvRegs registers per thread.  Radix
+// stages are at most kConvMaxRadix.
+constexpr int kConvClasses = 4;
+constexpr int kConvRegs = 64;
+constexpr int kConvMaxRadix = 8;
+__host__ __device__ constexpr int conv_class_threads(int c) {
+    return c == 0 ? 128 : c == 1 ? 256 : c == 2 ? 512 : 1024;
+}
+__host__ __device__ constexpr int conv_class_max_M(int c) {
+    return c == 0 ? 3072 : c == 1 ? 6144 : c == 2 ? 12288 : kMaxConvM;
+}
+__host__ __device__ constexpr int conv_class(int M) {
+    return M <= conv_class_max_M(0) ? 0 : M <= conv_class_max_M(1) ? 1
+         : M <= conv_class_max_M(2) ? 2 : 3;
+}
 __host__ __device__ constexpr int conv_threads(int M) {
-    return M <= 3072 ? 64 : M <= 6144 ? 128 : M <= 12288 ? 256 : 512;
+    return conv_class_threads(conv_class(M));
 }
 __host__ __device__ constexpr size_t conv_smem(int M) {
     return (size_t)(M + M / 32) * sizeof(float2);
@@ -137,10 +152,8 @@ struct K1Desc {
     int N, T;
     ConvPlan plan;
 };
-// Thread-count classes of the any-length engine (fft::conv_threads).
-constexpr int kConvClasses = 4;
-// A grouped K1 plan: every (problem, row pair) of the group, in class order
-// (64, 128, 256, 512 threads) and within a class by decreasing M.
+// A grouped K1 plan: every (problem, row pair) of the group, by thread class
+// (conv_class) and within a class by decreasing M.
 struct K1Group {
     const K1Desc *descs;     // device
     const int2 *items;       // device: (problem, row pair)

@@ -26,8 +26,8 @@ int choose_M(int T) {
 }
 
 // Radix order of the transform: 3 first for M = 3 * 2^a (every later span is
-// then a power of two), then radix-16 stages and one remainder radix
-// 2^(a mod 4).  The remainder goes where it leaves the fewest twiddle loads
+// then a power of two), then stages of the largest radix R = kConvMaxRadix
+// and one remainder radix 2^(a mod log2 R).  The remainder goes where it leaves the fewest twiddle loads
 // on the device: a stage whose sub-block length (span / R) exceeds the CTA's
 // thread count loads its R - 1 twiddles per butterfly, a later one loads
 // them once per thread; the last forward stage has none.
@@ -40,7 +40,9 @@ std::vector<int> schedule(int M) {
     }
     int a = 0;
     while ((1 << a) < m) ++a;
-    const int n16 = a / 4, rem = 1 << (a % 4);
+    int lr = 0;  // log2 of the largest radix
+    while ((2 << lr) <= kConvMaxRadix) ++lr;
+    const int n16 = a / lr, rem = 1 << (a % lr);
     const int threads = conv_threads(M);
     std::vector<int> best;
     double best_cost = 0.0;
@@ -48,7 +50,7 @@ std::vector<int> schedule(int M) {
         std::vector<int> r = head;
         for (int k = 0; k < n16; ++k) {
             if (k == pos && rem > 1) r.push_back(rem);
-            r.push_back(16);
+            r.push_back(kConvMaxRadix);
         }
         if (pos == n16 && rem > 1) r.push_back(rem);
         double cost = 0.0;

@@ -490,8 +490,13 @@ __device__ __forceinline__ void conv_stage(float2 *s, int M, int R, int lsub,
                                            const ConvPlan &plan, const Task &task,
                                            const typename Task::Rows &rs, int T, int64_t ld,
                                            float *pw, float floor2) {
+    // radices above kConvMaxRadix never occur (the plan's schedule) and are
+    // not compiled, so they do not count against the register budget
     switch (R) {
-        case 16: conv_stage_r<16, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
+        case 16:
+            if constexpr (kConvMaxRadix >= 16)
+                conv_stage_r<16, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2);
+            break;
         case 8: conv_stage_r<8, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
         case 4: conv_stage_r<4, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
         case 3: conv_stage_r<3, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
@@ -560,7 +565,7 @@ __device__ __forceinline__ void conv_pair(const Task &task, const ConvPlan &plan
 
 // Persistent over the row pairs of one problem.
 template <class Task, int THREADS>
-__global__ void __launch_bounds__(THREADS, 512 / THREADS)
+__global__ void __launch_bounds__(THREADS, 65536 / (kConvRegs * THREADS))
 k_hilbert_conv(const Task task, const ConvPlan plan, int T, int64_t ld, int64_t rows) {
     extern __shared__ __align__(16) float2 smem[];
     __shared__ float s_pow;
@@ -570,16 +575,14 @@ k_hilbert_conv(const Task task, const ConvPlan plan, int T, int64_t ld, int64_t 
         conv_pair(task, plan, T, ld, rows, pr, smem, &s_pow);
 }
 
-template <class Task, int THREADS>
+template <class Task, int C>
 cudaError_t launch_hilbert_conv_t(int num_sms, cudaStream_t st, const Task &task,
                                   const ConvPlan &plan, int T, int64_t ld, int64_t rows) {
+    constexpr int THREADS = conv_class_threads(C);
     auto kern = k_hilbert_conv<Task, THREADS>;
     static LaunchSetup ls;
-    // the largest transform of this thread count
-    constexpr int kMaxM = THREADS == 64 ? 3072 : THREADS == 128 ? 6144
-                        : THREADS == 256 ? 12288 : kMaxConvM;
     int per_sm = 0;
-    cudaError_t e = setup_once(ls, kern, THREADS, conv_smem(kMaxM), per_sm);
+    cudaError_t e = setup_once(ls, kern, THREADS, conv_smem(conv_class_max_M(C)), per_sm);
     if (e != cudaSuccess) return e;
     const int64_t npairs = (rows + 1) / 2;
     if (npairs == 0) return cudaSuccess;
@@ -592,11 +595,11 @@ cudaError_t launch_hilbert_conv_t(int num_sms, cudaStream_t st, const Task &task
 template <class Task>
 cudaError_t launch_hilbert_conv(int num_sms, cudaStream_t st, const Task &task,
                                 const ConvPlan &plan, int T, int64_t ld, int64_t rows) {
-    switch (conv_threads(plan.M)) {
-        case 64: return launch_hilbert_conv_t<Task, 64>(num_sms, st, task, plan, T, ld, rows);
-        case 128: return launch_hilbert_conv_t<Task, 128>(num_sms, st, task, plan, T, ld, rows);
-        case 256: return launch_hilbert_conv_t<Task, 256>(num_sms, st, task, plan, T, ld, rows);
-        default: return launch_hilbert_conv_t<Task, 512>(num_sms, st, task, plan, T, ld, rows);
+    switch (conv_class(plan.M)) {
+        case 0: return launch_hilbert_conv_t<Task, 0>(num_sms, st, task, plan, T, ld, rows);
+        case 1: return launch_hilbert_conv_t<Task, 1>(num_sms, st, task, plan, T, ld, rows);
+        case 2: return launch_hilbert_conv_t<Task, 2>(num_sms, st, task, plan, T, ld, rows);
+        default: return launch_hilbert_conv_t<Task, 3>(num_sms, st, task, plan, T, ld, rows);
     }
 }
 

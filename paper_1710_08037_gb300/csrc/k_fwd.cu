@@ -46,7 +46,7 @@ typedef TaskOf<Tin, KIND> Tk;
 // memory when the problem changes (items of one problem are contiguous per
 // CTA stride, so this is rare).
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 512 / THREADS)
+__global__ void __launch_bounds__(THREADS, 65536 / (kConvRegs * THREADS))
 k_hilbert_conv_group(const K1Desc *__restrict__ descs, const int2 *__restrict__ items,
                      int64_t n) {
     extern __shared__ __align__(16) float2 smem[];
@@ -71,15 +71,15 @@ k_hilbert_conv_group(const K1Desc *__restrict__ descs, const int2 *__restrict__ 
     }
 }
 
-template <int THREADS>
-cudaError_t launch_group_class(const Handle *h, cudaStream_t s, const K1Group &g, int c) {
+template <int C>
+cudaError_t launch_group_class(const Handle *h, cudaStream_t s, const K1Group &g) {
+    constexpr int THREADS = conv_class_threads(C);
     auto kern = k_hilbert_conv_group<THREADS>;
     static LaunchSetup ls;
-    constexpr int kMaxM = THREADS == 64 ? 3072 : THREADS == 128 ? 6144
-                        : THREADS == 256 ? 12288 : kMaxConvM;
     int per_sm = 0;
-    cudaError_t e = setup_once(ls, kern, THREADS, conv_smem(kMaxM), per_sm);
+    cudaError_t e = setup_once(ls, kern, THREADS, conv_smem(conv_class_max_M(C)), per_sm);
     if (e != cudaSuccess) return e;
+    const int c = C;
     const int64_t n = g.count[c];
     if (n == 0) return cudaSuccess;
     int64_t grid = (int64_t)per_sm * h->num_sms;
@@ -108,10 +108,11 @@ cudaError_t k1_conv_group(const Handle *h, cudaStream_t s, const K1Group &g) {
     if constexpr (KIND_ == kK1Prep) {
         return cudaErrorInvalidValue;  // the backward recompute is not grouped
     } else {
-        cudaError_t e = launch_group_class<64>(h, s, g, 0);
-        if (e == cudaSuccess) e = launch_group_class<128>(h, s, g, 1);
-        if (e == cudaSuccess) e = launch_group_class<256>(h, s, g, 2);
-        if (e == cudaSuccess) e = launch_group_class<512>(h, s, g, 3);
+        static_assert(kConvClasses == 4, "one launch per class");
+        cudaError_t e = launch_group_class<0>(h, s, g);
+        if (e == cudaSuccess) e = launch_group_class<1>(h, s, g);
+        if (e == cudaSuccess) e = launch_group_class<2>(h, s, g);
+        if (e == cudaSuccess) e = launch_group_class<3>(h, s, g);
         return e;
     }
 }

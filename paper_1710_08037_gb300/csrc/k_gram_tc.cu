@@ -66,7 +66,7 @@ constexpr int ACC_COLS = 256;                 // Re (128) + Im (128)
 // for a coherent pair); the FP16 split is the accuracy-first mode.
 template <uint32_t FMT>
 struct Chunk {
-    static constexpr int CH = FMT == 1u ? 8 : 4;
+    static constexpr int CH = FMT == 1u ? 16 : 4;
 };
 constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s bound on any wait
 constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align*/ + 256;

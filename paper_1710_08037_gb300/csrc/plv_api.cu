@@ -333,13 +333,6 @@ struct plv_group {
 
 namespace {
 
-// Thread class of the any-length engine for transform length M: 64, 128,
-// 256, 512 threads (conv_threads).
-int conv_class(int M) {
-    const int t = conv_threads(M);
-    return t == 64 ? 0 : t == 128 ? 1 : t == 256 ? 2 : 3;
-}
-
 // The analytic-signal part of a plan: descriptors, (problem, pair) items by
 // class and decreasing M, padding rows zeroed.  Called with the handle's
 // device current.
