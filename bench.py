@@ -513,7 +513,7 @@ def run_backward(args):
     dev = torch.device("cuda", local)
     B, N, T = 16, 1024, 4096
     hf = plv.Handle(precision=args.precision, device=local)
-    hb = plv.Handle(precision="fp32", device=local)
+    hb = hf  # split handles take the backward contraction to the tensor cores
     x = synth.bandlimited(B, N, T, seed=1005 + rank, device=dev)
     mask = synth.random_pair_mask(N, 0.10, seed=1005, device=dev)
     g3 = mask.to(torch.float32).expand(B, N, N).contiguous()
@@ -563,29 +563,56 @@ def run_backward(args):
     gemm_flops = 8.0 * N * N * ld * B
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    split = args.precision != "fp32"
+    peak = float(peaks["bf16_tflops"]) if split else fp32_peak
+    # the FP32 CUDA-core backward on the same input, for comparison
+    fp32_bwd = None
+    if split and not args.no_fp32_compare:
+        h32 = plv.Handle(precision="fp32", device=local)
+        g32 = torch.empty_like(grad)
+        h32.plv_backward(x, out["C"], None, None, g3, grad_x=g32)
+        torch.cuda.synchronize(dev)
+        a, b = ev(), ev()
+        a.record(s)
+        for _ in range(2):
+            h32.plv_backward(x, out["C"], None, None, g3, grad_x=g32)
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        rel = float(torch.linalg.norm(grad - g32) / torch.linalg.norm(g32))
+        fp32_bwd = {"backward_ms": a.elapsed_time(b) / 2,
+                    "rel_l2_diff_vs_split": rel}
+        h32.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"forward {args.precision}, backward f32",
+            "dtype": f"{args.precision} (backward contraction "
+                     f"{'bf16x3' if args.precision != 'fp32' else 'f32'}, "
+                     f"rest f32)",
             "data": "synthetic",
             "config": {"workload": BACKWARD, "B": B, "N": N, "T": T,
                        "loss": "sum of ciPLV over a seeded 10% mask of ordered "
                                "pairs", "recompute": "analytic signal "
                        "recomputed in the backward pass"},
             "forward_ms": fwd_ms, "backward_ms": bwd_ms,
-            "backward_gemm": {"flops_per_launch": gemm_flops,
-                              "note": "Gamma = S P / T, FP32 on the CUDA "
-                                      "cores; the roofline is the FP32 ALU "
-                                      "peak (%s)" % peak_kind,
-                              "peak_tflops": peak},
-            "gpu_launches": 6 * args.steps, "clocks": clk,
-            "device_status": hb.plv_sync_status()}
+            "backward_contraction": {
+                "flops_per_step": gemm_flops * (3 if split else 1),
+                "note": ("Gamma = S P / T on the tensor cores, BF16 hi+lo "
+                         "splits (3 products per term); bound: tensor, "
+                         "peak %s BF16 burst" % peak_kind) if split else
+                        ("Gamma = S P / T, FP32 on the CUDA cores; bound: "
+                         "alu, peak derived from 152 SMs x 128 FMA x 2 x "
+                         "max SM clock"),
+                "peak_tflops": peak,
+                "lower_bound_tflops_over_whole_backward":
+                    gemm_flops * (3 if split else 1) / (bwd_ms / 1e3) / 1e12},
+            "fp32_backward": fp32_bwd,
+            "gpu_launches": (2 + (6 if split else 4)) * args.steps,
+            "clocks": clk, "device_status": hb.plv_sync_status()}
         print(json.dumps(line), flush=True)
     hf.close()
-    hb.close()
     if dist:
         dist.destroy_process_group()
 

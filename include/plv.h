@@ -229,10 +229,15 @@ plv_status plv_metrics(plv_handle *h, void *stream, const void *C, int batch,
  *   grad_x   : float [batch][N][T] (row stride T), written completely.
  * Conventions: dPLV/dC = C/|C| (0 at |C| = 0); d|Im C|/dIm C = sign(Im C)
  * (0 at 0); ciPLV is differentiated where (1 - Re C)(1 + Re C) > 0.
- * Arithmetic FP32.  Supported T: as plv_analytic.  Uses handle scratch of
- * batch*N*ld*20 + batch*N*N*8 bytes, allocated on first use for a size
- * (cudaMalloc; fails with PLV_ERR_INVALID if that first use is inside a
- * stream capture). */
+ * Arithmetic FP32, except the one dense contraction Gamma = S P / T
+ * (S = G + G^H): on an FP32 handle FP32 FMA on the CUDA cores; on a BF16X3
+ * or FP16X3 handle the tensor cores, with S and P as BF16 hi + lo splits
+ * and three products per term (BF16 for both handle kinds: gradients can
+ * exceed the FP16 range).  Supported T: as plv_analytic.  Uses handle
+ * scratch of batch*N*ld*20 bytes plus, on an FP32 handle, batch*N*N*8, or,
+ * on a split handle, batch*(ceil(N/128) + ceil(ld/128))*128*ceil(N/32)*32*8;
+ * allocated on first use for a size (cudaMalloc; fails with PLV_ERR_INVALID
+ * if that first use is inside a stream capture). */
 plv_status plv_backward(plv_handle *h, void *stream, const void *x,
                         plv_dtype dtype, int batch, int N, int T, int64_t ldx,
                         const void *C, const float *g_plv, const float *g_iplv,

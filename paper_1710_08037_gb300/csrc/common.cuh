@@ -186,10 +186,16 @@ cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_
                             int64_t rows, int log2T, int64_t ldx, float *P, float *rinv,
                             int T, const ConvPlan *plan);
 // K5: S = G + G^H, Gamma = S P / T, grad = Re Gamma_z - H{Im Gamma_z}.
+// tc_ops NULL: FP32 contraction on the CUDA cores with S FP32 planar
+// [batch][2][N][N]; else the tensor-core contraction with its split operands
+// (backward_tc_bytes bytes at tc_ops) and S unused.
 cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
                             int log2T, const float2 *C, const float *g1, const float *g2,
                             const float *g3, const float *P, const float *rinv, float *S,
-                            float *Gm, float *grad, const ConvPlan *plan);
+                            float *Gm, float *grad, const ConvPlan *plan, void *tc_ops);
+// Bytes of the tensor-core backward's split operands (S rows, then conj(P)^T
+// rows); *a_bytes receives the first part's size.
+size_t backward_tc_bytes(int batch, int N, int T, size_t *a_bytes);
 // Eq. 4 on a given analytic signal.
 cudaError_t launch_normalize(const Handle *h, cudaStream_t s, const void *z,
                              plv_dtype dt, int64_t rows, int N, int T,
@@ -216,6 +222,20 @@ struct TcProblem {
     GramOut out;
 };
 TcProblem make_tc_problem(const void *P, int batch, int N, int T, GramOut out);
+// The backward pass's contraction on the tensor cores (BF16 split):
+// G[e][i][2][ld] = (1/T) sum_k S[e][i][k] P[e][k][t], from A = split rows of S
+// (row i, K = k; rows padded to nrb_a blocks of 128) and B = split rows of
+// conj(P)^T (row t, K = k; nrb_b blocks of 128 rows), both in the tiled split
+// layout with nkb blocks of 32 along k.  Every (I, J) tile of every epoch.
+struct TcGemm {
+    const uint8_t *A, *B;
+    int nrb_a, nrb_b, nkb, tpe;  // tpe = nrb_a * nrb_b tiles per epoch
+    int N;                       // valid rows i (and k)
+    int64_t ld;                  // row length of G (valid t)
+    float invT;
+    float *G;
+};
+cudaError_t launch_gemm_tc(const Handle *h, cudaStream_t s, const TcGemm &g, int batch);
 // One persistent launch over a list of (problem, epoch, I, J) tiles.
 cudaError_t launch_gram_tc_group(const Handle *h, cudaStream_t s, const TcProblem *probs,
                                  const int4 *items, int nitems);

@@ -16,14 +16,19 @@
 //   part the Hilbert transform H, H^T = -H):
 //     dL/dx = Re Gamma_z - H{Im Gamma_z}.
 //
-// Stages (all FP32):
-//   1. recompute P and 1/|z| from x (the forward FFT task, fft.cuh);
-//   2. k_bwd_s: S = G + G^H from C and the upstream gradients, 32x32 tiles
-//      staged through shared memory for the transposed reads;
-//   3. k_bwd_gemm: Gamma = S P / T.  S is Hermitian, so
-//      Gamma[i][t] = sum_k conj(S[k][i]) P[k][t] / T and both operands are
-//      read as rows (no transposes): 128x128 tiles, 8x8 complex register
-//      blocks, double-buffered shared memory;
+// Stages:
+//   1. recompute P and 1/|z| from x (the forward FFT task, fft.cuh), FP32;
+//   2. S = G + G^H from C and the upstream gradients, 32x32 tiles staged
+//      through shared memory for the transposed reads;
+//   3. Gamma = S P / T, the one dense contraction of the pass:
+//      - FP32 handles: k_bwd_gemm on the CUDA cores.  S is Hermitian, so
+//        Gamma[i][t] = sum_k conj(S[k][i]) P[k][t] / T and both operands are
+//        read as rows (no transposes): 128x128 tiles, 8x8 complex register
+//        blocks, double-buffered shared memory;
+//      - split-precision handles: the tensor-core kernel of the Gram in its
+//        GEMM mode (BF16 hi + lo splits, three products per term).  Stage 2
+//        then writes S as split rows (k_bwd_s_split) and k_bwd_pt_split
+//        writes conj(P)^T as split rows, so that both operands are K-major;
 //   4. BwdTask on the FFT engine: u = -Im(P) s, v = Re(P) s with
 //      s = Im(conj(P) Gamma) / |z|, then grad = u - H{v}.
 #include "fft.cuh"
@@ -83,6 +88,76 @@ k_bwd_s(const float2 *__restrict__ C, const float *__restrict__ g1,
         const int64_t q = (int64_t)b * 2 * NN + (int64_t)i * N + j;
         S[q] = gij.x + gji.x;       // Re(G_ij + conj(G_ji))
         S[q + NN] = gij.y - gji.y;  // Im
+    }
+}
+
+// One complex value as BF16 hi + lo splits at plane-0 element `off` of the
+// tiled split layout (planes Re_hi, Re_lo, Im_hi, Im_lo, kTileRows x kTileK
+// elements apart).
+__device__ __forceinline__ void store_split_bf16(__nv_bfloat16 *base, int64_t off, float2 v) {
+    constexpr int64_t ps = kTileRows * kTileK;
+    const __nv_bfloat16 rh = __float2bfloat16_rn(v.x);
+    const __nv_bfloat16 ih = __float2bfloat16_rn(v.y);
+    base[off] = rh;
+    base[off + ps] = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+    base[off + 2 * ps] = ih;
+    base[off + 3 * ps] = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+}
+
+// S = G + G^H as the A operand of the tensor-core contraction: row i, K = k,
+// tiled split layout with NRB row blocks and NKB blocks of 32 along k.  The
+// grid covers the padded extents, which are written as zeros.
+__global__ void __launch_bounds__(256)
+k_bwd_s_split(const float2 *__restrict__ C, const float *__restrict__ g1,
+              const float *__restrict__ g2, const float *__restrict__ g3, int N, int64_t NRB,
+              int64_t NKB, __nv_bfloat16 *__restrict__ A) {
+    __shared__ float2 Gt[32][33];
+    const int b = blockIdx.z;
+    const int bi = blockIdx.y * 32, bk = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t eb = (int64_t)b * N * N;
+    auto G = [&](int r, int c) -> float2 {
+        if (r >= N || c >= N || r == c) return make_float2(0.f, 0.f);
+        const int64_t q = eb + (int64_t)r * N + c;
+        return gfun(C[q], g1 ? g1[q] : 0.f, g2 ? g2[q] : 0.f, g3 ? g3[q] : 0.f);
+    };
+    for (int yy = ty; yy < 32; yy += 8) Gt[yy][tx] = G(bk + yy, bi + tx);
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const int i = bi + yy, k = bk + tx;
+        const float2 gik = G(i, k);
+        const float2 gki = Gt[tx][yy];  // G(k, i)
+        store_split_bf16(A, split_offset(b, i, k, NRB, NKB),
+                         make_float2(gik.x + gki.x, gik.y - gki.y));
+    }
+}
+
+// conj(P)^T as the B operand: row t, K = k (rows k of P are channels), tiled
+// split layout with NRBT row blocks along t and NKB blocks of 32 along k.
+// P is FP32 planar [batch * N][2][ld]; t >= ld and k >= N are zeros.
+__global__ void __launch_bounds__(256)
+k_bwd_pt_split(const float *__restrict__ P, int N, int64_t ld, int64_t NRBT, int64_t NKB,
+               __nv_bfloat16 *__restrict__ B) {
+    __shared__ float2 tile[32][33];  // [k][t]
+    const int b = blockIdx.z;
+    const int64_t t0 = (int64_t)blockIdx.y * 32;
+    const int k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int kk = ty; kk < 32; kk += 8) {
+        const int k = k0 + kk;
+        const int64_t t = t0 + tx;
+        float2 v = make_float2(0.f, 0.f);
+        if (k < N && t < ld) {
+            const float *row = P + ((int64_t)b * N + k) * 2 * ld;
+            v = make_float2(__ldg(row + t), __ldg(row + ld + t));
+        }
+        tile[kk][tx] = v;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const float2 v = tile[tx][yy];  // P[k0 + tx][t0 + yy]
+        store_split_bf16(B, split_offset(b, t0 + yy, k0 + tx, NRBT, NKB),
+                         make_float2(v.x, -v.y));
     }
 }
 
@@ -241,19 +316,59 @@ struct BwdTask {
 
 }  // namespace
 
+size_t backward_tc_bytes(int batch, int N, int T, size_t *a_bytes) {
+    const int64_t NKB = ((int64_t)N + kTileK - 1) / kTileK;
+    const size_t a = (size_t)batch * row_blocks(N) * NKB * kBlockElems * 2;
+    const size_t b = (size_t)batch * row_blocks((int)padded_len(T)) * NKB * kBlockElems * 2;
+    if (a_bytes) *a_bytes = a;
+    return a + b;
+}
+
 cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
                             int log2T, const float2 *C, const float *g1, const float *g2,
                             const float *g3, const float *P, const float *rinv, float *S,
-                            float *Gm, float *grad, const ConvPlan *plan) {
+                            float *Gm, float *grad, const ConvPlan *plan, void *tc_ops) {
     const int64_t ld = padded_len(T);
-    dim3 sg((N + 31) / 32, (N + 31) / 32, batch);
-    k_bwd_s<<<sg, 256, 0, st>>>(C, g1, g2, g3, N, S);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    dim3 gg((unsigned)((ld + BM - 1) / BM), (N + BM - 1) / BM, batch);
-    k_bwd_gemm<<<gg, 256, 0, st>>>(S, P, N, ld, 1.0f / (float)T, Gm);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (tc_ops) {
+        // split operands, then the contraction on the tensor cores
+        size_t a_bytes = 0;
+        backward_tc_bytes(batch, N, T, &a_bytes);
+        __nv_bfloat16 *A = (__nv_bfloat16 *)tc_ops;
+        __nv_bfloat16 *B = (__nv_bfloat16 *)((uint8_t *)tc_ops + a_bytes);
+        const int64_t NRB = row_blocks(N), NKB = ((int64_t)N + kTileK - 1) / kTileK;
+        const int64_t NRBT = row_blocks((int)ld);
+        dim3 sg((unsigned)NKB, (unsigned)(NRB * 4), batch);
+        k_bwd_s_split<<<sg, 256, 0, st>>>(C, g1, g2, g3, N, NRB, NKB, A);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dim3 pg((unsigned)NKB, (unsigned)(NRBT * 4), batch);
+        k_bwd_pt_split<<<pg, 256, 0, st>>>(P, N, ld, NRBT, NKB, B);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        TcGemm g;
+        g.A = (const uint8_t *)A;
+        g.B = (const uint8_t *)B;
+        g.nrb_a = (int)NRB;
+        g.nrb_b = (int)NRBT;
+        g.nkb = (int)NKB;
+        g.tpe = (int)(NRB * NRBT);
+        g.N = N;
+        g.ld = ld;
+        g.invT = 1.0f / (float)T;
+        g.G = Gm;
+        e = launch_gemm_tc(h, st, g, batch);
+        if (e != cudaSuccess) return e;
+    } else {
+        dim3 sg((N + 31) / 32, (N + 31) / 32, batch);
+        k_bwd_s<<<sg, 256, 0, st>>>(C, g1, g2, g3, N, S);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dim3 gg((unsigned)((ld + BM - 1) / BM), (N + BM - 1) / BM, batch);
+        k_bwd_gemm<<<gg, 256, 0, st>>>(S, P, N, ld, 1.0f / (float)T, Gm);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     BwdTask task{P, Gm, rinv, grad, ld, T};
     if (plan) return launch_hilbert_conv(h->num_sms, st, task, *plan, T, ld, (int64_t)batch * N);
     return launch_hilbert_pow2(h->num_sms, st, log2T, task, twiddle_table(h, log2T),

@@ -12,9 +12,15 @@
 // accumulator and 6 into the Im accumulator; the minus sign of a b^T is the
 // MMA's negate-A bit.
 //
+// The same machinery serves the backward pass's dense contraction
+// Gamma = S P / T (GEMM mode): with A the split rows of S (row i, K = k) and
+// B the split rows of conj(P)^T (row t, K = k), the products above give
+// sum_k S[i][k] P[k][t].  The tile grid is then full (every (I, J)) and the
+// epilogue stores the complex tile instead of read-outs.
+//
 // Accumulation.  The tensor core's FP32 accumulation into TMEM does not
 // round to nearest, and its error grows with the number of K blocks added
-// into one accumulator.  So the K loop runs in chunks (256 samples for BF16,
+// into one accumulator.  So the K loop runs in chunks (512 samples for BF16,
 // 128 for FP16):
 // each chunk accumulates into a fresh TMEM region (two regions, ping-pong),
 // and the epilogue warps drain every finished chunk into FP32 running sums
@@ -60,10 +66,11 @@ constexpr int NEPI_WARPS = 16;               // 4 lane quarters x 4 column quart
 constexpr int NTHREADS = 64 + 32 * NEPI_WARPS;
 constexpr int TMEM_COLS = 512;
 constexpr int ACC_COLS = 256;                 // Re (128) + Im (128)
-// Stages per K chunk, by split: BF16x3 drains every 256 samples, FP16x3 every
+// Stages per K chunk, by split: BF16x3 drains every 512 samples, FP16x3 every
 // 128.  Longer chunks leave the MMAs more slack over the tile-end stores but
-// add accumulation error in proportion (about 5.6e-6 against 2.8e-6 at worst,
-// for a coherent pair); the FP16 split is the accuracy-first mode.
+// add accumulation error (measured full-size worst error against the FP64
+// oracle: 1.1e-6 at 512, 5.3e-7 at 256); the FP16 split is the
+// accuracy-first mode.
 template <uint32_t FMT>
 struct Chunk {
     static constexpr int CH = FMT == 1u ? 16 : 4;
@@ -218,9 +225,19 @@ struct TcArgs {
     TcProblem single;         // the problem when items == nullptr
     const TcProblem *probs;   // group: problem descriptors
     const int4 *items;        // group: (problem, epoch, I, J), longest first
+    TcGemm gemm;              // GEMM mode: the contraction
     int total_items;
     int *status;
 };
+
+// GEMM mode: item t is (epoch, I, J) with J fastest, so CTAs working at the
+// same time share A row blocks and one epoch's B in L2.
+__device__ __forceinline__ void gemm_item(const TcGemm &g, int t, int &e, int &I, int &J) {
+    e = t / g.tpe;
+    const int r = t - e * g.tpe;
+    I = r / g.nrb_b;
+    J = r - I * g.nrb_b;
+}
 
 __device__ __forceinline__ const TcProblem &item_of(const TcArgs &a, int t, int &e, int &I,
                                                     int &J) {
@@ -236,7 +253,7 @@ __device__ __forceinline__ const TcProblem &item_of(const TcArgs &a, int t, int 
     return a.single;
 }
 
-template <uint32_t FMT>
+template <uint32_t FMT, bool GEMM>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_gram_tc(const __grid_constant__ TcArgs args) {
     extern __shared__ uint8_t smem_raw[];
@@ -285,12 +302,24 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             uint32_t pending = 0;        // stages with a copy issued
             uint32_t pend_parity = 0;    // FULL parity each pending copy completes
             for (int t = blockIdx.x; t < args.total_items && !*abort_flag; t += gridDim.x) {
-                int e, I, J;
-                const TcProblem &pb = item_of(args, t, e, I, J);
-                const bool diag = I == J;
-                const uint8_t *pa = pb.P + (size_t)((int64_t)e * pb.nrb + I) * pb.nkb * SIDE_BYTES;
-                const uint8_t *pj = pb.P + (size_t)((int64_t)e * pb.nrb + J) * pb.nkb * SIDE_BYTES;
-                for (int kb = 0; kb < pb.nkb; ++kb) {
+                int e, I, J, nkb;
+                bool diag;
+                const uint8_t *pa, *pj;
+                if constexpr (GEMM) {
+                    const TcGemm &g = args.gemm;
+                    gemm_item(g, t, e, I, J);
+                    diag = false;
+                    nkb = g.nkb;
+                    pa = g.A + (size_t)((int64_t)e * g.nrb_a + I) * nkb * SIDE_BYTES;
+                    pj = g.B + (size_t)((int64_t)e * g.nrb_b + J) * nkb * SIDE_BYTES;
+                } else {
+                    const TcProblem &pb = item_of(args, t, e, I, J);
+                    diag = I == J;
+                    nkb = pb.nkb;
+                    pa = pb.P + (size_t)((int64_t)e * pb.nrb + I) * nkb * SIDE_BYTES;
+                    pj = pb.P + (size_t)((int64_t)e * pb.nrb + J) * nkb * SIDE_BYTES;
+                }
+                for (int kb = 0; kb < nkb; ++kb) {
                     if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status)) break;
                     const uint32_t sa = base + stage * STAGE_BYTES;
                     mbar_expect_tx(FULL(stage), diag ? SIDE_BYTES : 2 * SIDE_BYTES);
@@ -328,10 +357,17 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             bool ok = true;
             for (int t = blockIdx.x; ok && t < args.total_items && !*abort_flag;
                  t += gridDim.x) {
-                int e, I, J;
-                const TcProblem &pb = item_of(args, t, e, I, J);
-                const bool diag = I == J;
-                const int nkb = pb.nkb;
+                int e, I, J, nkb;
+                bool diag;
+                if constexpr (GEMM) {
+                    gemm_item(args.gemm, t, e, I, J);
+                    diag = false;
+                    nkb = args.gemm.nkb;
+                } else {
+                    const TcProblem &pb = item_of(args, t, e, I, J);
+                    diag = I == J;
+                    nkb = pb.nkb;
+                }
                 for (int kb0 = 0; ok && kb0 < nkb; kb0 += Chunk<FMT>::CH) {
                     if (!wait_bar(TEMPTY(buf), buf_phase ^ 1u, abort_flag, args.status)) {
                         ok = false;
@@ -404,13 +440,19 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
         uint32_t buf_phase = 0;
         bool ok = true;
         for (int t = blockIdx.x; ok && t < args.total_items; t += gridDim.x) {
-            int e, I, J;
-            const TcProblem &pb = item_of(args, t, e, I, J);
-            const int N = pb.N;
+            int e, I, J, nkb;
+            const TcProblem *pbp = nullptr;
+            if constexpr (GEMM) {
+                gemm_item(args.gemm, t, e, I, J);
+                nkb = args.gemm.nkb;
+            } else {
+                pbp = &item_of(args, t, e, I, J);
+                nkb = pbp->nkb;
+            }
             float sre[32], sim[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
-            for (int kb0 = 0; kb0 < pb.nkb; kb0 += Chunk<FMT>::CH) {
+            for (int kb0 = 0; kb0 < nkb; kb0 += Chunk<FMT>::CH) {
                 if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status)) {
                     ok = false;
                     break;
@@ -436,9 +478,29 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             }
             if (!ok) break;
             const int i = I * TM + row;
-            const int j0 = J * TN + cq * 32;
-            store_tile_row(pb.out, (int64_t)e * N * N, N, i, j0, I == J, sre, sim, pb.invT,
-                           pb.invT_d, pb.out.diag ? pb.out.diag + e : nullptr);
+            if constexpr (GEMM) {
+                // the complex tile, scaled, as planar FP32 rows [e N + i][2][ld]
+                const TcGemm &g = args.gemm;
+                const int64_t t0 = (int64_t)J * TN + cq * 32;
+                if (i < g.N && t0 < g.ld) {  // ld is a multiple of 32: all 32 or none
+                    float *gr = g.G + ((int64_t)e * g.N + i) * 2 * g.ld + t0;
+#pragma unroll
+                    for (int c = 0; c < 32; c += 4) {
+                        *(float4 *)(gr + c) = make_float4(sre[c] * g.invT, sre[c + 1] * g.invT,
+                                                          sre[c + 2] * g.invT,
+                                                          sre[c + 3] * g.invT);
+                        *(float4 *)(gr + g.ld + c) =
+                            make_float4(sim[c] * g.invT, sim[c + 1] * g.invT,
+                                        sim[c + 2] * g.invT, sim[c + 3] * g.invT);
+                    }
+                }
+            } else {
+                const TcProblem &pb = *pbp;
+                const int N = pb.N;
+                const int j0 = J * TN + cq * 32;
+                store_tile_row(pb.out, (int64_t)e * N * N, N, i, j0, I == J, sre, sim, pb.invT,
+                               pb.invT_d, pb.out.diag ? pb.out.diag + e : nullptr);
+            }
         }
     }
 
@@ -471,10 +533,32 @@ static cudaError_t launch_tc(const Handle *h, cudaStream_t s, const TcArgs &a) {
     if (a.total_items <= 0) return cudaSuccess;
     const int grid = a.total_items < h->num_sms ? a.total_items : h->num_sms;
     const bool fp16 = h->prec == PLV_PREC_FP16X3;
-    auto kern = fp16 ? k_gram_tc<0u> : k_gram_tc<1u>;
+    auto kern = fp16 ? k_gram_tc<0u, false> : k_gram_tc<1u, false>;
     static LaunchSetup ls16, ls_bf;
     int per_sm = 0;
     cudaError_t e = setup_once(fp16 ? ls16 : ls_bf, kern, NTHREADS, SMEM_BYTES, per_sm);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(const Handle *h, cudaStream_t s, const TcGemm &g, int batch) {
+    TcArgs a;
+    a.single = TcProblem{};
+    a.probs = nullptr;
+    a.items = nullptr;
+    a.gemm = g;
+    const int64_t total = (int64_t)g.tpe * batch;
+    if (total > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    a.total_items = (int)total;
+    a.status = h->status;
+    if (a.total_items <= 0) return cudaSuccess;
+    const int grid = a.total_items < h->num_sms ? a.total_items : h->num_sms;
+    // the BF16 split: gradients can exceed the FP16 range
+    auto kern = k_gram_tc<1u, true>;
+    static LaunchSetup ls;
+    int per_sm = 0;
+    cudaError_t e = setup_once(ls, kern, NTHREADS, SMEM_BYTES, per_sm);
     if (e != cudaSuccess) return e;
     kern<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();

@@ -621,8 +621,12 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
     const int64_t ld = padded_len(T);
     const size_t rows = (size_t)batch * N;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // split-precision handles take the contraction to the tensor cores; their
+    // S (split rows) and conj(P)^T operands replace the FP32 S
+    const bool tc = h.prec != PLV_PREC_FP32;
     const size_t bP = up(rows * 2 * ld * 4), bR = up(rows * ld * 4), bG = up(rows * 2 * ld * 4),
-                 bS = up((size_t)batch * 2 * N * N * 4);
+                 bS = tc ? up(backward_tc_bytes(batch, N, T, nullptr))
+                         : up((size_t)batch * 2 * N * N * 4);
     std::lock_guard<std::mutex> lock(h.mu);
     plv_status st = ensure_workspace(h, s, bP + bR + bG + bS);
     if (st != PLV_OK) return st;
@@ -645,7 +649,8 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
                     "plv_backward: recompute");
     if (st != PLV_OK) return st;
     return check_cuda(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,
-                                      g_ciplv, P, rinv, S, Gm, grad_x, plan),
+                                      g_ciplv, P, rinv, tc ? nullptr : S, Gm, grad_x, plan,
+                                      tc ? (void *)S : nullptr),
                       "plv_backward launch");
 }
 

@@ -19,6 +19,16 @@ def h32():
     h.close()
 
 
+# the contraction Gamma = S P / T runs on the CUDA cores (FP32 handle) or on
+# the tensor cores in BF16 hi + lo splits (split handles)
+@pytest.fixture(scope="module", params=["fp32", "bf16x3"])
+def hb(request):
+    import paper_1710_08037_gb300 as plv
+    h = plv.Handle(precision=request.param)
+    yield h
+    h.close()
+
+
 def _grads(rng, B, N, which):
     out = []
     for w in ("plv", "iplv", "ciplv"):
@@ -30,9 +40,8 @@ def _grads(rng, B, N, which):
     return out
 
 
-def _gpu_grad(h, x, gs, prec_forward="fp32"):
-    import paper_1710_08037_gb300 as plv
-    hf = h if prec_forward == "fp32" else plv.Handle(precision=prec_forward)
+def _gpu_grad(h, x, gs):
+    hf = h
     xd = torch.tensor(x, device="cuda", dtype=torch.float32)
     E, N, T = x.shape
     P = hf.plv_analytic(xd)
@@ -47,14 +56,14 @@ def _gpu_grad(h, x, gs, prec_forward="fp32"):
 @pytest.mark.parametrize("which", [("plv",), ("iplv",), ("ciplv",),
                                    ("plv", "iplv", "ciplv")])
 @pytest.mark.parametrize("N,T", [(16, 256), (67, 128), (20, 300)])
-def test_backward_vs_torch_fp64(h32, which, N, T):
+def test_backward_vs_torch_fp64(hb, which, N, T):
     rng = np.random.default_rng(N * 7 + T + len(which))
     B = 2
     x = synth.bandlimited(B, N, T, seed=N + T, fs=1000.0, band=(8, 60),
                           dtype=torch.float64).numpy()
     x = x.astype(np.float32).astype(np.float64)
     gs = _grads(rng, B, N, which)
-    got = _gpu_grad(h32, x, gs)
+    got = _gpu_grad(hb, x, gs)
     ref = np.stack([obw.torch_grad(x[e], *(None if g is None else g[e]
                                            for g in gs)) for e in range(B)])
     scale = np.abs(ref).max()
@@ -63,7 +72,7 @@ def test_backward_vs_torch_fp64(h32, which, N, T):
     assert err < 2e-3 and rel2 < 5e-4, (err, rel2)
 
 
-def test_backward_vs_finite_differences(h32):
+def test_backward_vs_finite_differences(hb):
     """FP64 central differences of the oracle's forward (direct DFT + the
     pairwise loop) at 24 entries, N = 16, T = 256."""
     rng = np.random.default_rng(5)
@@ -72,14 +81,14 @@ def test_backward_vs_finite_differences(h32):
     g1 = rng.standard_normal((N, N))
     g3 = rng.standard_normal((N, N))
     np.fill_diagonal(g3, 0.0)
-    got = _gpu_grad(h32, x, [g1[None], None, g3[None]])[0].reshape(-1)
+    got = _gpu_grad(hb, x, [g1[None], None, g3[None]])[0].reshape(-1)
     ent = rng.choice(N * T, size=24, replace=False)
     fd = obw.fd_grad(x[0], g1, None, g3, entries=ent)
     scale = np.abs(got).max()
     assert np.max(np.abs(got[ent] - fd)) < 2e-3 * scale
 
 
-def test_ciplv_loss_workload_sampled(h32):
+def test_ciplv_loss_workload_sampled(hb):
     """The differentiable-loss workload: 16 recordings, N = 1024, T = 4096,
     loss = sum of ciPLV over a seeded 10 % pair mask; two recordings checked
     against FP64 autograd through plain torch ops."""
@@ -87,10 +96,10 @@ def test_ciplv_loss_workload_sampled(h32):
     x = synth.bandlimited(B, N, T, seed=1005, device="cuda")
     mask = synth.random_pair_mask(N, 0.10, seed=1005, device="cuda")
     g3 = mask.to(torch.float32).expand(B, N, N).contiguous()
-    P = h32.plv_analytic(x)
-    C = h32.plv_gram(P, B, N, T, plv=False, iplv=False, ciplv=False,
-                     C=True)["C"]
-    g = h32.plv_backward(x, C, None, None, g3)
+    P = hb.plv_analytic(x)
+    C = hb.plv_gram(P, B, N, T, plv=False, iplv=False, ciplv=False,
+                    C=True)["C"]
+    g = hb.plv_backward(x, C, None, None, g3)
     torch.cuda.synchronize()
     assert torch.isfinite(g).all()
     for e in (0, 11):
@@ -103,7 +112,7 @@ def test_ciplv_loss_workload_sampled(h32):
         assert rel2 < 1e-3 and err < 5e-3
 
 
-def test_autograd_function(h32):
+def test_autograd_function(hb):
     """connectivity() is a torch.autograd.Function whose backward is
     plv_backward; its gradient matches FP64 autograd of plain torch ops."""
     import paper_1710_08037_gb300 as plv
@@ -111,7 +120,7 @@ def test_autograd_function(h32):
     N, T = 12, 128
     x = rng.standard_normal((1, N, T)).astype(np.float32)
     xd = torch.tensor(x, device="cuda", requires_grad=True)
-    p, ip, cp = plv.connectivity(xd, h32)
+    p, ip, cp = plv.connectivity(xd, hb)
     w = torch.tensor(rng.standard_normal((1, N, N)), device="cuda",
                      dtype=torch.float32)
     (p * w).sum().add((cp * w.transpose(1, 2)).sum()).backward()
@@ -131,3 +140,28 @@ def test_backward_zero_grads_and_validation(h32):
     rc = h32.lib.plv_backward(h32.h, None, xl.data_ptr(), 0, 1, 8, 20000, 20000,
                               C.data_ptr(), C.data_ptr(), None, None, g.data_ptr())
     assert rc == _lib.PLV_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("N,T", [(67, 300), (130, 1000), (200, 129), (33, 4096)])
+def test_tensor_core_contraction_equals_fp32(h32, N, T):
+    """The split-precision backward (S and conj(P)^T as BF16 split rows, the
+    contraction on the tensor cores) against the FP32 CUDA-core backward on
+    the same x and C, at sizes that leave ragged 32- and 128-blocks in both
+    operands."""
+    import paper_1710_08037_gb300 as plv
+    rng = np.random.default_rng(N + T)
+    B = 3
+    x = synth.bandlimited(B, N, T, seed=N * T, band=(8, 60), device="cuda")
+    P = h32.plv_analytic(x)
+    C = h32.plv_gram(P, B, N, T, plv=False, iplv=False, ciplv=False, C=True)["C"]
+    gs = [torch.tensor(rng.standard_normal((B, N, N)), device="cuda",
+                       dtype=torch.float32) for _ in range(3)]
+    ref = h32.plv_backward(x, C, *gs)
+    hs = plv.Handle(precision="bf16x3")
+    got = hs.plv_backward(x, C, *gs)
+    torch.cuda.synchronize()
+    assert hs.plv_sync_status() == 0
+    rel = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+    err = float((got - ref).abs().max() / ref.abs().max())
+    assert rel < 2e-5 and err < 1e-4, (rel, err)
+    hs.close()
