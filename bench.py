@@ -51,6 +51,29 @@ BACKWARD = "backward-ciplv-loss-B16-N1024-T4096"
 BANDS = [(4.0, 8.0), (8.0, 12.0), (13.0, 30.0), (30.0, 45.0), (55.0, 80.0)]
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """The largest of every rank's value (for times: the slowest rank), or
+    the value itself without a process group."""
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_per_step):
+    """Whole-job throughput: the units all ranks processed per second of the
+    slowest rank's step time."""
+    return units_per_rank * world / (ms_per_step / 1e3)
+
+
+def rank_seed(seed, rank):
+    """Each replica generates its own input: the workload's seed plus its
+    rank."""
+    return seed + rank
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -161,7 +184,7 @@ def run_ours(args):
     E, N, T, seed = WORKLOADS[args.workload]
     dev = torch.device("cuda", local)
     h = plv.Handle(precision=args.precision, device=local)
-    x = synth.bandlimited(E, N, T, seed=seed + rank, device=dev)
+    x = synth.bandlimited(E, N, T, seed=rank_seed(seed, rank), device=dev)
     P = h.empty_phasors(E, N, T)
     out = {k: torch.empty((E, N, N), dtype=torch.float32, device=dev)
            for k in ("plv", "iplv", "ciplv")}
@@ -202,13 +225,10 @@ def run_ours(args):
     ms = t0.elapsed_time(t1)
     k1_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
     gram_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
     units = float(N) * N * T * E  # channel-pair x samples per step per rank
-    value = units * world / (ms_step / 1e3)
+    value = job_value(units, world, ms_step)
     device_status = h.plv_sync_status()
 
     # end to end through the C ABI: host x -> device, path, outputs -> host.
@@ -255,11 +275,8 @@ def run_ours(args):
         b_.record(s)
         torch.cuda.synchronize(dev)
         ems = a_.elapsed_time(b_)
-        if dist:
-            tt = torch.tensor([ems], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
-        e2e = {"value": units * world / (ems / args.steps / 1e3), "unit": UNIT,
+        ems = max_over_ranks(ems, dist, dev)
+        e2e = {"value": job_value(units, world, ems / args.steps), "unit": UNIT,
                "h2d_bytes_per_step": int(x.numel() * x.element_size()),
                "d2h_bytes_per_step": int(sum(v.numel() * 4 for v in out.values())),
                "ms_per_step": ems / args.steps,
@@ -289,7 +306,7 @@ def run_ours(args):
         step()  # refresh the split-precision outputs for the comparison
         torch.cuda.synchronize(dev)
         agree = {k: float((out[k] - out32[k]).abs().max()) for k in out}
-        fp32 = {"ms_per_step": ms32, "value": units * world / (ms32 / 1e3),
+        fp32 = {"ms_per_step": ms32, "value": job_value(units, world, ms32),
                 "speedup_of_split_path": ms32 / ms_step,
                 "max_abs_diff_vs_split_path": agree, "steps": n32}
         del out32, P32
@@ -405,7 +422,7 @@ def run_grouped(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     h = plv.Handle(precision=args.precision, device=local)
-    specs = grouped_problems(seed=1004 + rank, nsub=args.subjects)
+    specs = grouped_problems(seed=rank_seed(1004, rank), nsub=args.subjects)
     t_gen = time.perf_counter()
     probs = []
     for (N, T, band, sd) in specs:
@@ -453,13 +470,10 @@ def run_grouped(args):
     ms = sum(p[0].elapsed_time(p[2]) for p in per)
     k1_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
     gram_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
     units = float(sum(N * N * T for (N, T, _, _) in specs))
-    value = units * world / (ms_step / 1e3)
+    value = job_value(units, world, ms_step)
     flops = sum(gram_flops(N, T, 1, args.precision) for (N, T, _, _) in specs)
     peaks, peak_kind = _peaks()
     peak = float(peaks["bf16_tflops"])
@@ -514,7 +528,7 @@ def run_backward(args):
     B, N, T = 16, 1024, 4096
     hf = plv.Handle(precision=args.precision, device=local)
     hb = hf  # split handles take the backward contraction to the tensor cores
-    x = synth.bandlimited(B, N, T, seed=1005 + rank, device=dev)
+    x = synth.bandlimited(B, N, T, seed=rank_seed(1005, rank), device=dev)
     mask = synth.random_pair_mask(N, 0.10, seed=1005, device=dev)
     g3 = mask.to(torch.float32).expand(B, N, N).contiguous()
     P = hf.empty_phasors(B, N, T)
@@ -550,15 +564,12 @@ def run_backward(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = sum(p[0].elapsed_time(p[2]) for p in per)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     fwd_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
     bwd_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
     ms_step = ms / args.steps
     units = float(N) * N * T * B
-    value = units * world / (ms_step / 1e3)
+    value = job_value(units, world, ms_step)
     ld = (T + 31) // 32 * 32
     gemm_flops = 8.0 * N * N * ld * B
     peaks, peak_kind = _peaks()
