@@ -54,11 +54,16 @@ def _load():
             lib.oracle_plv_pairwise.argtypes = [d, d, L, L, d, d, d, d, d]
             lib.oracle_gram_direct.argtypes = [d, d, L, L, d, d]
             lib.oracle_metrics.argtypes = [d, d, L, d, d, d]
+            lib.oracle_plv_time_resolved.argtypes = [d, d, L, L, L, L, L, d, d,
+                                                     d, d, d]
+            lib.oracle_dft_bins.argtypes = [d, L, L, L, L, L, d, d]
+            lib.oracle_coherency_trials.argtypes = [d, d, L, L, L, d, d, d, d, d]
             lib.oracle_set_threads.argtypes = [ctypes.c_int]
             lib.oracle_max_threads.restype = ctypes.c_int
             for f in ("oracle_analytic", "oracle_plv_pairwise_rows",
                       "oracle_plv_pairwise", "oracle_gram_direct",
-                      "oracle_metrics"):
+                      "oracle_metrics", "oracle_plv_time_resolved",
+                      "oracle_dft_bins", "oracle_coherency_trials"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -186,3 +191,56 @@ def connectivity_pairs(x: np.ndarray, pairs_i, pairs_j) -> dict:
     out["ciplv"][diag] = 0.0
     out["c"] = c
     return out
+
+
+def time_resolved(z: np.ndarray, t0: int = 0, L=None) -> dict:
+    """Time-resolved PLV (Eq. 1 / Eq. 8) of trials ``z`` (E, N, T) complex:
+    for samples t0 .. t0+L-1 the mean over trials of exp(i (phi_i - phi_j)),
+    with the read-outs.  Returns dict of (L, N, N) arrays (c complex)."""
+    z = np.asarray(z)
+    E, N, T = z.shape
+    L = T - t0 if L is None else L
+    zr = np.ascontiguousarray(z.real, dtype=np.float64)
+    zi = np.ascontiguousarray(z.imag, dtype=np.float64)
+    out = {k: np.empty((L, N, N)) for k in ("cr", "ci", "plv", "iplv", "ciplv")}
+    rc = _load().oracle_plv_time_resolved(
+        _p(zr), _p(zi), E, N, T, t0, L, _p(out["cr"]), _p(out["ci"]),
+        _p(out["plv"]), _p(out["iplv"]), _p(out["ciplv"]))
+    if rc != 0:
+        raise RuntimeError("oracle_plv_time_resolved failed")
+    return {"c": out["cr"] + 1j * out["ci"], "plv": out["plv"],
+            "iplv": out["iplv"], "ciplv": out["ciplv"]}
+
+
+def dft_bins(x: np.ndarray, f0: int, F: int) -> np.ndarray:
+    """DFT of the real rows of ``x`` (..., T) at bins f0 .. f0+F-1, by the
+    direct sum in FP64.  Returns complex128 (..., F)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    shape = x.shape
+    T = shape[-1]
+    rows = int(np.prod(shape[:-1])) if len(shape) > 1 else 1
+    Xr = np.empty((rows, F))
+    Xi = np.empty((rows, F))
+    rc = _load().oracle_dft_bins(_p(x.reshape(rows, T)), rows, T, T, f0, F,
+                                 _p(Xr), _p(Xi))
+    if rc != 0:
+        raise RuntimeError("oracle_dft_bins failed")
+    return (Xr + 1j * Xi).reshape(shape[:-1] + (F,))
+
+
+def coherency_trials(X: np.ndarray) -> dict:
+    """Coherency across trials (Eq. 12) of ``X`` (E, N, L) complex, per
+    column l: coh (complex), coherence |coh|, imaginary coherency |Im coh|
+    and lagged coherence Im coh / sqrt(1 - Re coh^2), each (L, N, N)."""
+    X = np.asarray(X)
+    E, N, L = X.shape
+    xr = np.ascontiguousarray(X.real, dtype=np.float64)
+    xi = np.ascontiguousarray(X.imag, dtype=np.float64)
+    out = {k: np.empty((L, N, N)) for k in ("cr", "ci", "coh", "icoh", "lcoh")}
+    rc = _load().oracle_coherency_trials(
+        _p(xr), _p(xi), E, N, L, _p(out["cr"]), _p(out["ci"]), _p(out["coh"]),
+        _p(out["icoh"]), _p(out["lcoh"]))
+    if rc != 0:
+        raise RuntimeError("oracle_coherency_trials failed")
+    return {"c": out["cr"] + 1j * out["ci"], "coh": out["coh"],
+            "icoh": out["icoh"], "lcoh": out["lcoh"]}

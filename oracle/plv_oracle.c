@@ -31,6 +31,17 @@
  *     ciPLV is defined as 0 (Eq. 14 is undefined there).
  *   - the diagonal of iPLV and ciPLV is 0 by definition (Im c_ii = 0).
  *
+ * Extensions over trials (the time-resolved PLV and coherency across trials):
+ *   6. the time-resolved PLV of Lachaux et al. (Eq. 1; Eq. 8 is its matrix
+ *      form): for every sample t, c_ij(t) = (1/E) sum_n exp(i (phi_i(t, n) -
+ *      phi_j(t, n))) over the E trials n, then the read-outs of step 4;
+ *   7. the DFT of real rows at selected bins, X[f] = sum_t x[t] w^{f t}
+ *      (the Fourier coefficients of Eq. 10-12), by the direct sum;
+ *   8. coherency across trials (Eq. 12): coh_ij = sum_n X_i(n) conj(X_j(n)) /
+ *      sqrt(sum_n |X_i(n)|^2 sum_n |X_j(n)|^2), with the read-outs of step 4
+ *      (coherence |coh|, imaginary coherency |Im coh|, lagged coherence
+ *      Im coh / sqrt(1 - (Re coh)^2)); a channel of zero power has coh = 0.
+ *
  * Parity is pinned (tests/test_oracle.py) against scipy's FFT-based analytic
  * signal, closed forms for on-bin tones and lagged tones, brute force, and
  * statistical invariants.  No function here is "parity unpinned".
@@ -261,6 +272,132 @@ int oracle_metrics(const double *c_re, const double *c_im, long n, double *plv,
         if (plv) plv[q] = p;
         if (iplv) iplv[q] = ip;
         if (ciplv) ciplv[q] = cp;
+    }
+    return 0;
+}
+
+/*
+ * Step 6: the time-resolved PLV (Eq. 1 / Eq. 8) for samples t0 .. t0+L-1.
+ * z: E x N x T complex (planar re / im, row stride T).  Outputs L x N x N
+ * (row stride N, matrix stride N*N); any output pointer may be NULL.  A
+ * sample with |z| = 0 has no phase and contributes nothing (the normaliser
+ * stays 1/E).
+ */
+int oracle_plv_time_resolved(const double *z_re, const double *z_im, long E,
+                             long N, long T, long t0, long L, double *c_re,
+                             double *c_im, double *plv, double *iplv,
+                             double *ciplv) {
+    if (E < 1 || N < 0 || T < 1 || L < 0 || t0 < 0 || t0 + L > T) return -1;
+    if (N == 0 || L == 0) return 0;
+    int nt = oracle_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1) collapse(2)
+    for (long l = 0; l < L; ++l) {
+        for (long i = 0; i < N; ++i) {
+            const long t = t0 + l;
+            for (long j = 0; j < N; ++j) {
+                double sr = 0.0, si = 0.0;
+                for (long n = 0; n < E; ++n) {
+                    const long qi = (n * N + i) * T + t, qj = (n * N + j) * T + t;
+                    if ((z_re[qi] == 0.0 && z_im[qi] == 0.0) ||
+                        (z_re[qj] == 0.0 && z_im[qj] == 0.0))
+                        continue;
+                    const double d = atan2(z_im[qi], z_re[qi]) - atan2(z_im[qj], z_re[qj]);
+                    sr += cos(d);
+                    si += sin(d);
+                }
+                const double cr = sr / (double)E, ci = si / (double)E;
+                const long o = (l * N + i) * N + j;
+                if (c_re) c_re[o] = cr;
+                if (c_im) c_im[o] = ci;
+                double p, ip, cp;
+                readout(cr, ci, &p, &ip, &cp);
+                if (i == j) { ip = 0.0; cp = 0.0; }
+                if (plv) plv[o] = p;
+                if (iplv) iplv[o] = ip;
+                if (ciplv) ciplv[o] = cp;
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * Step 7: X[r][f] = sum_t x[r][t] exp(-2 pi i (f0 + f) t / T) for f < F, by
+ * the direct sum with an FP64 twiddle table indexed ((f0 + f) t) mod T.
+ * x: rows x T (row stride ldx); X planar re / im, rows x F.
+ */
+int oracle_dft_bins(const double *x, long rows, long T, long ldx, long f0,
+                    long F, double *X_re, double *X_im) {
+    if (rows < 0 || T < 1 || ldx < T || F < 0 || f0 < 0) return -1;
+    double *twc = (double *)malloc(sizeof(double) * (size_t)T);
+    double *tws = (double *)malloc(sizeof(double) * (size_t)T);
+    if (!twc || !tws) { free(twc); free(tws); return -1; }
+    for (long m = 0; m < T; ++m) {
+        twc[m] = cos(2.0 * M_PI * (double)m / (double)T);
+        tws[m] = -sin(2.0 * M_PI * (double)m / (double)T);
+    }
+    int nt = oracle_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(static)
+    for (long r = 0; r < rows; ++r) {
+        for (long f = 0; f < F; ++f) {
+            const long k = (f0 + f) % T;
+            double sr = 0.0, si = 0.0;
+            for (long t = 0; t < T; ++t) {
+                const long m = (k * t) % T;
+                sr += x[r * ldx + t] * twc[m];
+                si += x[r * ldx + t] * tws[m];
+            }
+            X_re[r * F + f] = sr;
+            X_im[r * F + f] = si;
+        }
+    }
+    free(twc);
+    free(tws);
+    return 0;
+}
+
+/*
+ * Step 8: coherency across trials (Eq. 12) for every column l < L (a
+ * frequency bin, or any per-trial complex value).  X: E x N x L complex
+ * (planar, row stride L).  Outputs L x N x N as in step 6.
+ */
+int oracle_coherency_trials(const double *x_re, const double *x_im, long E,
+                            long N, long L, double *c_re, double *c_im,
+                            double *coh, double *icoh, double *lcoh) {
+    if (E < 1 || N < 0 || L < 0) return -1;
+    if (N == 0 || L == 0) return 0;
+    int nt = oracle_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1) collapse(2)
+    for (long l = 0; l < L; ++l) {
+        for (long i = 0; i < N; ++i) {
+            double pii = 0.0;
+            for (long n = 0; n < E; ++n) {
+                const long q = (n * N + i) * L + l;
+                pii += x_re[q] * x_re[q] + x_im[q] * x_im[q];
+            }
+            for (long j = 0; j < N; ++j) {
+                double sr = 0.0, si = 0.0, pjj = 0.0;
+                for (long n = 0; n < E; ++n) {
+                    const long qi = (n * N + i) * L + l, qj = (n * N + j) * L + l;
+                    /* X_i conj(X_j) */
+                    sr += x_re[qi] * x_re[qj] + x_im[qi] * x_im[qj];
+                    si += x_im[qi] * x_re[qj] - x_re[qi] * x_im[qj];
+                    pjj += x_re[qj] * x_re[qj] + x_im[qj] * x_im[qj];
+                }
+                const double den = sqrt(pii * pjj);
+                const double cr = den > 0.0 ? sr / den : 0.0;
+                const double ci = den > 0.0 ? si / den : 0.0;
+                const long o = (l * N + i) * N + j;
+                if (c_re) c_re[o] = cr;
+                if (c_im) c_im[o] = ci;
+                double p, ip, cp;
+                readout(cr, ci, &p, &ip, &cp);
+                if (i == j) { ip = 0.0; cp = 0.0; }
+                if (coh) coh[o] = p;
+                if (icoh) icoh[o] = ip;
+                if (lcoh) lcoh[o] = cp;
+            }
+        }
     }
     return 0;
 }

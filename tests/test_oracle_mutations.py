@@ -3,7 +3,7 @@
 Each case plants one mistake in a temporary copy of the oracle's C source (a
 flipped sign, a dropped term, a transposed index, a wrong mask value or
 normaliser), compiles it, swaps it in, and checks that at least one pin of
-tests/test_oracle.py fails.  CPU only; the committed oracle is untouched.
+tests/test_oracle.py or tests/test_oracle_trials.py fails.  CPU only; the committed oracle is untouched.
 """
 import ctypes
 import os
@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from tests import test_oracle as pins
+from tests import test_oracle_trials as trial_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "plv_oracle.c")
 
@@ -32,6 +33,18 @@ MUTATIONS = {
     "ciplv_denominator": ("double d = (1.0 - cr) * (1.0 + cr);",
                           "double d = (1.0 - cr);"),
     "zero_phase_kept": ("if (!(hi[t] && hj[t])) continue;", ""),
+    # functions over trials
+    "trial_normaliser": ("const double cr = sr / (double)E, ci = si / (double)E;",
+                         "const double cr = sr / (double)T, ci = si / (double)T;"),
+    "trial_index_swapped": ("const double d = atan2(z_im[qi], z_re[qi]) - atan2(z_im[qj], z_re[qj]);",
+                            "const double d = atan2(z_im[qj], z_re[qj]) - atan2(z_im[qi], z_re[qi]);"),
+    "bins_offset_dropped": ("const long k = (f0 + f) % T;", "const long k = f % T;"),
+    "bins_sign": ("tws[m] = -sin(2.0 * M_PI * (double)m / (double)T);",
+                  "tws[m] = sin(2.0 * M_PI * (double)m / (double)T);"),
+    "coh_denominator": ("const double den = sqrt(pii * pjj);",
+                        "const double den = sqrt(pii * pii);"),
+    "coh_conjugate": ("si += x_im[qi] * x_re[qj] - x_re[qi] * x_im[qj];",
+                      "si += x_im[qi] * x_re[qj] + x_re[qi] * x_im[qj];"),
 }
 
 PIN_CALLS = [
@@ -46,6 +59,13 @@ PIN_CALLS = [
     pins.test_metrics_closed_forms,
     pins.test_zero_row_contributes_nothing,
     pins.test_rayleigh_null_mean,
+    trial_pins.test_time_resolved_equals_reformulated_gram_per_sample,
+    trial_pins.test_time_resolved_tones_closed_form,
+    trial_pins.test_time_resolved_rayleigh_null,
+    trial_pins.test_dft_bins_equals_numpy_fft,
+    trial_pins.test_coherency_of_unit_phasors_is_plv_over_trials,
+    trial_pins.test_coherency_closed_form_of_a_scaled_copy,
+    trial_pins.test_coherency_invariances_and_bounds,
 ]
 
 
@@ -68,7 +88,9 @@ def test_pins_catch_mutation(tmp_path, name):
     mut = ctypes.CDLL(so)
     for f in ("oracle_analytic", "oracle_plv_pairwise_rows",
               "oracle_plv_pairwise", "oracle_gram_direct", "oracle_metrics",
-              "oracle_set_threads", "oracle_max_threads"):
+              "oracle_plv_time_resolved", "oracle_dft_bins",
+              "oracle_coherency_trials", "oracle_set_threads",
+              "oracle_max_threads"):
         getattr(mut, f).argtypes = getattr(good, f).argtypes
         getattr(mut, f).restype = getattr(good, f).restype
     failed = 0
