@@ -148,9 +148,7 @@ class ClockSampler:
 # launch by epochs (profiles/k_gram_tc_and_k_hilbert_pairs_bandlimited-N4096-T4096-E4.md).
 # An entry is removed when the kernel changes after its capture.
 TRAFFIC = {
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_gram_tc launch
-    # on bandlimited-N4096-T4096-E4, scaled by epochs (traffic grows with them)
-    ("k_gram_tc", "bandlimited-N4096-T4096-E30", "bf16x3"): (1.945232e9 + 1.038737e9) * 30 / 4,
+
 }
 
 
@@ -628,6 +626,102 @@ def run_backward(args):
         dist.destroy_process_group()
 
 
+TIMERES = "time-resolved-E64-N512-T1000"
+
+
+def run_time_resolved(args):
+    """The time-resolved PLV over trials (Eq. 1 / 8): analytic signal of
+    every trial (FP32 phasors), the trial operands of every sample, and one
+    Gram per sample with K = trials (outputs L x N x N per metric)."""
+    import torch
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    E, N, T = 64, 512, 1000
+    h = plv.Handle(precision=args.precision, device=local)
+    h32 = h._fp32()
+    x = synth.bandlimited(E, N, T, seed=rank_seed(1006, rank), device=dev)
+    ld = plv.phasor_ld(T)
+    V = h32.empty_phasors(E, N, T)
+    P = h.empty_phasors(T, N, E)
+    out = {k: torch.empty((T, N, N), dtype=torch.float32, device=dev)
+           for k in ("plv", "iplv", "ciplv")}
+    s = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(e=None):
+        if e:
+            e[0].record(s)
+        h32.plv_analytic(x, V)
+        if e:
+            e[1].record(s)
+        h.plv_trial_operands(V, E, N, ld, 0, T, "asis", P)
+        if e:
+            e[2].record(s)
+        h.plv_gram(P, T, N, E, out=out)
+        if e:
+            e[3].record(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    per = [[ev(), ev(), ev(), ev()] for _ in range(args.steps)]
+    for p in per:
+        step(p)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(p[0].elapsed_time(p[3]) for p in per), dist, dev)
+    k1_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
+    tr_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
+    gram_ms = statistics.mean(p[2].elapsed_time(p[3]) for p in per)
+    ms_step = ms / args.steps
+    units = float(N) * N * E * T  # channel pairs x trials x samples
+    peaks, peak_kind = _peaks()
+    # the Gram over K = E = 64 trials is output-bound: its algorithmic bytes
+    # are the operands read once and the three full N x N outputs per sample
+    ldE = plv.phasor_ld(E)
+    gram_bytes = T * ((N + 127) // 128 * 128) * ldE * 8 + 3 * 4 * T * N * N
+    roof = {"bound": "hbm", "kernel": "k_gram_tc (batch = samples, K = trials)",
+            "achieved": gram_bytes / (gram_ms / 1e3) / 1e9,
+            "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+            "peak_source": f"{peak_kind} HBM copy", "traffic": None,
+            "launch_ms": gram_ms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    if rank == 0:
+        line = {
+            "metric": "channel-pair·trial·samples/s (N²·E·T/s), time-resolved "
+                      "PLV+iPLV+ciPLV over trials",
+            "value": job_value(units, world, ms_step),
+            "unit": "channel-pair·trial·samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": TIMERES, "E_trials": E, "N": N, "T": T,
+                       "outputs": "3 x T x N x N FP32 (3.1 GB per step)"},
+            "roofline": roof,
+            "parts_ms": {"analytic_fp32": k1_ms, "trial_operands": tr_ms,
+                         "gram": gram_ms},
+            "gpu_launches": 3 * args.steps, "clocks": clk,
+            "device_status": h.plv_sync_status()}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(E, N, T, seed, nsub):
     """The FP64 oracle as it stands, on a bounded sample of the same
     workload: one epoch, a random subset S of ``nsub`` channels; direct-DFT
@@ -699,7 +793,7 @@ def main():
                     default="bf16x3")
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the split one")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED, BACKWARD],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED, BACKWARD, TIMERES],
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--subjects", type=int, default=256,
                     help="subjects of the grouped workload")
@@ -719,6 +813,8 @@ def main():
         run_grouped(args)
     elif args.workload == BACKWARD:
         run_backward(args)
+    elif args.workload == TIMERES:
+        run_time_resolved(args)
     else:
         run_ours(args)
 

@@ -243,6 +243,37 @@ plv_status plv_backward(plv_handle *h, void *stream, const void *x,
                         const void *C, const float *g_plv, const float *g_iplv,
                         const float *g_ciplv, float *grad_x);
 
+/* Normalisation of plv_trial_operands. */
+enum {
+    PLV_TRIAL_ASIS = 0, /* values as given (unit phasors: Eq. 1 / Eq. 8)  */
+    PLV_TRIAL_RMS = 1   /* divided by their RMS over trials (Eq. 12)     */
+};
+
+/* Operands of a Gram over trials, one problem per column l (a time sample
+ * or a frequency bin).  The time-resolved PLV of Lachaux et al. (Eq. 1;
+ * Eq. 8 is its matrix form) and coherency across trials (Eq. 12) are the
+ * Gram of Eq. 7 with the E trials as the summation index:
+ *   V    : float, FP32 planar rows [E][N][2][ldv] (Re plane, Im plane), the
+ *          layout an FP32 handle's plv_analytic / plv_normalize writes, or
+ *          any per-trial complex values in that layout (e.g. from
+ *          plv_dft_bins).
+ *   l0, L: the columns taken, 0 <= l0 and l0 + L <= ldv.
+ *   mode : PLV_TRIAL_ASIS: row i of problem l is (V[0][i][l0+l], ...,
+ *          V[E-1][i][l0+l]).  With unit phasors, plv_gram then gives the
+ *          time-resolved PLV, iPLV and ciPLV of Eq. 1, 13, 14 (1/E over the
+ *          trials).
+ *          PLV_TRIAL_RMS: each row divided by sqrt(mean_n |V[n][i][l0+l]|^2)
+ *          first (a zero row stays zero).  plv_gram then gives the coherency
+ *          of Eq. 12, its magnitude (coherence), |Im| (imaginary coherency)
+ *          and Im / sqrt(1 - Re^2) (lagged coherence).
+ *   P    : plv_phasor_bytes(h, L, N, E) bytes in the handle's operand layout,
+ *          written completely: the input of plv_gram(h, stream, P, L, N, E,
+ *          ...), whose outputs are [L][N][N].
+ * 1 <= E, 0 <= N <= 65408.  Errors: PLV_ERR_INVALID (sizes, NULL or
+ * misaligned pointers: V 4-byte, P 16-byte), PLV_ERR_UNSUPPORTED (N). */
+plv_status plv_trial_operands(plv_handle *h, void *stream, const float *V, int E, int N,
+                              int64_t ldv, int l0, int L, int mode, void *P);
+
 /* Size of the fixed scratch array behind plv_backward_noalloc: 64 MiB. */
 #define PLV_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 

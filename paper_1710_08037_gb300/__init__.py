@@ -67,6 +67,9 @@ class Handle:
         self.h = h
 
     def close(self):
+        if getattr(self, "_h32", None) is not None:
+            self._h32.close()
+            self._h32 = None
         if getattr(self, "h", None):
             self.lib.plv_destroy(self.h)
             self.h = None
@@ -230,6 +233,54 @@ class Handle:
         _lib.check(self.lib.plv_gram_grouped(self.h, _stream(self.device),
                                              group.g), self.h)
         return group.problems
+
+    def plv_trial_operands(self, V, E, N, ldv, l0, L, mode="asis", P=None):
+        """Operands of the Gram over trials (Eq. 1 / 8 with mode "asis",
+        Eq. 12 with mode "rms") from FP32 planar rows V [E][N][2][ldv]:
+        columns l0 .. l0+L-1 become L problems of N rows and E samples."""
+        assert V.is_cuda and V.dtype == torch.float32 and V.is_contiguous()
+        assert V.numel() >= E * N * 2 * ldv
+        if P is None:
+            P = self.empty_phasors(L, N, E)
+        m = {"asis": _lib.PLV_TRIAL_ASIS, "rms": _lib.PLV_TRIAL_RMS}[mode]
+        _lib.check(self.lib.plv_trial_operands(self.h, _stream(self.device),
+                                               _ptr(V), E, N, ldv, l0, L, m,
+                                               _ptr(P)), self.h)
+        return P
+
+    def _fp32(self):
+        """This handle if it is FP32, else an FP32 handle on the same device
+        (for FP32 planar per-trial values)."""
+        if self.precision == PLV_PREC_FP32:
+            return self
+        if getattr(self, "_h32", None) is None:
+            self._h32 = Handle("fp32", device=self.device.index)
+        return self._h32
+
+    def time_resolved(self, x, l0=0, L=None, C=False, out=None):
+        """Time-resolved PLV, iPLV, ciPLV over trials (Eq. 1 / 8, 13, 14) of
+        x (E trials, N, T) at samples l0 .. l0+L-1: dict of (L, N, N)."""
+        E, N, T = x.shape
+        L = T - l0 if L is None else L
+        if l0 < 0 or L < 0 or l0 + L > T:
+            raise PlvError(_lib.PLV_ERR_INVALID, "samples out of range")
+        V = self._fp32().plv_analytic(x)
+        P = self.plv_trial_operands(V, E, N, phasor_ld(T), l0, L, "asis")
+        return self.plv_gram(P, L, N, E, C=C, out=out)
+
+    def coherency(self, X, C=False, out=None):
+        """Coherency across trials (Eq. 12) of per-trial complex values X
+        (E, N, L) on the device: coherence |coh|, imaginary coherency
+        |Im coh| and lagged coherence Im coh / sqrt(1 - Re coh^2) under the
+        keys plv, iplv, ciplv, each (L, N, N)."""
+        assert X.is_cuda and X.is_complex() and X.dim() == 3
+        E, N, L = X.shape
+        ldv = phasor_ld(L)
+        V = torch.zeros((E, N, 2, ldv), dtype=torch.float32, device=X.device)
+        V[:, :, 0, :L] = X.real
+        V[:, :, 1, :L] = X.imag
+        P = self.plv_trial_operands(V, E, N, ldv, 0, L, "rms")
+        return self.plv_gram(P, L, N, E, C=C, out=out)
 
     def plv_sync_status(self) -> int:
         v = ctypes.c_int(0)

@@ -29,6 +29,8 @@ PLV_OUT_PLV = 1
 PLV_OUT_IPLV = 2
 PLV_OUT_CIPLV = 4
 PLV_OUT_C = 8
+PLV_TRIAL_ASIS = 0
+PLV_TRIAL_RMS = 1
 
 STATUS_NAMES = {0: "PLV_OK", 1: "PLV_ERR_INVALID", 2: "PLV_ERR_ALLOC",
                 3: "PLV_ERR_CUDA", 4: "PLV_ERR_UNSUPPORTED",
@@ -60,6 +62,7 @@ SIGNATURES = {
     "plv_group_create": (_i, [_vp, _vp, _i, _u, ctypes.POINTER(_vp)]),
     "plv_gram_grouped": (_i, [_vp, _vp, _vp]),
     "plv_analytic_grouped": (_i, [_vp, _vp, _vp]),
+    "plv_trial_operands": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _i, _i, _vp]),
     "plv_group_destroy": (_i, [_vp]),
     "plv_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
 }

@@ -241,6 +241,9 @@ cudaError_t launch_gram_tc_group(const Handle *h, cudaStream_t s, const TcProble
                                  const int4 *items, int nitems);
 // Zero the diagonal-check outputs of every problem of a group.
 cudaError_t launch_zero_group_diag(cudaStream_t s, const TcProblem *probs, int nprob);
+// Operands of a Gram over trials (k_trials.cu): one problem per column.
+cudaError_t launch_trial_operands(const Handle *h, cudaStream_t s, const float *V, int E, int N,
+                                  int64_t ldv, int l0, int L, int rms, void *P);
 // K6: read-outs from a stored C.
 cudaError_t launch_metrics(cudaStream_t s, const float2 *C, int batch, int N,
                            float *plv, float *iplv, float *ciplv);

@@ -120,4 +120,57 @@ __device__ __forceinline__ void store_tile_row(const GramOut &o, int64_t eNN, in
     }
 }
 
+// One metric of an off-diagonal Gram entry (re, im already scaled): the same
+// arithmetic as readout(), so both store paths give identical bits.
+__device__ __forceinline__ float metric_of(int m, float re, float im) {
+    if (m == 0) return sqrtf(fmaf(re, re, im * im));
+    if (m == 1) return fabsf(im);
+    const float d = ciplv_den(re);
+    return d > 0.0f ? im / sqrtf(d) : 0.0f;
+}
+
+// The store of one warp's 32 x 32 block of an interior off-diagonal tile:
+// lane l holds row i0 + l, columns j0 .. j0+31 (unscaled sums).  Every row,
+// column and output of the block is in range, N % 4 == 0 and the outputs
+// are 16-byte aligned (the caller checks; the condition is warp-uniform).
+// Per metric and per 8-column quarter:
+//   - mirrored store (j, i) straight from registers: for each column the
+//     warp writes 32 consecutive floats (one 128-byte line);
+//   - row-wise store through the warp's 32 x 8 staging tile S (1 KB; the
+//     16-byte chunk q of row r sits at chunk q ^ ((r >> 2) & 1), so writes
+//     and reads are free of bank conflicts): each instruction writes 16 rows
+//     x 32 contiguous bytes (whole sectors) instead of 32 rows x 16 bytes.
+__device__ __forceinline__ void store_tile_staged(const GramOut &o, int64_t eNN, int N, int i0,
+                                                  int j0, int lane, const float (&sre)[32],
+                                                  const float (&sim)[32], float invT,
+                                                  float *S) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        float *out = m == 0 ? o.plv : (m == 1 ? o.iplv : o.ciplv);
+        if (!out) continue;
+        const float sgn = m == 2 ? -1.0f : 1.0f;  // ciPLV is antisymmetric
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                v[c] = metric_of(m, sre[8 * h + c] * invT, sim[8 * h + c] * invT);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                out[eNN + (int64_t)(j0 + 8 * h + c) * N + i0 + lane] = sgn * v[c];
+            __syncwarp();  // the previous round's reads of S are done
+            const int sw = (lane >> 2) & 1;
+            *(float4 *)(S + lane * 8 + 4 * sw) = make_float4(v[0], v[1], v[2], v[3]);
+            *(float4 *)(S + lane * 8 + 4 * (1 ^ sw)) = make_float4(v[4], v[5], v[6], v[7]);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int r = 16 * k + (lane >> 1), qq = lane & 1;
+                const float4 w = *(const float4 *)(S + r * 8 + 4 * (qq ^ ((r >> 2) & 1)));
+                *(float4 *)(out + eNN + (int64_t)(i0 + r) * N + j0 + 8 * h + 4 * qq) = w;
+            }
+        }
+    }
+}
+
 }  // namespace plv

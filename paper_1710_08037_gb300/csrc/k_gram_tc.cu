@@ -76,7 +76,13 @@ struct Chunk {
     static constexpr int CH = FMT == 1u ? 16 : 4;
 };
 constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s bound on any wait
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align*/ + 256;
+// per epilogue warp, a 32-row x 8-column FP32 staging tile for the row-wise
+// stores (after the operand ring and the barriers)
+constexpr int STAGE_TILE_FLOATS = 32 * 8;
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 /*align*/ + BAR_BYTES +
+                           NEPI_WARPS * STAGE_TILE_FLOATS * 4;
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 
 enum { P_RH = 0, P_RL = 1, P_IH = 2, P_IL = 3 };
 
@@ -264,6 +270,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
     // bars: full[0..S), empty[0..S), tfull[2], tempty[2]
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NSTAGE + 4);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    float *stage_tiles = (float *)(gbase + NSTAGE * STAGE_BYTES + BAR_BYTES);
     const uint32_t bar0 = smem_u32(bars);
     auto FULL = [&](int s) { return bar0 + 8u * s; };
     auto EMPTY = [&](int s) { return bar0 + 8u * (NSTAGE + s); };
@@ -498,8 +505,17 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                 const TcProblem &pb = *pbp;
                 const int N = pb.N;
                 const int j0 = J * TN + cq * 32;
-                store_tile_row(pb.out, (int64_t)e * N * N, N, i, j0, I == J, sre, sim, pb.invT,
-                               pb.invT_d, pb.out.diag ? pb.out.diag + e : nullptr);
+                // warp-uniform: interior off-diagonal tiles without C take the
+                // staged stores; edges, diagonal tiles and C the element path
+                const bool staged = pb.out.vec_ok && I != J && !pb.out.C &&
+                                    (I + 1) * TM <= N && j0 + 32 <= N;
+                if (staged)
+                    store_tile_staged(pb.out, (int64_t)e * N * N, N, I * TM + q * 32, j0, lane,
+                                      sre, sim, pb.invT,
+                                      stage_tiles + (warp - 2) * STAGE_TILE_FLOATS);
+                else
+                    store_tile_row(pb.out, (int64_t)e * N * N, N, i, j0, I == J, sre, sim,
+                                   pb.invT, pb.invT_d, pb.out.diag ? pb.out.diag + e : nullptr);
             }
         }
     }

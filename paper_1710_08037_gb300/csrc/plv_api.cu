@@ -578,6 +578,25 @@ plv_status plv_group_destroy(plv_group *g) {
     return PLV_OK;
 }
 
+plv_status plv_trial_operands(plv_handle *hp, void *stream, const float *V, int E, int N,
+                              int64_t ldv, int l0, int L, int mode, void *P) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_trial_operands: handle is NULL");
+    if (E < 1 || N < 0 || L < 0 || l0 < 0 || ldv < 0 || (int64_t)l0 + L > ldv)
+        return fail(PLV_ERR_INVALID, "plv_trial_operands: bad sizes E=%d N=%d ldv=%lld l0=%d L=%d",
+                    E, N, (long long)ldv, l0, L);
+    if (mode != PLV_TRIAL_ASIS && mode != PLV_TRIAL_RMS)
+        return fail(PLV_ERR_INVALID, "plv_trial_operands: unknown mode %d", mode);
+    if (N > 65408) return fail(PLV_ERR_UNSUPPORTED, "plv_trial_operands: N = %d > 65408", N);
+    if (N == 0 || L == 0) return PLV_OK;
+    if (!V || !P) return fail(PLV_ERR_INVALID, "plv_trial_operands: NULL pointer");
+    if (((uintptr_t)V % 4) != 0 || ((uintptr_t)P % 16) != 0)
+        return fail(PLV_ERR_INVALID, "plv_trial_operands: misaligned pointer");
+    PLV_GUARD(&hp->h);
+    return check_cuda(launch_trial_operands(&hp->h, (cudaStream_t)stream, V, E, N, ldv, l0, L,
+                                            mode == PLV_TRIAL_RMS, P),
+                      "plv_trial_operands launch");
+}
+
 plv_status plv_metrics(plv_handle *hp, void *stream, const void *C, int batch,
                        int N, float *plv, float *iplv, float *ciplv) {
     if (!hp) return fail(PLV_ERR_INVALID, "plv_metrics: handle is NULL");

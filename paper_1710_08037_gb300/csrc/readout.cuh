@@ -7,15 +7,14 @@
 
 namespace plv {
 
-// Denominator of Eq. 14, d = 1 - (Re C)^2, formed as (1 - r)(1 + r).  Where
-// |r| > 1/2 the factors are formed and multiplied in FP64 (the region where
-// 1 - r^2 can cancel as |r| -> 1); elsewhere both factors lie in [1/2, 3/2]
-// and the FP32 product is already correct to one rounding.
+// Denominator of Eq. 14, d = 1 - (Re C)^2, formed as (1 - r)(1 + r) in
+// FP32, which does not cancel: for |r| >= 1/2 the factor 1 - |r| is exact
+// (Sterbenz's lemma: 1 and |r| are within a factor of two) and the other
+// factor lies in [3/2, 2) with at most half an ulp of rounding; below 1/2
+// both factors lie in (1/2, 3/2).  So d carries about one ulp of relative
+// rounding in every range, far below the effect of the input's own error
+// (2 |r| dr).  Forming it in FP64 changes d by at most that ulp.
 __device__ __forceinline__ float ciplv_den(float r) {
-    if (fabsf(r) > 0.5f) {
-        const double rd = (double)r;
-        return (float)((1.0 - rd) * (1.0 + rd));
-    }
     return (1.0f - r) * (1.0f + r);
 }
 
