@@ -148,6 +148,9 @@ class ClockSampler:
 # launch by epochs (profiles/k_gram_tc_and_k_hilbert_pairs_bandlimited-N4096-T4096-E4.md).
 # An entry is removed when the kernel changes after its capture.
 TRAFFIC = {
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_gram_tc launch
+    # on bandlimited-N4096-T4096-E4 (staged-store build), scaled by epochs
+    ("k_gram_tc", "bandlimited-N4096-T4096-E30", "bf16x3"): (2.250376e9 + 0.913603e9) * 30 / 4,
 
 }
 
