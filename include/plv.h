@@ -274,6 +274,20 @@ enum {
 plv_status plv_trial_operands(plv_handle *h, void *stream, const float *V, int E, int N,
                               int64_t ldv, int l0, int L, int mode, void *P);
 
+/* The DFT of real rows at F consecutive bins (the Fourier coefficients of
+ * Eq. 10-12):  X[r][f] = sum_t x[r][t] exp(-2 pi i (f0 + f) t / T).
+ *   x    : real [rows][ldx] (ldx >= T), F32 or F64 (converted to FP32).
+ *   X    : float, FP32 planar rows [rows][2][ldX] (ldX >= F): Re in
+ *          columns 0..F-1 of plane 0, Im in plane 1; columns F..ldX-1 are not
+ *          written.  With rows = E * N this is the V of plv_trial_operands
+ *          (ldv = ldX), whose mode PLV_TRIAL_RMS then gives coherency across
+ *          the E trials (Eq. 12).
+ * FP32 arithmetic on the CUDA cores: twiddles from the exact phase index
+ * ((f0 + f) t) mod T, partial sums per 32 samples.  1 <= T <= 32768,
+ * 0 <= f0, 1 <= F, f0 + F <= T.  Errors: PLV_ERR_INVALID. */
+plv_status plv_dft_bins(plv_handle *h, void *stream, const void *x, plv_dtype dtype, int rows,
+                        int T, int64_t ldx, int f0, int F, float *X, int64_t ldX);
+
 /* Size of the fixed scratch array behind plv_backward_noalloc: 64 MiB. */
 #define PLV_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 

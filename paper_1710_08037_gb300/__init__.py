@@ -268,6 +268,33 @@ class Handle:
         P = self.plv_trial_operands(V, E, N, phasor_ld(T), l0, L, "asis")
         return self.plv_gram(P, L, N, E, C=C, out=out)
 
+    def plv_dft_bins(self, x, f0, F, X=None):
+        """DFT of the real rows of x (..., T) at bins f0 .. f0+F-1, as FP32
+        planar rows (..., 2, ld(F)) on the device."""
+        assert x.is_cuda and x.dim() >= 1
+        T = x.shape[-1]
+        xs = x.reshape(-1, T)
+        if xs.stride(-1) != 1:
+            xs = xs.contiguous()
+        rows = xs.shape[0]
+        ldX = phasor_ld(F)
+        if X is None:
+            X = torch.empty(x.shape[:-1] + (2, ldX), dtype=torch.float32, device=x.device)
+        _lib.check(self.lib.plv_dft_bins(self.h, _stream(self.device), _ptr(xs),
+                                         _dtype_code(xs), rows, T, xs.stride(0),
+                                         f0, F, _ptr(X), ldX), self.h)
+        return X
+
+    def coherency_bins(self, x, f0, F, C=False, out=None):
+        """Coherency across trials (Eq. 12) of real x (E trials, N, T) at
+        DFT bins f0 .. f0+F-1, entirely on the device: coherence, imaginary
+        coherency and lagged coherence under the keys plv, iplv, ciplv,
+        each (F, N, N)."""
+        E, N, T = x.shape
+        V = self.plv_dft_bins(x, f0, F)
+        P = self.plv_trial_operands(V, E, N, phasor_ld(F), 0, F, "rms")
+        return self.plv_gram(P, F, N, E, C=C, out=out)
+
     def coherency(self, X, C=False, out=None):
         """Coherency across trials (Eq. 12) of per-trial complex values X
         (E, N, L) on the device: coherence |coh|, imaginary coherency

@@ -244,6 +244,9 @@ cudaError_t launch_zero_group_diag(cudaStream_t s, const TcProblem *probs, int n
 // Operands of a Gram over trials (k_trials.cu): one problem per column.
 cudaError_t launch_trial_operands(const Handle *h, cudaStream_t s, const float *V, int E, int N,
                                   int64_t ldv, int l0, int L, int rms, void *P);
+// DFT of real rows at selected bins (k_dft.cu), FP32 planar rows out.
+cudaError_t launch_dft_bins(cudaStream_t s, const void *x, plv_dtype dt, int64_t rows, int T,
+                            int64_t ldx, int f0, int F, float *X, int64_t ldX);
 // K6: read-outs from a stored C.
 cudaError_t launch_metrics(cudaStream_t s, const float2 *C, int batch, int N,
                            float *plv, float *iplv, float *ciplv);

@@ -78,13 +78,21 @@ struct Dft<1> {
     __device__ __forceinline__ static void run(float2 (&)[1]) {}
 };
 
-// Pass schedule for T = 2^L: 16 first, then the remainder radix 2^(L mod 4)
-// if any, then radix-16 passes.  For L < 8 the schedule is [16, 2^(L-4)].
+// Elements per thread of the power-of-two engine (its largest radix, R_E),
+// and the registers per thread its launch bounds plan for.
+constexpr int kPow2EPT = 16;
+constexpr int kPow2LogEPT = kPow2EPT == 16 ? 4 : (kPow2EPT == 8 ? 3 : 2);
+constexpr int kPow2Regs = 128;
+
+// Pass schedule for T = 2^L: R_E first, then the remainder radix
+// 2^(L mod log2 R_E) if any, then radix-R_E passes.
 __host__ __device__ constexpr int npasses(int L) {
-    return L / 4 + (L % 4 != 0 ? 1 : 0);
+    return L / kPow2LogEPT + (L % kPow2LogEPT != 0 ? 1 : 0);
 }
 __host__ __device__ constexpr int radix_of(int L, int p) {
-    return (p == 0) ? 16 : ((p == 1 && (L % 4) != 0) ? (1 << (L % 4)) : 16);
+    return (p == 0) ? kPow2EPT
+                    : ((p == 1 && (L % kPow2LogEPT) != 0) ? (1 << (L % kPow2LogEPT))
+                                                          : kPow2EPT);
 }
 __host__ __device__ constexpr int ns_of(int L, int p) {
     return p == 0 ? 1 : ns_of(L, p - 1) * radix_of(L, p - 1);
@@ -102,8 +110,8 @@ template <int T, int R, int NS, int MODE, typename Load>
 __device__ __forceinline__ void stockham(const float2 *src, float2 *dst,
                                          const float2 *__restrict__ tw, int lt,
                                          const Load &load, float *power = nullptr) {
-    constexpr int B = 16 / R;  // butterflies per thread
-    constexpr int Q = T / 16;  // threads per sequence
+    constexpr int B = kPow2EPT / R;  // butterflies per thread
+    constexpr int Q = T / kPow2EPT;  // threads per sequence
     float pw = 0.f;
 #pragma unroll
     for (int q = 0; q < B; ++q) {
@@ -201,7 +209,7 @@ __device__ __forceinline__ float2 unit_phasor_inv(float a, float b, float floor2
 template <int L>
 struct K1Cfg {
     static constexpr int T = 1 << L;
-    static constexpr int Q = T / 16;                  // threads / sequence
+    static constexpr int Q = T / kPow2EPT;            // threads / sequence
     static constexpr int SEQ = Q >= 256 ? 1 : 256 / Q;  // sequences / CTA
     static constexpr int THREADS = Q * SEQ;
     static constexpr int SMEM_SEQ = T + T / 32;         // padded elements
@@ -209,7 +217,8 @@ struct K1Cfg {
     static constexpr size_t SMEM =
         (size_t)SEQ * 2 * SMEM_SEQ * sizeof(float2) + (size_t)SEQ * sizeof(float);
     // resident CTAs per SM the register budget is sized for
-    static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;
+    static constexpr int MIN_BLOCKS = 65536 / (kPow2Regs * THREADS) > 0
+                                          ? 65536 / (kPow2Regs * THREADS) : 1;
 };
 
 // The Hilbert transform of real rows, two rows per complex FFT, for any
@@ -268,7 +277,7 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
 
         const float floor2 = 0x1p-40f * (s_pow[sq] * invT);
 #pragma unroll 4
-        for (int u = 0; u < 16; ++u) {
+        for (int u = 0; u < kPow2EPT; ++u) {
             const int m = lt + u * C::Q;
             const float2 w = w_out[padi(m)];
             task.finish(rs, m, w.x * invT, -w.y * invT, floor2);

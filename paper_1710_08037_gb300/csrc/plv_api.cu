@@ -597,6 +597,24 @@ plv_status plv_trial_operands(plv_handle *hp, void *stream, const float *V, int 
                       "plv_trial_operands launch");
 }
 
+plv_status plv_dft_bins(plv_handle *hp, void *stream, const void *x, plv_dtype dtype, int rows,
+                        int T, int64_t ldx, int f0, int F, float *X, int64_t ldX) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_dft_bins: handle is NULL");
+    if (dtype != PLV_F32 && dtype != PLV_F64)
+        return fail(PLV_ERR_INVALID, "plv_dft_bins: unknown dtype %d", (int)dtype);
+    if (rows < 0 || T < 1 || T > 32768 || ldx < T || f0 < 0 || F < 1 || f0 + F > T || ldX < F)
+        return fail(PLV_ERR_INVALID,
+                    "plv_dft_bins: bad sizes rows=%d T=%d ldx=%lld f0=%d F=%d ldX=%lld", rows, T,
+                    (long long)ldx, f0, F, (long long)ldX);
+    if (rows == 0) return PLV_OK;
+    if (!x || !X) return fail(PLV_ERR_INVALID, "plv_dft_bins: NULL pointer");
+    if (((uintptr_t)x % (dtype == PLV_F32 ? 4 : 8)) != 0 || ((uintptr_t)X % 4) != 0)
+        return fail(PLV_ERR_INVALID, "plv_dft_bins: misaligned pointer");
+    PLV_GUARD(&hp->h);
+    return check_cuda(launch_dft_bins((cudaStream_t)stream, x, dtype, rows, T, ldx, f0, F, X, ldX),
+                      "plv_dft_bins launch");
+}
+
 plv_status plv_metrics(plv_handle *hp, void *stream, const void *C, int batch,
                        int N, float *plv, float *iplv, float *ciplv) {
     if (!hp) return fail(PLV_ERR_INVALID, "plv_metrics: handle is NULL");

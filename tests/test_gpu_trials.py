@@ -112,3 +112,33 @@ def test_trial_operands_rejections(handles):
     P = h.empty_phasors(8, 3, 2)
     rc = h.lib.plv_trial_operands(h.h, None, V.data_ptr(), 2, 3, 32, 0, 8, 7, P.data_ptr())
     assert rc == _lib.PLV_ERR_INVALID                        # unknown mode
+
+
+@pytest.mark.parametrize("T,f0,F", [(256, 3, 20), (1000, 40, 70), (4096, 0, 33), (97, 1, 96)])
+def test_dft_bins_vs_oracle(handles, T, f0, F):
+    """The device DFT at selected bins against the oracle's FP64 direct sum
+    (F > 32 splits over launches; odd and prime T)."""
+    h = handles["fp32"]
+    rows = 300
+    x = synth.bandlimited(1, rows, T, seed=T + F, band=(5, 200))[0].double().numpy()
+    X = h.plv_dft_bins(torch.tensor(x, device="cuda", dtype=torch.float32), f0, F)
+    torch.cuda.synchronize()
+    got = (X[:, 0, :F] + 1j * X[:, 1, :F]).cpu().numpy().astype(np.complex128)
+    ref = oracle.dft_bins(x.astype(np.float32).astype(np.float64), f0, F)
+    rms = np.sqrt(np.mean(x ** 2))
+    err = np.abs(got - ref)
+    assert err.max() < 1e-5 * np.sqrt(T) * rms, err.max() / (np.sqrt(T) * rms)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-6
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_coherency_from_signals_vs_oracle(handles, prec):
+    """x -> DFT at bins -> trial operands (RMS) -> Gram, all on the device,
+    against the oracle's direct DFT and coherency across trials."""
+    h = handles[prec]
+    E, N, T, f0, F = 40, 45, 512, 4, 24
+    x = synth.bandlimited(E, N, T, seed=77, band=(4, 60)).numpy()
+    res = h.coherency_bins(torch.tensor(x, device="cuda"), f0, F)
+    torch.cuda.synchronize()
+    X = oracle.dft_bins(x.astype(np.float64), f0, F)
+    _check(res, oracle.coherency_trials(X), prec, keys=("coh", "icoh", "lcoh"))
