@@ -122,6 +122,84 @@ __device__ __forceinline__ void store_phasor(void *P, const RowAddr<PREC> &ra, i
     }
 }
 
+// Eight consecutive samples m0 .. m0+7 (m0 a multiple of 8) of a row of x.
+template <typename Tin>
+__device__ __forceinline__ void load_x8(const Tin *p, float (&v)[8]) {
+    if constexpr (sizeof(Tin) == 4) {
+        if (((uintptr_t)p & 15) == 0) {
+            const float4 a = __ldg((const float4 *)p), b = __ldg((const float4 *)p + 1);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            return;
+        }
+    } else {
+        if (((uintptr_t)p & 15) == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double2 a = __ldg((const double2 *)p + k);
+                v[2 * k] = (float)a.x;
+                v[2 * k + 1] = (float)a.y;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = ldx_f(p + k);
+}
+
+// Two 16-bit values (a at the lower address) as one 32-bit word, with the
+// rounding of the per-sample store: hi = RN(p), lo = RN(p - hi).
+template <int PREC>
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    if constexpr (PREC == PLV_PREC_FP16X3) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const __half2 l = __floats2half2_rn(a - __low2float(h), b - __high2float(h));
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const __nv_bfloat162 l =
+            __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+// Store eight consecutive phasors m0 .. m0+7 of a row (m0 a multiple of 8):
+// FP32, two 16-byte stores per plane; split layout, one 16-byte chunk (the
+// eight samples of one swizzled chunk of the row) per plane.  Same values
+// as eight store_phasor calls.
+template <int PREC>
+__device__ __forceinline__ void store_phasor8(void *P, const RowAddr<PREC> &ra, int64_t ld,
+                                              int m0, const float2 (&p)[8]) {
+    if constexpr (PREC == PLV_PREC_FP32) {
+        float4 *o = (float4 *)((float *)P + ra.base + m0);
+        o[0] = make_float4(p[0].x, p[1].x, p[2].x, p[3].x);
+        o[1] = make_float4(p[4].x, p[5].x, p[6].x, p[7].x);
+        float4 *q = (float4 *)((float *)P + ra.base + ld + m0);
+        q[0] = make_float4(p[0].y, p[1].y, p[2].y, p[3].y);
+        q[1] = make_float4(p[4].y, p[5].y, p[6].y, p[7].y);
+    } else {
+        const int64_t off = ra.base + (int64_t)(m0 >> 5) * kBlockElems +
+                            ((((m0 & 31) >> 3) ^ ra.sw) << 3);
+        constexpr int64_t ps = kTileRows * kTileK;  // plane stride in a block
+        uint4 rh, rl, ih, il;
+        split2<PREC>(p[0].x, p[1].x, rh.x, rl.x);
+        split2<PREC>(p[2].x, p[3].x, rh.y, rl.y);
+        split2<PREC>(p[4].x, p[5].x, rh.z, rl.z);
+        split2<PREC>(p[6].x, p[7].x, rh.w, rl.w);
+        split2<PREC>(p[0].y, p[1].y, ih.x, il.x);
+        split2<PREC>(p[2].y, p[3].y, ih.y, il.y);
+        split2<PREC>(p[4].y, p[5].y, ih.z, il.z);
+        split2<PREC>(p[6].y, p[7].y, ih.w, il.w);
+        uint16_t *o = (uint16_t *)P + off;
+        *(uint4 *)o = rh;
+        *(uint4 *)(o + ps) = rl;
+        *(uint4 *)(o + 2 * ps) = ih;
+        *(uint4 *)(o + 3 * ps) = il;
+    }
+}
+
 // Forward task: rows of x in, phasors P = z/|z| in the operand layout out
 // (z = x + i H{x}; |z|^2 below the rounding floor counts as |z| = 0).
 template <typename Tin, int PREC>
@@ -149,6 +227,22 @@ struct FwdTask {
     __device__ void finish(const Rows &rs, int m, float h0, float h1, float floor2) const {
         if (rs.x0) store_phasor<PREC>(P, rs.a0, ld, m, unit_phasor(ldx_f(rs.x0 + m), h0, floor2));
         if (rs.x1) store_phasor<PREC>(P, rs.a1, ld, m, unit_phasor(ldx_f(rs.x1 + m), h1, floor2));
+    }
+    // finish() for eight consecutive samples m0 .. m0+7 < ld (m0 % 8 == 0)
+    static constexpr bool kFinish8 = true;
+    __device__ void row8(const Tin *xr, const RowAddr<PREC> &ra, int m0, const float (&h)[8],
+                         float floor2) const {
+        float xv[8];
+        load_x8(xr + m0, xv);
+        float2 p[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) p[k] = unit_phasor(xv[k], h[k], floor2);
+        store_phasor8<PREC>(P, ra, ld, m0, p);
+    }
+    __device__ void finish8(const Rows &rs, int m0, const float (&h0)[8], const float (&h1)[8],
+                            float floor2) const {
+        if (rs.x0) row8(rs.x0, rs.a0, m0, h0, floor2);
+        if (rs.x1) row8(rs.x1, rs.a1, m0, h1, floor2);
     }
     // padding samples T <= m < ld are zero
     __device__ void pad(const Rows &rs, int m) const {
