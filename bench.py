@@ -98,6 +98,9 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Start sampling and wait (at most 3 s) until the sampler runs, so
+        that even a short timed region gets a sample."""
+        self.first = 0
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
@@ -105,6 +108,10 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:
+                time.sleep(0.01)
+            self.first = len(self.lines)  # samples before the timed region
         except Exception:
             self.proc = None
 
@@ -115,6 +122,10 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return None
+        # at least one sample taken from the timed region on (at most 1 s)
+        t0 = time.time()
+        while len(self.lines) <= self.first and time.time() - t0 < 1.0:
+            time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -124,7 +135,7 @@ class ClockSampler:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.first:] or self.lines[-1:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue
@@ -725,6 +736,90 @@ def run_time_resolved(args):
         dist.destroy_process_group()
 
 
+WINDOWS = "sliding-N1024-T4096-W512-hop256-E8"
+
+
+def run_windows(args):
+    """Dynamic PLV: the analytic signal of every epoch, then the Gram of
+    every window of 512 samples at a hop of 256 (15 windows per epoch), one
+    persistent launch over all (epoch, window) matrices."""
+    import torch
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    E, N, T, W, hop = 8, 1024, 4096, 512, 256
+    nw = (T - W) // hop + 1
+    h = plv.Handle(precision=args.precision, device=local)
+    x = synth.bandlimited(E, N, T, seed=rank_seed(1007, rank), device=dev)
+    P = h.empty_phasors(E, N, T)
+    out = {k: torch.empty((E, nw, N, N), dtype=torch.float32, device=dev)
+           for k in ("plv", "iplv", "ciplv")}
+    s = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(e=None):
+        if e:
+            e[0].record(s)
+        h.plv_analytic(x, P)
+        if e:
+            e[1].record(s)
+        h.plv_gram_windows(P, E, N, T, 0, W, hop, nw, out=out)
+        if e:
+            e[2].record(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    per = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    for p in per:
+        step(p)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(p[0].elapsed_time(p[2]) for p in per), dist, dev)
+    k1_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
+    gram_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
+    ms_step = ms / args.steps
+    units = float(N) * N * W * nw * E  # channel pairs x window samples
+    peaks, peak_kind = _peaks()
+    flops = gram_flops(N, W, E * nw, args.precision)
+    split = args.precision != "fp32"
+    roof = {"bound": "tensor" if split else "alu", "kernel": "k_gram_tc (windows)",
+            "achieved": flops / (gram_ms / 1e3) / 1e12,
+            "peak": float(peaks["bf16_tflops"]) if split else
+            152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12,
+            "unit": "TFLOP/s", "peak_source": f"{peak_kind}", "traffic": None,
+            "launch_ms": gram_ms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": job_value(units, world, ms_step), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": WINDOWS, "E": E, "N": N, "T": T, "W": W, "hop": hop,
+                       "windows": nw, "outputs": f"3 x {E * nw} x N x N FP32"},
+            "roofline": roof, "parts_ms": {"analytic": k1_ms, "gram_windows": gram_ms},
+            "gpu_launches": 2 * args.steps, "clocks": clk,
+            "device_status": h.plv_sync_status()}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(E, N, T, seed, nsub):
     """The FP64 oracle as it stands, on a bounded sample of the same
     workload: one epoch, a random subset S of ``nsub`` channels; direct-DFT
@@ -796,7 +891,8 @@ def main():
                     default="bf16x3")
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the split one")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED, BACKWARD, TIMERES],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED, BACKWARD, TIMERES,
+                                                               WINDOWS],
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--subjects", type=int, default=256,
                     help="subjects of the grouped workload")
@@ -818,6 +914,8 @@ def main():
         run_backward(args)
     elif args.workload == TIMERES:
         run_time_resolved(args)
+    elif args.workload == WINDOWS:
+        run_windows(args)
     else:
         run_ours(args)
 

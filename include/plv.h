@@ -160,6 +160,21 @@ plv_status plv_gram(plv_handle *h, void *stream, const void *P, int batch,
                     int N, int T, unsigned out_mask, float *plv, float *iplv,
                     float *ciplv, void *C, double *diag_dev);
 
+/* Sliding-window Grams (dynamic PLV, Eq. 7 restricted to windows of the
+ * samples): for every epoch b and window w < nw of W samples starting at
+ * t0 + w * hop, C = (1/W) sum over the window of P_i conj(P_j), with the
+ * read-outs of plv_gram.
+ *   P        : as for plv_gram(h, stream, P, batch, N, T, ...).
+ *   t0, W, hop: multiples of 32 (the operand layout's sample blocks), W >= 32,
+ *              and every window inside the T samples:
+ *              t0 + (nw - 1) * hop + W <= T.
+ *   outputs  : [batch][nw][N][N] (diag_dev: [batch][nw]); layouts and NULL
+ *              handling as in plv_gram.
+ * Errors: PLV_ERR_INVALID. */
+plv_status plv_gram_windows(plv_handle *h, void *stream, const void *P, int batch, int N,
+                            int T, int t0, int W, int hop, int nw, unsigned out_mask,
+                            float *plv, float *iplv, float *ciplv, void *C, double *diag_dev);
+
 /* One problem of a grouped plan: its phasors P for (batch, N, T) in the
  * handle's operand layout, its Gram outputs (layouts as in plv_gram; NULL
  * outputs are skipped) and, optionally, its real input x for

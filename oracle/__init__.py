@@ -244,3 +244,13 @@ def coherency_trials(X: np.ndarray) -> dict:
         raise RuntimeError("oracle_coherency_trials failed")
     return {"c": out["cr"] + 1j * out["ci"], "coh": out["coh"],
             "icoh": out["icoh"], "lcoh": out["lcoh"]}
+
+
+def windows(z: np.ndarray, t0: int, W: int, hop: int, nw: int) -> dict:
+    """Sliding-window PLV (Eq. 2 over the W samples of each window w < nw,
+    starting at t0 + w hop) of one analytic signal z (N, T), by the pairwise
+    definition on each window's samples.  Returns dict of (nw, N, N) arrays
+    (c complex, plv, iplv, ciplv)."""
+    z = np.asarray(z)
+    res = [pairwise(z[:, t0 + w * hop: t0 + w * hop + W]) for w in range(nw)]
+    return {k: np.stack([r[k] for r in res]) for k in ("c", "plv", "iplv", "ciplv")}

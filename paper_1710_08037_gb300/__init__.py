@@ -144,6 +144,34 @@ class Handle:
                    self.h)
         return res
 
+    def plv_gram_windows(self, P, batch, N, T, t0, W, hop, nw, plv=True, iplv=True,
+                         ciplv=True, C=False, diag=False, out=None):
+        """Sliding-window Grams (Eq. 7 over windows of W samples starting at
+        t0 + w hop, w < nw) with the read-outs: dict of (batch, nw, N, N)."""
+        dev = self.device
+        res = {} if out is None else dict(out)
+
+        def mk(key, want, shape, dtype):
+            if not want:
+                return None
+            if key not in res:
+                res[key] = torch.empty(shape, dtype=dtype, device=dev)
+            return res[key]
+
+        sh = (batch, nw, N, N)
+        o_plv = mk("plv", plv, sh, torch.float32)
+        o_iplv = mk("iplv", iplv, sh, torch.float32)
+        o_ci = mk("ciplv", ciplv, sh, torch.float32)
+        o_C = mk("C", C, sh, torch.complex64)
+        o_d = mk("diag", diag, (batch, nw), torch.float64)
+        mask = ((PLV_OUT_PLV if plv else 0) | (PLV_OUT_IPLV if iplv else 0) |
+                (PLV_OUT_CIPLV if ciplv else 0) | (PLV_OUT_C if C else 0))
+        _lib.check(self.lib.plv_gram_windows(self.h, _stream(dev), _ptr(P), batch, N, T,
+                                             t0, W, hop, nw, mask, _ptr(o_plv),
+                                             _ptr(o_iplv), _ptr(o_ci), _ptr(o_C),
+                                             _ptr(o_d)), self.h)
+        return res
+
     def plv_metrics(self, C):
         """Eq. 7, 13, 14 elementwise on a stored complex64 C (batch, N, N)."""
         assert C.is_cuda and C.dtype == torch.complex64

@@ -216,12 +216,23 @@ cudaError_t launch_gram_tc(const Handle *h, cudaStream_t s, const void *P,
 // in the tiled split layout, sizes and outputs.
 struct TcProblem {
     const uint8_t *P;
-    int batch, N, nrb, nkb, tpe;  // epochs, rows, row blocks, 32-sample blocks, tiles/epoch
+    int batch, N, nrb, nkb, tpe;  // output matrices, rows, row blocks, K blocks, tiles/matrix
+    // sample windows: output matrix e is window w = e % nw of epoch e / nw and
+    // covers K blocks kb0 + w * hop_kb .. + nkb of rows kb_stride blocks long
+    // (one window, kb_stride = nkb and kb0 = 0, for the whole epoch)
+    int kb_stride, nw, kb0, hop_kb;
     float invT;
     double invT_d;
     GramOut out;
 };
 TcProblem make_tc_problem(const void *P, int batch, int N, int T, GramOut out);
+// Sliding windows of W samples (t0, W, hop multiples of 32) over each epoch.
+TcProblem make_tc_window_problem(const void *P, int batch, int N, int T, int t0, int W, int hop,
+                                 int nw, GramOut out);
+cudaError_t launch_gram_tc_windows(const Handle *h, cudaStream_t s, const void *P, int batch,
+                                   int N, int T, int t0, int W, int hop, int nw, GramOut out);
+cudaError_t launch_gram_fp32_windows(const Handle *h, cudaStream_t s, const float *P, int batch,
+                                     int N, int T, int t0, int W, int hop, int nw, GramOut out);
 // The backward pass's contraction on the tensor cores (BF16 split):
 // G[e][i][2][ld] = (1/T) sum_k S[e][i][k] P[e][k][t], from A = split rows of S
 // (row i, K = k; rows padded to nrb_a blocks of 128) and B = split rows of

@@ -30,16 +30,21 @@ __device__ __forceinline__ void tile_of(int t, int &I, int &J) {
     I = t - j * (j + 1) / 2;
 }
 
+// Output matrix e is window w = e % nw of epoch e / nw: samples t0 + w hop
+// .. + kl (kl, t0, hop multiples of BK; one window of kl = ld for the whole
+// epoch).
 __global__ void __launch_bounds__(256, 1)
-k_gram_fp32(const float *__restrict__ P, int N, int T, int64_t ld,
-            int tiles_per_epoch, GramOut out, float invT, double invT_d) {
+k_gram_fp32(const float *__restrict__ P, int N, int kl, int64_t ld,
+            int tiles_per_epoch, GramOut out, float invT, double invT_d, int nw, int64_t t0,
+            int64_t hop) {
     __shared__ __align__(16) float As[2][2][BK][LDS];
     __shared__ __align__(16) float Bs[2][2][BK][LDS];
 
     const int e = blockIdx.x / tiles_per_epoch;
     int I, J;
     tile_of(blockIdx.x - e * tiles_per_epoch, I, J);
-    const float *Pe = P + (int64_t)e * N * 2 * ld;
+    const int eb = e / nw, w = e - eb * nw;
+    const float *Pe = P + (int64_t)eb * N * 2 * ld + t0 + (int64_t)w * hop;
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -75,7 +80,7 @@ k_gram_fp32(const float *__restrict__ P, int N, int T, int64_t ld,
     stash(0);
     __syncthreads();
 
-    const int nk = (int)(ld / BK);
+    const int nk = kl / BK;
     for (int kt = 0; kt < nk; ++kt) {
         const int st = kt & 1;
         if (kt + 1 < nk) {
@@ -156,9 +161,20 @@ cudaError_t launch_gram_fp32(const Handle *h, cudaStream_t s, const float *P,
     const int tiles = nt * (nt + 1) / 2;
     const int64_t grid = (int64_t)tiles * batch;
     if (grid > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    k_gram_fp32<<<(unsigned)grid, 256, 0, s>>>(P, N, T, padded_len(T), tiles,
-                                               out, 1.0f / (float)T,
-                                               1.0 / (double)T);
+    k_gram_fp32<<<(unsigned)grid, 256, 0, s>>>(P, N, (int)padded_len(T), padded_len(T), tiles,
+                                               out, 1.0f / (float)T, 1.0 / (double)T, 1, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_fp32_windows(const Handle *h, cudaStream_t s, const float *P, int batch,
+                                     int N, int T, int t0, int W, int hop, int nw, GramOut out) {
+    const int nt = (N + BM - 1) / BM;
+    const int tiles = nt * (nt + 1) / 2;
+    const int64_t grid = (int64_t)tiles * batch * nw;
+    if (grid > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    if (grid == 0) return cudaSuccess;
+    k_gram_fp32<<<(unsigned)grid, 256, 0, s>>>(P, N, W, padded_len(T), tiles, out,
+                                               1.0f / (float)W, 1.0 / (double)W, nw, t0, hop);
     return cudaGetLastError();
 }
 

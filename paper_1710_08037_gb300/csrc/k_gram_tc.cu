@@ -323,8 +323,11 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     const TcProblem &pb = item_of(args, t, e, I, J);
                     diag = I == J;
                     nkb = pb.nkb;
-                    pa = pb.P + (size_t)((int64_t)e * pb.nrb + I) * nkb * SIDE_BYTES;
-                    pj = pb.P + (size_t)((int64_t)e * pb.nrb + J) * nkb * SIDE_BYTES;
+                    // output matrix e: window w of epoch b
+                    const int b = e / pb.nw, w = e - b * pb.nw;
+                    const int64_t k0 = pb.kb0 + (int64_t)w * pb.hop_kb;
+                    pa = pb.P + (size_t)(((int64_t)b * pb.nrb + I) * pb.kb_stride + k0) * SIDE_BYTES;
+                    pj = pb.P + (size_t)(((int64_t)b * pb.nrb + J) * pb.kb_stride + k0) * SIDE_BYTES;
                 }
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status)) break;
@@ -539,11 +542,31 @@ TcProblem make_tc_problem(const void *P, int batch, int N, int T, GramOut out) {
     p.nrb = (int)row_blocks(N);
     p.nkb = (int)(padded_len(T) / KB);
     p.tpe = p.nrb * (p.nrb + 1) / 2;
+    p.kb_stride = p.nkb;
+    p.nw = 1;
+    p.kb0 = 0;
+    p.hop_kb = 0;
     p.invT = 1.0f / (float)T;
     p.invT_d = 1.0 / (double)T;
     p.out = out;
     return p;
 }
+
+TcProblem make_tc_window_problem(const void *P, int batch, int N, int T, int t0, int W, int hop,
+                                 int nw, GramOut out) {
+    TcProblem p = make_tc_problem(P, batch, N, T, out);
+    p.batch = batch * nw;
+    p.nkb = W / KB;
+    p.kb_stride = (int)(padded_len(T) / KB);
+    p.nw = nw;
+    p.kb0 = t0 / KB;
+    p.hop_kb = hop / KB;
+    p.invT = 1.0f / (float)W;
+    p.invT_d = 1.0 / (double)W;
+    return p;
+}
+
+
 
 static cudaError_t launch_tc(const Handle *h, cudaStream_t s, const TcArgs &a) {
     if (a.total_items <= 0) return cudaSuccess;
@@ -556,6 +579,19 @@ static cudaError_t launch_tc(const Handle *h, cudaStream_t s, const TcArgs &a) {
     if (e != cudaSuccess) return e;
     kern<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc_windows(const Handle *h, cudaStream_t s, const void *P, int batch,
+                                   int N, int T, int t0, int W, int hop, int nw, GramOut out) {
+    TcArgs a;
+    a.single = make_tc_window_problem(P, batch, N, T, t0, W, hop, nw, out);
+    a.probs = nullptr;
+    a.items = nullptr;
+    const int64_t total = (int64_t)a.single.tpe * a.single.batch;
+    if (total > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    a.total_items = (int)total;
+    a.status = h->status;
+    return launch_tc(h, s, a);
 }
 
 cudaError_t launch_gemm_tc(const Handle *h, cudaStream_t s, const TcGemm &g, int batch) {

@@ -312,6 +312,47 @@ plv_status plv_gram(plv_handle *hp, void *stream, const void *P, int batch,
     return check_cuda(launch_gram_tc(&hp->h, s, P, batch, N, T, o), "plv_gram launch");
 }
 
+plv_status plv_gram_windows(plv_handle *hp, void *stream, const void *P, int batch, int N,
+                            int T, int t0, int W, int hop, int nw, unsigned out_mask,
+                            float *plv, float *iplv, float *ciplv, void *C, double *diag_dev) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_gram_windows: handle is NULL");
+    if (batch < 0 || N < 0 || T <= 0 || nw < 0 || t0 < 0 || W < kTileK || hop < 0 ||
+        t0 % kTileK || W % kTileK || hop % kTileK ||
+        (nw > 0 && (int64_t)t0 + (int64_t)(nw - 1) * hop + W > T))
+        return fail(PLV_ERR_INVALID,
+                    "plv_gram_windows: bad windows batch=%d N=%d T=%d t0=%d W=%d hop=%d nw=%d "
+                    "(t0, W, hop multiples of %d; windows inside T)",
+                    batch, N, T, t0, W, hop, nw, kTileK);
+    if (out_mask & ~15u) return fail(PLV_ERR_INVALID, "plv_gram_windows: unknown output bits");
+    if (batch == 0 || N == 0 || nw == 0) return PLV_OK;
+    if (!P || ((uintptr_t)P % 16) != 0)
+        return fail(PLV_ERR_INVALID, "plv_gram_windows: P NULL or misaligned");
+    GramOut o;
+    o.plv = (out_mask & PLV_OUT_PLV) ? plv : nullptr;
+    o.iplv = (out_mask & PLV_OUT_IPLV) ? iplv : nullptr;
+    o.ciplv = (out_mask & PLV_OUT_CIPLV) ? ciplv : nullptr;
+    o.C = (out_mask & PLV_OUT_C) ? (float2 *)C : nullptr;
+    o.diag = diag_dev;
+    if ((o.C && ((uintptr_t)o.C % 8)) || (o.plv && ((uintptr_t)o.plv % 4)) ||
+        (o.iplv && ((uintptr_t)o.iplv % 4)) || (o.ciplv && ((uintptr_t)o.ciplv % 4)))
+        return fail(PLV_ERR_INVALID, "plv_gram_windows: output misaligned");
+    o.vec_ok = (N % 4 == 0) && !((uintptr_t)o.plv % 16) && !((uintptr_t)o.iplv % 16) &&
+               !((uintptr_t)o.ciplv % 16) && !((uintptr_t)o.C % 16);
+    PLV_GUARD(&hp->h);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (o.diag) {
+        plv_status st = check_cuda(cudaMemsetAsync(o.diag, 0, sizeof(double) * batch * nw, s),
+                                   "plv_gram_windows: clear diag");
+        if (st != PLV_OK) return st;
+    }
+    if (hp->h.prec == PLV_PREC_FP32)
+        return check_cuda(launch_gram_fp32_windows(&hp->h, s, (const float *)P, batch, N, T, t0,
+                                                   W, hop, nw, o),
+                          "plv_gram_windows launch");
+    return check_cuda(launch_gram_tc_windows(&hp->h, s, P, batch, N, T, t0, W, hop, nw, o),
+                      "plv_gram_windows launch");
+}
+
 }  // extern "C"
 
 struct plv_group {

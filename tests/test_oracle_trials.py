@@ -1,7 +1,8 @@
-"""Pins of the oracle's functions over trials (CPU): the time-resolved PLV
-(Eq. 1 / Eq. 8), the DFT at selected bins, and coherency across trials
-(Eq. 12), each against something other than itself -- the reformulated
-Gram, closed forms for on-bin tones, the Rayleigh null, numpy's FFT, and
+"""Pins of the oracle's functions over trials and windows (CPU): the
+time-resolved PLV (Eq. 1 / Eq. 8), the DFT at selected bins, coherency
+across trials (Eq. 12) and the sliding-window PLV, each against something
+other than itself -- the reformulated Gram, closed forms for on-bin tones
+and lag changes, the Rayleigh null, numpy's FFT, the tiling identity, and
 invariances that a wrong index, sign or normaliser breaks."""
 import numpy as np
 import pytest
@@ -122,3 +123,33 @@ def test_coherency_invariances_and_bounds():
     # amplitude weighting: coherency is not the PLV of the same values
     p = oracle.time_resolved(X[:, :5], 0, L)["c"]
     assert np.abs(c[:, :5, :5] - p).max() > 1e-3
+
+
+def test_windows_tile_the_whole_signal():
+    """Windows that tile [0, T) without overlap: T c_full = sum_w W c_w (the
+    per-window normaliser and offsets), for random phases."""
+    rng = np.random.default_rng(12)
+    N, T, W = 6, 160, 32
+    z = rng.standard_normal((N, T)) + 1j * rng.standard_normal((N, T))
+    r = oracle.windows(z, 0, W, W, T // W)
+    full = oracle.pairwise(z)["c"]
+    assert np.allclose(W * r["c"].sum(axis=0), T * full, atol=1e-12)
+    one = oracle.windows(z, 0, T, 0, 1)
+    assert np.allclose(one["c"][0], full, atol=1e-14)
+
+
+def test_windows_track_a_lag_change():
+    """The lag between two channels switches at T/2: windows inside each half
+    give exp(i delta) of that half, a window across the switch the weighted
+    mean of the two (closed forms)."""
+    T, W = 256, 64
+    t = np.arange(T)
+    d1, d2 = 0.7, -1.9
+    ph = 2 * np.pi * 0.05 * t
+    z = np.stack([np.exp(1j * ph), np.exp(1j * (ph - np.where(t < T // 2, d1, d2)))])
+    r = oracle.windows(z, 0, W, 32, (T - W) // 32 + 1)
+    for w in range(r["c"].shape[0]):
+        a = w * 32
+        n1 = max(0, min(T // 2, a + W) - a)
+        want = (n1 * np.exp(1j * d1) + (W - n1) * np.exp(1j * d2)) / W
+        assert abs(r["c"][w, 0, 1] - want) < 1e-12, (w, r["c"][w, 0, 1], want)
