@@ -130,9 +130,10 @@ __device__ __forceinline__ float metric_of(int m, float re, float im) {
 }
 
 // The store of one warp's 32 x 32 block of an interior off-diagonal tile:
-// lane l holds row i0 + l, columns j0 .. j0+31 (unscaled sums).  Every row,
-// column and output of the block is in range, N % 4 == 0 and the outputs
-// are 16-byte aligned (the caller checks; the condition is warp-uniform).
+// lane l holds row i0 + l, columns j0 .. j0+31 (unscaled sums).  Every row
+// and column of the block is in range (the caller checks; the condition is
+// warp-uniform).  With vec (N % 4 == 0, outputs 16-byte aligned) the
+// row-wise segments are written as 16-byte vectors, else as four floats.
 // Per metric and per 8-column quarter:
 //   - mirrored store (j, i) straight from registers: for each column the
 //     warp writes 32 consecutive floats (one 128-byte line);
@@ -143,7 +144,7 @@ __device__ __forceinline__ float metric_of(int m, float re, float im) {
 __device__ __forceinline__ void store_tile_staged(const GramOut &o, int64_t eNN, int N, int i0,
                                                   int j0, int lane, const float (&sre)[32],
                                                   const float (&sim)[32], float invT,
-                                                  float *S) {
+                                                  float *S, bool vec) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         float *out = m == 0 ? o.plv : (m == 1 ? o.iplv : o.ciplv);
@@ -167,7 +168,15 @@ __device__ __forceinline__ void store_tile_staged(const GramOut &o, int64_t eNN,
             for (int k = 0; k < 2; ++k) {
                 const int r = 16 * k + (lane >> 1), qq = lane & 1;
                 const float4 w = *(const float4 *)(S + r * 8 + 4 * (qq ^ ((r >> 2) & 1)));
-                *(float4 *)(out + eNN + (int64_t)(i0 + r) * N + j0 + 8 * h + 4 * qq) = w;
+                float *d = out + eNN + (int64_t)(i0 + r) * N + j0 + 8 * h + 4 * qq;
+                if (vec) {
+                    *(float4 *)d = w;
+                } else {
+                    d[0] = w.x;
+                    d[1] = w.y;
+                    d[2] = w.z;
+                    d[3] = w.w;
+                }
             }
         }
     }

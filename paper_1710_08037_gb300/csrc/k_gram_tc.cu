@@ -510,12 +510,12 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                 const int j0 = J * TN + cq * 32;
                 // warp-uniform: interior off-diagonal tiles without C take the
                 // staged stores; edges, diagonal tiles and C the element path
-                const bool staged = pb.out.vec_ok && I != J && !pb.out.C &&
-                                    (I + 1) * TM <= N && j0 + 32 <= N;
+                const bool staged = I != J && !pb.out.C && (I + 1) * TM <= N && j0 + 32 <= N;
                 if (staged)
                     store_tile_staged(pb.out, (int64_t)e * N * N, N, I * TM + q * 32, j0, lane,
                                       sre, sim, pb.invT,
-                                      stage_tiles + (warp - 2) * STAGE_TILE_FLOATS);
+                                      stage_tiles + (warp - 2) * STAGE_TILE_FLOATS,
+                                      pb.out.vec_ok);
                 else
                     store_tile_row(pb.out, (int64_t)e * N * N, N, i, j0, I == J, sre, sim,
                                    pb.invT, pb.invT_d, pb.out.diag ? pb.out.diag + e : nullptr);
