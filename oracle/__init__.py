@@ -54,6 +54,8 @@ def _load():
             lib.oracle_plv_pairwise.argtypes = [d, d, L, L, d, d, d, d, d]
             lib.oracle_gram_direct.argtypes = [d, d, L, L, d, d]
             lib.oracle_metrics.argtypes = [d, d, L, d, d, d]
+            lib.oracle_analytic_band.argtypes = [d, L, L, L, d, d, d]
+            lib.oracle_analytic_band.restype = ctypes.c_int
             lib.oracle_plv_time_resolved.argtypes = [d, d, L, L, L, L, L, d, d,
                                                      d, d, d]
             lib.oracle_dft_bins.argtypes = [d, L, L, L, L, L, d, d]
@@ -254,3 +256,22 @@ def windows(z: np.ndarray, t0: int, W: int, hop: int, nw: int) -> dict:
     z = np.asarray(z)
     res = [pairwise(z[:, t0 + w * hop: t0 + w * hop + W]) for w in range(nw)]
     return {k: np.stack([r[k] for r in res]) for k in ("c", "plv", "iplv", "ciplv")}
+
+
+def analytic_band(x: np.ndarray, band: np.ndarray) -> np.ndarray:
+    """Analytic signal of the band-passed rows of real x (..., T): the band
+    mask (floor(T/2) + 1 real values on the bins 0 .. T/2) and the analytic
+    mask in one transform, by direct DFT in FP64.  Complex128, x's shape."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    shape = x.shape
+    T = shape[-1]
+    band = np.ascontiguousarray(np.asarray(band, dtype=np.float64))
+    assert band.shape == (T // 2 + 1,)
+    rows = int(np.prod(shape[:-1])) if len(shape) > 1 else 1
+    zr = np.empty((rows, T))
+    zi = np.empty((rows, T))
+    rc = _load().oracle_analytic_band(_p(x.reshape(rows, T)), rows, T, T, _p(band),
+                                      _p(zr), _p(zi))
+    if rc != 0:
+        raise RuntimeError("oracle_analytic_band failed")
+    return (zr + 1j * zi).reshape(shape)

@@ -37,6 +37,9 @@
  *      phi_j(t, n))) over the E trials n, then the read-outs of step 4;
  *   7. the DFT of real rows at selected bins, X[f] = sum_t x[t] w^{f t}
  *      (the Fourier coefficients of Eq. 10-12), by the direct sum;
+ *   9. the analytic signal of a band-passed row, band-pass and analytic
+ *      mask in one transform: z = IDFT(h B DFT(x)) for a real band mask B
+ *      (the band-pass then analytic signal of Section III.A);
  *   8. coherency across trials (Eq. 12): coh_ij = sum_n X_i(n) conj(X_j(n)) /
  *      sqrt(sum_n |X_i(n)|^2 sum_n |X_j(n)|^2), with the read-outs of step 4
  *      (coherence |coh|, imaginary coherency |Im coh|, lagged coherence
@@ -88,8 +91,8 @@ static double hmask(long k, long T) {
  * Direct DFT; twiddles from an FP64 table tw[m] = exp(-2 pi i m / T), indexed
  * by (k t) mod T so the argument never grows.  Returns 0, or -1 on bad args.
  */
-int oracle_analytic(const double *x, long rows, long T, long ldx,
-                    double *z_re, double *z_im) {
+static int analytic_impl(const double *x, long rows, long T, long ldx,
+                         const double *band, double *z_re, double *z_im) {
     if (rows < 0 || T < 1 || ldx < T) return -1;
     if (rows == 0) return 0;
     double *twc = (double *)malloc(sizeof(double) * (size_t)T);
@@ -124,7 +127,7 @@ int oracle_analytic(const double *x, long rows, long T, long ldx,
                         idx += k;
                         if (idx >= T) idx -= T;
                     }
-                    double h = hmask(k, T);
+                    double h = hmask(k, T) * (band ? band[k] : 1.0);
                     Xr[k] = h * sr;
                     Xi[k] = h * si;
                 }
@@ -151,6 +154,24 @@ int oracle_analytic(const double *x, long rows, long T, long ldx,
     free(twc);
     free(tws);
     return fail ? -1 : 0;
+}
+
+int oracle_analytic(const double *x, long rows, long T, long ldx,
+                    double *z_re, double *z_im) {
+    return analytic_impl(x, rows, T, ldx, NULL, z_re, z_im);
+}
+
+/*
+ * Step 9: the analytic signal of the band-passed rows, the band-pass and the
+ * analytic mask applied in one transform: Z[k] = h[k] B[k] X[k] with a real
+ * band mask B on the bins k = 0 .. floor(T/2) (B[k] for the negative
+ * frequency -k is irrelevant, h being 0 there), then the inverse DFT as in
+ * step 1.  band: floor(T/2) + 1 values.
+ */
+int oracle_analytic_band(const double *x, long rows, long T, long ldx,
+                         const double *band, double *z_re, double *z_im) {
+    if (!band) return -1;
+    return analytic_impl(x, rows, T, ldx, band, z_re, z_im);
 }
 
 /* Step 4 (Eq. 7, 13, 14): read-outs of one complex c. */

@@ -3,7 +3,8 @@
 Each case plants one mistake in a temporary copy of the oracle's C source (a
 flipped sign, a dropped term, a transposed index, a wrong mask value or
 normaliser), compiles it, swaps it in, and checks that at least one pin of
-tests/test_oracle.py or tests/test_oracle_trials.py fails.  CPU only; the committed oracle is untouched.
+tests/test_oracle.py, tests/test_oracle_trials.py or tests/test_oracle_bands.py
+fails.  CPU only; the committed oracle is untouched.
 """
 import ctypes
 import os
@@ -13,6 +14,7 @@ import pytest
 
 import oracle
 from tests import test_oracle as pins
+from tests import test_oracle_bands as band_pins
 from tests import test_oracle_trials as trial_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "plv_oracle.c")
@@ -43,6 +45,8 @@ MUTATIONS = {
                   "tws[m] = sin(2.0 * M_PI * (double)m / (double)T);"),
     "coh_denominator": ("const double den = sqrt(pii * pjj);",
                         "const double den = sqrt(pii * pii);"),
+    "band_mask_ignored": ("double h = hmask(k, T) * (band ? band[k] : 1.0);",
+                          "double h = hmask(k, T);"),
     "coh_conjugate": ("si += x_im[qi] * x_re[qj] - x_re[qi] * x_im[qj];",
                       "si += x_im[qi] * x_re[qj] + x_re[qi] * x_im[qj];"),
 }
@@ -66,6 +70,8 @@ PIN_CALLS = [
     trial_pins.test_coherency_of_unit_phasors_is_plv_over_trials,
     trial_pins.test_coherency_closed_form_of_a_scaled_copy,
     trial_pins.test_coherency_invariances_and_bounds,
+    band_pins.test_band_selects_one_on_bin_tone,
+    band_pins.test_band_is_linear_in_the_mask,
 ]
 
 
@@ -89,7 +95,7 @@ def test_pins_catch_mutation(tmp_path, name):
     for f in ("oracle_analytic", "oracle_plv_pairwise_rows",
               "oracle_plv_pairwise", "oracle_gram_direct", "oracle_metrics",
               "oracle_plv_time_resolved", "oracle_dft_bins",
-              "oracle_coherency_trials", "oracle_set_threads",
+              "oracle_coherency_trials", "oracle_analytic_band", "oracle_set_threads",
               "oracle_max_threads"):
         getattr(mut, f).argtypes = getattr(good, f).argtypes
         getattr(mut, f).restype = getattr(good, f).restype
