@@ -820,6 +820,107 @@ def run_windows(args):
         dist.destroy_process_group()
 
 
+BANDS_WL = "bands-5-N2048-T4096-E8"
+
+
+def run_bands(args):
+    """The multi-band front end: broadband x, five band masks (4-8, 8-12,
+    13-30, 30-45, 55-80 Hz, 4th-order Butterworth magnitude squared), the
+    band-limited phasors of every band from one forward FFT per row pair,
+    then one grouped Gram over the five bands."""
+    import numpy as np
+    import torch
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    E, N, T = 8, 2048, 4096
+    nb = len(BANDS)
+    h = plv.Handle(precision=args.precision, device=local)
+    x = synth.bandlimited(E, N, T, seed=rank_seed(1008, rank), band=(1.0, 120.0), device=dev)
+    masks = torch.tensor(np.stack([synth.butter_power(T, 1000.0, b) for b in BANDS]),
+                         dtype=torch.float32, device=dev)
+    P = h.plv_analytic_bands(x, masks)
+    probs = [{"P": P[b], "batch": E, "N": N, "T": T} for b in range(nb)]
+    grp = h.plv_group_create(probs)
+    s = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(e=None):
+        if e:
+            e[0].record(s)
+        h.plv_analytic_bands(x, masks, P)
+        if e:
+            e[1].record(s)
+        h.plv_gram_grouped(grp)
+        if e:
+            e[2].record(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    per = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    for p in per:
+        step(p)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(p[0].elapsed_time(p[2]) for p in per), dist, dev)
+    fe_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
+    gram_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
+    # the per-band analytic signal alone (no band-pass), five times, for scale
+    Pa = h.empty_phasors(E, N, T)
+    a, b_ = ev(), ev()
+    h.plv_analytic(x, Pa)
+    a.record(s)
+    for _ in range(nb):
+        h.plv_analytic(x, Pa)
+    b_.record(s)
+    torch.cuda.synchronize(dev)
+    five_hilbert_ms = a.elapsed_time(b_)
+    ms_step = ms / args.steps
+    units = float(N) * N * T * E * nb
+    peaks, peak_kind = _peaks()
+    flops = gram_flops(N, T, E * nb, args.precision)
+    roof = {"bound": "tensor", "kernel": "k_gram_tc (grouped over bands)",
+            "achieved": flops / (gram_ms / 1e3) / 1e12, "peak": float(peaks["bf16_tflops"]),
+            "unit": "TFLOP/s", "peak_source": f"{peak_kind} bf16 dense (burst)",
+            "traffic": None, "launch_ms": gram_ms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # front end bytes: x read once, 8 B of phasor per sample and band written
+    fe_bytes = E * N * T * (4 + 8 * nb)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": job_value(units, world, ms_step), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": BANDS_WL, "E": E, "N": N, "T": T, "bands": BANDS},
+            "roofline": roof,
+            "front_end": {"kernel": "k_hilbert_bands", "ms": fe_ms, "bound": "hbm",
+                          "achieved_GBps": fe_bytes / (fe_ms / 1e3) / 1e9,
+                          "peak": float(peaks["hbm_gbs"]),
+                          "five_plain_analytic_ms": five_hilbert_ms},
+            "gpu_launches": (1 + nb + 1) * args.steps, "clocks": clk,
+            "device_status": h.plv_sync_status()}
+        print(json.dumps(line), flush=True)
+    grp.close()
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(E, N, T, seed, nsub):
     """The FP64 oracle as it stands, on a bounded sample of the same
     workload: one epoch, a random subset S of ``nsub`` channels; direct-DFT
@@ -892,7 +993,7 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the split one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED, BACKWARD, TIMERES,
-                                                               WINDOWS],
+                                                               WINDOWS, BANDS_WL],
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--subjects", type=int, default=256,
                     help="subjects of the grouped workload")
@@ -916,6 +1017,8 @@ def main():
         run_time_resolved(args)
     elif args.workload == WINDOWS:
         run_windows(args)
+    elif args.workload == BANDS_WL:
+        run_bands(args)
     else:
         run_ours(args)
 

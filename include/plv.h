@@ -134,6 +134,21 @@ plv_status plv_analytic(plv_handle *h, void *stream, const void *x,
                         plv_dtype dtype, int batch, int N, int T, int64_t ldx,
                         void *P);
 
+/* The band-pass and Eq. 3 in one transform, for several bands (the
+ * band-pass then analytic signal of Section III.A), fused with Eq. 4: for
+ * band b, z_b = IFFT(h B_b FFT(x)) with a real band mask B_b, then
+ * P_b = z_b / |z_b| in the handle's operand layout.  One forward FFT per
+ * pair of rows serves every band.
+ *   x     : real [batch][N][ldx] (ldx >= T), F32 or F64, broadband.
+ *   masks : float [nbands][T/2 + 1]: B_b at the bins 0 .. T/2 (the mask of
+ *           bin -k is that of k; h zeroes the negative frequencies).
+ *   P     : nbands operand buffers back to back, each
+ *           plv_phasor_bytes(h, batch, N, T) bytes (written completely).
+ * T: powers of two from 128 to 8192 (others: PLV_ERR_UNSUPPORTED). */
+plv_status plv_analytic_bands(plv_handle *h, void *stream, const void *x,
+                              plv_dtype dtype, int batch, int N, int T, int64_t ldx,
+                              const float *masks, int nbands, void *P);
+
 /* Eq. 4 alone, for callers that already hold an analytic signal (for
  * example from a wavelet transform): P = z/|z| in the operand layout.
  *   z    : complex interleaved (re, im), [batch][N][ldz] complex elements,

@@ -106,6 +106,27 @@ class Handle:
                                          _ptr(P)), self.h)
         return P
 
+    def plv_analytic_bands(self, x, masks, P=None):
+        """Band-pass and Eq. 3 + 4 for every band of ``masks`` (nbands,
+        T//2 + 1) float32 on the device, from one forward FFT per row pair:
+        returns the phasors of the bands, (nbands, bytes of one buffer)
+        uint8 (buffer b is P[b])."""
+        assert x.is_cuda and x.dim() == 3
+        B, N, T = x.shape
+        if not (x.stride(-1) == 1 and (N == 1 or x.stride(0) == N * x.stride(1))):
+            x = x.contiguous()
+        ldx = x.stride(1) if N > 1 else max(x.stride(0), T)
+        masks = masks.to(device=x.device, dtype=torch.float32).contiguous()
+        nb = masks.shape[0]
+        assert masks.shape == (nb, T // 2 + 1)
+        nbytes = self.lib.plv_phasor_bytes(self.h, B, N, T)
+        if P is None:
+            P = torch.empty((nb, nbytes), dtype=torch.uint8, device=x.device)
+        _lib.check(self.lib.plv_analytic_bands(self.h, _stream(self.device), _ptr(x),
+                                               _dtype_code(x), B, N, T, ldx, _ptr(masks),
+                                               nb, _ptr(P)), self.h)
+        return P
+
     def plv_normalize(self, z, P=None):
         """Eq. 4 on a given complex analytic signal z (batch, N, T)."""
         assert z.is_cuda and z.dim() == 3 and z.is_complex()

@@ -63,6 +63,7 @@ SIGNATURES = {
     "plv_gram_grouped": (_i, [_vp, _vp, _vp]),
     "plv_analytic_grouped": (_i, [_vp, _vp, _vp]),
     "plv_trial_operands": (_i, [_vp, _vp, _vp, _i, _i, _i64, _i, _i, _i, _vp]),
+    "plv_analytic_bands": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i64, _vp, _i, _vp]),
     "plv_dft_bins": (_i, [_vp, _vp, _vp, _i, _i, _i, _i64, _i, _i, _vp, _i64]),
     "plv_gram_windows": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _u, _vp, _vp, _vp,
                               _vp, _vp]),

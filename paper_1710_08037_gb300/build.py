@@ -34,10 +34,14 @@ def _nvcc() -> str:
 
 
 # Sources compiled more than once, with different -D flags (object suffix,
-# flags): k_fwd.cu holds the K1 launchers of one (input type, task kind).
+# flags): k_fwd.cu and k_bands.cu hold the launchers of one (input type, task
+# kind).
 VARIANTS = {
     "k_fwd.cu": [(f"_{t}_{k}", [f"-DPLV_K1_F64={f64}", f"-DPLV_K1_KIND={k}"])
                  for f64, t in ((0, "f32"), (1, "f64")) for k in range(4)],
+    # the multi-band transform: forward task kinds only
+    "k_bands.cu": [(f"_{t}_{k}", [f"-DPLV_K1_F64={f64}", f"-DPLV_K1_KIND={k}"])
+                   for f64, t in ((0, "f32"), (1, "f64")) for k in range(3)],
 }
 
 

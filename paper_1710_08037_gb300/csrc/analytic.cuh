@@ -39,6 +39,25 @@ cudaError_t k1_conv(const Handle *h, cudaStream_t s, const K1Args &a, const Conv
 template <typename Tin, int KIND>
 cudaError_t k1_conv_group(const Handle *h, cudaStream_t s, const K1Group &g);
 
+// The multi-band analytic signal (k_bands.cu), one instantiation per
+// (Tin, operand precision); T = 2^log2T with kMinLog2Bands <= log2T <= 13.
+template <typename Tin, int PREC>
+cudaError_t launch_bands(const Handle *h, cudaStream_t st, const Tin *x, int64_t ldx, int N,
+                         int64_t rows, int log2T, const float *masks, int nbands, void *P,
+                         int64_t band_bytes);
+#define PLV_BANDS_EXTERN(TIN, KIND)                                                           \
+    extern template cudaError_t launch_bands<TIN, KIND>(const Handle *, cudaStream_t,        \
+                                                        const TIN *, int64_t, int, int64_t,  \
+                                                        int, const float *, int, void *,     \
+                                                        int64_t);
+PLV_BANDS_EXTERN(float, kK1Fp32)
+PLV_BANDS_EXTERN(double, kK1Fp32)
+PLV_BANDS_EXTERN(float, kK1Bf16)
+PLV_BANDS_EXTERN(double, kK1Bf16)
+PLV_BANDS_EXTERN(float, kK1Fp16)
+PLV_BANDS_EXTERN(double, kK1Fp16)
+#undef PLV_BANDS_EXTERN
+
 #define PLV_K1_EXTERN(TIN, KIND)                                                              \
     extern template cudaError_t k1_pow2<TIN, KIND>(const Handle *, cudaStream_t,              \
                                                    const K1Args &);                           \

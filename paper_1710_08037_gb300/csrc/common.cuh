@@ -49,6 +49,7 @@ __host__ __device__ inline int64_t split_offset(int64_t e, int64_t n, int64_t t,
 constexpr int kMinLog2T = 5;
 constexpr int kMaxLog2T = 14;        // twiddle tables
 constexpr int kMaxLog2Direct = 13;   // lengths the two-buffer FFT kernel fits
+constexpr int kMinLog2Bands = 7;     // shortest length of the multi-band transform
 
 // Device status codes written by kernels into the handle's status word.
 enum : int { kDevOk = 0, kDevTimeout = 5 };
@@ -138,6 +139,11 @@ inline cudaError_t setup_once(LaunchSetup &ls, Kern kern, int threads, size_t sm
 // The any-length plan for T (built and cached on first use: allocates).
 plv_status get_conv_plan(Handle &h, int T, const ConvPlan **plan);
 void free_conv_plans(Handle &h);
+// The multi-band analytic signal for T = 2^log2T (k_bands.cu): nbands
+// operand buffers band_bytes apart.
+cudaError_t launch_analytic_bands(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
+                                  int64_t rows, int N, int log2T, int64_t ldx, const float *masks,
+                                  int nbands, void *P, int64_t band_bytes);
 // K1 for lengths the direct FFT does not take (any T up to kMaxConvM / 2).
 cudaError_t launch_analytic_conv(const Handle *h, cudaStream_t s, const void *x,
                                  plv_dtype dt, int64_t rows, int N, int T, int64_t ldx,

@@ -69,6 +69,15 @@ struct Conv {
     }
 };
 template <typename Tin, int KIND>
+struct Bands {
+    static cudaError_t run(const Handle *h, cudaStream_t s, const void *x, int64_t ldx, int N,
+                           int64_t rows, int log2T, const float *masks, int nbands, void *P,
+                           int64_t band_bytes) {
+        return launch_bands<Tin, KIND>(h, s, (const Tin *)x, ldx, N, rows, log2T, masks, nbands,
+                                       P, band_bytes);
+    }
+};
+template <typename Tin, int KIND>
 struct Group {
     static cudaError_t run(const Handle *h, cudaStream_t s, const K1Group &g) {
         return k1_conv_group<Tin, KIND>(h, s, g);
@@ -99,6 +108,13 @@ cudaError_t launch_analytic_pow2(const Handle *h, cudaStream_t s,
                                  int N, int log2T, int64_t ldx, void *P) {
     const K1Args a{x, ldx, P, nullptr, N, 1 << log2T, log2T, (int64_t)1 << log2T, rows};
     return by_kind<Pow2>(h->prec, dt, h, s, a);
+}
+
+cudaError_t launch_analytic_bands(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
+                                  int64_t rows, int N, int log2T, int64_t ldx, const float *masks,
+                                  int nbands, void *P, int64_t band_bytes) {
+    return by_kind<Bands>(h->prec, dt, h, s, x, ldx, N, rows, log2T, masks, nbands, P,
+                          band_bytes);
 }
 
 cudaError_t launch_analytic_group(const Handle *h, cudaStream_t s, plv_dtype dt,

@@ -250,6 +250,40 @@ plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
                       "plv_analytic launch");
 }
 
+plv_status plv_analytic_bands(plv_handle *hp, void *stream, const void *x, plv_dtype dtype,
+                              int batch, int N, int T, int64_t ldx, const float *masks,
+                              int nbands, void *P) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_analytic_bands: handle is NULL");
+    if (batch < 0 || N < 0 || T <= 0 || nbands < 0)
+        return fail(PLV_ERR_INVALID, "plv_analytic_bands: bad sizes batch=%d N=%d T=%d bands=%d",
+                    batch, N, T, nbands);
+    if (dtype != PLV_F32 && dtype != PLV_F64)
+        return fail(PLV_ERR_INVALID, "plv_analytic_bands: unknown dtype %d", (int)dtype);
+    if (ldx < T) return fail(PLV_ERR_INVALID, "plv_analytic_bands: ldx < T");
+    const int L = log2_exact(T);
+    if (L < kMinLog2Bands || L > kMaxLog2Direct)
+        return fail(PLV_ERR_UNSUPPORTED, "plv_analytic_bands: T = %d (powers of two %d .. %d)", T,
+                    1 << kMinLog2Bands, 1 << kMaxLog2Direct);
+    if (batch == 0 || N == 0 || nbands == 0) return PLV_OK;
+    if (!x || !masks || !P) return fail(PLV_ERR_INVALID, "plv_analytic_bands: NULL pointer");
+    const size_t esz = dtype == PLV_F32 ? 4 : 8;
+    if (((uintptr_t)x % esz) != 0 || ((uintptr_t)masks % 4) != 0 || ((uintptr_t)P % 16) != 0)
+        return fail(PLV_ERR_INVALID, "plv_analytic_bands: misaligned pointer");
+    PLV_GUARD(&hp->h);
+    const size_t band_bytes = plv_phasor_bytes(hp, batch, N, T);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (hp->h.prec != PLV_PREC_FP32)
+        for (int b = 0; b < nbands; ++b) {
+            plv_status st = check_cuda(
+                launch_zero_pad_rows(s, (uint8_t *)P + (size_t)b * band_bytes, batch, N, T),
+                "plv_analytic_bands: pad rows");
+            if (st != PLV_OK) return st;
+        }
+    return check_cuda(launch_analytic_bands(&hp->h, s, x, dtype, (int64_t)batch * N, N, L, ldx,
+                                            masks, nbands, P, (int64_t)band_bytes),
+                      "plv_analytic_bands launch");
+}
+
 plv_status plv_normalize(plv_handle *hp, void *stream, const void *z,
                          plv_dtype dtype, int batch, int N, int T, int64_t ldz,
                          void *P) {
