@@ -255,12 +255,12 @@ def run_ours(args):
         xd = torch.empty_like(x)
         nch = max(1, min(E, args.e2e_chunks))
         bounds = [(E * c // nch, E * (c + 1) // nch) for c in range(nch)]
-        streams = [torch.cuda.Stream(dev) for _ in range(2)]
+        streams = [torch.cuda.Stream(dev) for _ in range(max(1, args.e2e_streams))]
         Ps = [h.empty_phasors(max(b - a for a, b in bounds), N, T) for _ in streams]
 
         def e2e_step():
             for c, (a, b) in enumerate(bounds):
-                k = c % 2
+                k = c % len(streams)
                 with torch.cuda.stream(streams[k]):
                     xd[a:b].copy_(xh[a:b], non_blocking=True)
                     h.plv_analytic(xd[a:b], Ps[k])
@@ -292,7 +292,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(x.numel() * x.element_size()),
                "d2h_bytes_per_step": int(sum(v.numel() * 4 for v in out.values())),
                "ms_per_step": ems / args.steps,
-               "pipeline": f"{nch} epoch chunks on 2 streams"}
+               "pipeline": f"{nch} epoch chunks on {len(streams)} streams"}
 
     # the plain FP32 path on the same input: time and agreement
     fp32 = None
@@ -1003,6 +1003,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--e2e-chunks", type=int, default=6)
+    ap.add_argument("--e2e-streams", type=int, default=2)
     ap.add_argument("--ref-sample", type=int, default=192)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
