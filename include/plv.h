@@ -127,7 +127,7 @@ plv_status plv_prepare(plv_handle *h, int T);
  * Supported T: 2 <= T <= 12288.  Powers of two from 32 to 8192 take the
  * direct radix-16 FFT of length T; every other length takes the circular
  * convolution with the periodic Hilbert kernel through an FFT of length
- * M >= 2T - 1 (M = 2^a or 3 * 2^a), whose tables are made on first use of a
+ * M >= 2T - 1 (M = 2^a, 3 * 2^a or 5 * 2^a), whose tables are made on first use of a
  * T (allocates; see plv_prepare).  Others: PLV_ERR_UNSUPPORTED.
  * batch = 0 or N = 0 is a no-op. */
 plv_status plv_analytic(plv_handle *h, void *stream, const void *x,

@@ -1,5 +1,5 @@
 // conv_plan.cu -- host side of the any-length Hilbert transform: choice of
-// the FFT length M >= 2T - 1 (2^a or 3 * 2^a), its radix order, and the
+// the FFT length M >= 2T - 1 (2^a, 3 * 2^a or 5 * 2^a), its radix order, and the
 // spectrum of the periodic discrete Hilbert kernel, computed in FP64 with the
 // same in-place decimation-in-frequency algorithm the device runs, so it
 // lands in the device's output order.  Tables are cached per handle.
@@ -18,15 +18,15 @@ typedef std::complex<double> cd;
 int choose_M(int T) {
     const int need = 2 * T - 1;
     int best = 0;
-    for (int p = 32; p <= kMaxConvM; p *= 2) {
-        if (p >= need && (best == 0 || p < best)) best = p;
-        if (3 * p >= need && 3 * p <= kMaxConvM && (best == 0 || 3 * p < best)) best = 3 * p;
-    }
+    for (int p = 32; p <= kMaxConvM; p *= 2)
+        for (int f : {1, 3, 5})
+            if (f * p >= need && f * p <= kMaxConvM && (best == 0 || f * p < best)) best = f * p;
     return best;
 }
 
-// Radix order of the transform: 3 first for M = 3 * 2^a (every later span is
-// then a power of two), then stages of the largest radix R = kConvMaxRadix
+// Radix order of the transform: 3 or 5 first for M = 3 * 2^a or 5 * 2^a
+// (every later span is then a power of two), then stages of the largest
+// radix R = kConvMaxRadix
 // and one remainder radix 2^(a mod log2 R).  The remainder goes where it leaves the fewest twiddle loads
 // on the device: a stage whose sub-block length (span / R) exceeds the CTA's
 // thread count loads its R - 1 twiddles per butterfly, a later one loads
@@ -34,10 +34,11 @@ int choose_M(int T) {
 std::vector<int> schedule(int M) {
     std::vector<int> head;
     int m = M;
-    if (m % 3 == 0) {
-        head.push_back(3);
-        m /= 3;
-    }
+    for (int f : {3, 5})
+        if (m % f == 0) {
+            head.push_back(f);
+            m /= f;
+        }
     int a = 0;
     while ((1 << a) < m) ++a;
     int lr = 0;  // log2 of the largest radix

@@ -389,7 +389,8 @@ cudaError_t launch_hilbert_pow2(int num_sms, cudaStream_t st, int log2T, const T
 // FFT_M is an in-place decimation-in-frequency transform (digit-reversed
 // output), K is stored in that order (and divided by M), and the inverse is
 // the matching in-place decimation-in-time transform (digit-reversed input,
-// natural output), so no reordering pass is needed.  M = 2^a or 3 * 2^a.
+// natural output), so no reordering pass is needed.  M = 2^a, 3 * 2^a or
+// 5 * 2^a.
 // One sequence (row pair) per CTA; every thread loops over butterflies with
 // only R values in registers, so the shared buffer is single.
 
@@ -404,9 +405,34 @@ __device__ __forceinline__ void dft3(float2 (&a)[3]) {
     a[2] = csub(t2, t3);
 }
 
+// Forward DFT of length 5 with w = exp(-2 pi i / 5): with t1 = a1 + a4,
+// t2 = a2 + a3, t3 = a1 - a4, t4 = a2 - a3,
+//   X1,4 = a0 + c1 t1 + c2 t2 -/+ i (s1 t3 + s2 t4),
+//   X2,3 = a0 + c2 t1 + c1 t2 -/+ i (s2 t3 - s1 t4),
+// c_k = cos(2 pi k / 5), s_k = sin(2 pi k / 5).
+__device__ __forceinline__ void dft5(float2 (&a)[5]) {
+    const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+    const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+    const float2 t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+    const float2 t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+    const float2 b1 = make_float2(fmaf(c2, t2.x, fmaf(c1, t1.x, a[0].x)),
+                                  fmaf(c2, t2.y, fmaf(c1, t1.y, a[0].y)));
+    const float2 b2 = make_float2(fmaf(c1, t2.x, fmaf(c2, t1.x, a[0].x)),
+                                  fmaf(c1, t2.y, fmaf(c2, t1.y, a[0].y)));
+    const float2 d1 = make_float2(fmaf(s2, t4.x, s1 * t3.x), fmaf(s2, t4.y, s1 * t3.y));
+    const float2 d2 = make_float2(fmaf(-s1, t4.x, s2 * t3.x), fmaf(-s1, t4.y, s2 * t3.y));
+    a[0] = cadd(a[0], cadd(t1, t2));
+    // -i d = (d.y, -d.x)
+    a[1] = make_float2(b1.x + d1.y, b1.y - d1.x);
+    a[4] = make_float2(b1.x - d1.y, b1.y + d1.x);
+    a[2] = make_float2(b2.x + d2.y, b2.y - d2.x);
+    a[3] = make_float2(b2.x - d2.y, b2.y + d2.x);
+}
+
 template <int R>
 __device__ __forceinline__ void dft_any(float2 (&a)[R]) {
     if constexpr (R == 3) dft3(a);
+    else if constexpr (R == 5) dft5(a);
     else Dft<R>::run(a);
 }
 
@@ -565,6 +591,7 @@ __device__ __forceinline__ void conv_stage(float2 *s, int M, int R, int lsub,
                 conv_stage_r<16, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2);
             break;
         case 8: conv_stage_r<8, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
+        case 5: conv_stage_r<5, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
         case 4: conv_stage_r<4, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
         case 3: conv_stage_r<3, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;
         default: conv_stage_r<2, KIND>(s, M, lsub, plan, task, rs, T, ld, pw, floor2); break;

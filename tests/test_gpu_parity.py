@@ -50,7 +50,7 @@ def test_analytic_phasors_on_bin_tones(handles, prec, T):
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)
-@pytest.mark.parametrize("T", [2, 3, 33, 100, 500, 997, 1000, 3001, 4097, 8191,
+@pytest.mark.parametrize("T", [2, 3, 33, 100, 500, 600, 997, 1000, 2400, 3001, 4097, 8191,
                                9999, 10000, 12288])
 def test_analytic_any_length_vs_oracle(handles, prec, T):
     """Eq. 3-4 for lengths that are not powers of two (the circular
