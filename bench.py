@@ -404,11 +404,11 @@ def grouped_problems(seed=1004, nsub=256):
 
 
 def _conv_M(T):
-    """Transform length of the any-length engine for T: the smallest 2^a or
-    3 2^a (>= 32) that is >= 2T - 1."""
+    """Transform length of the any-length engine for T: the smallest 2^a,
+    3 2^a or 5 2^a (>= 32) that is >= 2T - 1."""
     need, best, p = 2 * T - 1, None, 32
     while p <= 24576:
-        for m in (p, 3 * p):
+        for m in (p, 3 * p, 5 * p):
             if m >= need and m <= 24576 and (best is None or m < best):
                 best = m
         p *= 2
@@ -454,6 +454,15 @@ def run_grouped(args):
         k1_all()
         h.plv_gram_grouped(grp)
     torch.cuda.synchronize(dev)
+    # launch shapes picked by the library's autotuner (timed on the plan's
+    # own buffers, outside the timed region)
+    tune = None
+    if not args.no_tune:
+        t_tune = time.perf_counter()
+        with torch.cuda.stream(s):
+            tune = h.plv_group_tune(grp, reps=3)
+        torch.cuda.synchronize(dev)
+        tune["seconds"] = time.perf_counter() - t_tune
     g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
         with torch.cuda.graph(g1, stream=s):
@@ -495,8 +504,9 @@ def run_grouped(args):
             "traffic": None, "launch_ms": gram_ms}
     roof["frac"] = roof["achieved"] / roof["peak"]
     k1b = sum(N * T * 12 for (N, T, _, _) in specs)
-    k1_launches = len({min(3, max(0, (_conv_M(T) > 3072) + (_conv_M(T) > 6144)
-                                  + (_conv_M(T) > 12288))) for (_, T, _, _) in specs})
+    k1_launches = (tune["k1_launches"] if tune else
+                   len({min(3, max(0, (_conv_M(T) > 3072) + (_conv_M(T) > 6144)
+                                   + (_conv_M(T) > 12288))) for (_, T, _, _) in specs}))
     device_status = h.plv_sync_status()
     if rank == 0:
         line = {
@@ -508,6 +518,7 @@ def run_grouped(args):
                        "sum_N2T": units, "precision": args.precision,
                        "graphs": "grouped phasor launches in one CUDA graph, "
                                  "grouped Gram in another",
+                       "autotune": tune,
                        "generation_s": t_gen},
             "roofline": roof,
             "k1": {"launches": k1_launches, "ms": k1_ms,
@@ -1000,6 +1011,8 @@ def main():
     ap.add_argument("--sustained", action="store_true",
                     help="roofline against the sustained tensor peak")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="grouped workload: keep the plan's default launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--e2e-chunks", type=int, default=6)

@@ -237,6 +237,64 @@ plv_status plv_gram_grouped(plv_handle *h, void *stream, const plv_group *group)
  * PLV_ERR_INVALID if the plan has no input. */
 plv_status plv_analytic_grouped(plv_handle *h, void *stream, const plv_group *group);
 
+/* What plv_group_tune chose and measured.  Times are medians of `reps`
+ * launches in milliseconds (0 where nothing was timed). */
+typedef struct {
+    float k1_ms_default, k1_ms_tuned;      /* plv_analytic_grouped's launches */
+    float gram_ms_default, gram_ms_tuned;  /* plv_gram_grouped's launch (split precisions) */
+    int k1_lengths;     /* distinct transform lengths M of the plan's analytic signal */
+    int k1_widened;     /* lengths moved to the next wider thread class (2x threads per transform) */
+    int k1_per_sm[4];   /* CTAs per SM of each thread class launch; 0: the occupancy limit */
+    int k1_launches;    /* non-empty thread class launches of plv_analytic_grouped */
+    int gram_schedule;  /* 0: longest first, round-robin; 1: balanced rounds */
+    int gram_tile_cost; /* per-tile cost (in 32-sample K blocks) the balanced rounds assumed */
+    int timed_configs;  /* configurations launched and timed */
+    int cached;         /* 1: the configuration came from the handle's cache; nothing was timed */
+} plv_tune_result;
+
+/* Autotuner of a grouped plan (the batching of Section IV's many subjects
+ * and bands; the paper has no GPU design to follow here).  Times, with CUDA
+ * events on `stream`, candidate launch shapes that leave every result the
+ * same and keeps the fastest in the plan:
+ *   - analytic signal: for each transform length M, the CTA width of the
+ *     any-length engine (its own thread class or the next wider one, timed
+ *     on that length's rows alone), then the CTAs per SM of each class
+ *     launch; the tuned set is kept only if the whole grouped launch is
+ *     faster than the default;
+ *   - Gram (BF16X3 / FP16X3): the tile schedule, i.e. the order of the
+ *     tile list that the persistent CTAs take round-robin: longest first
+ *     (default) or balanced rounds (each round of G tiles dealt to the
+ *     least-loaded CTAs under a per-tile cost of 0, 8 or 32 K blocks).
+ * The candidates run on the plan's own buffers and write the plan's outputs
+ * (with the values any run writes), so the phasors P must be valid for the
+ * Gram part: with an input x the tuner's own analytic-signal launches write
+ * them, without one the caller must have.  reps (1..100) timed launches per
+ * candidate.  The choice is cached in the handle under the plan's work
+ * signature (precision, SM count, transform lengths, tile K lengths): tuning
+ * an equal plan applies it without timing (result->cached = 1).
+ * Synchronises the device and allocates the new work lists: call outside
+ * stream capture (PLV_ERR_INVALID otherwise) and while no launch of the plan
+ * is in flight.  CUDA graphs captured before tuning keep their old lists
+ * (kept alive until plv_group_destroy) and so the old configuration.
+ * result may be NULL. */
+plv_status plv_group_tune(plv_handle *h, void *stream, plv_group *group, int reps,
+                          plv_tune_result *result);
+
+/* Set a plan's launch shapes without timing (to pin or reproduce one of
+ * the tuner's candidates; the paper has no counterpart):
+ *   k1_widen       0: every transform length in its own thread class;
+ *                  1: every length in the next wider class (the widest
+ *                     class stays);
+ *   k1_per_sm      [4] CTAs per SM of each class launch (0: the occupancy
+ *                  limit; values above it act as 0), or NULL for all 0;
+ *   gram_schedule  0: longest first; 1: balanced rounds with per-tile cost
+ *                  gram_tile_cost (0 .. 2^20 K blocks).
+ * Results do not depend on these.  Same synchronisation, allocation and
+ * graph rules as plv_group_tune.  Errors: PLV_ERR_INVALID for values out of
+ * range. */
+plv_status plv_group_configure(plv_handle *h, void *stream, plv_group *group, int k1_widen,
+                               const int *k1_per_sm, int gram_schedule, int gram_tile_cost);
+
 /* Free a plan (synchronises the device).  NULL is ignored. */
 plv_status plv_group_destroy(plv_group *group);
 

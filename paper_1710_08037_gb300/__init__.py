@@ -283,6 +283,29 @@ class Handle:
                                              group.g), self.h)
         return group.problems
 
+    def plv_group_tune(self, group, reps=3):
+        """Autotune the plan's launch shapes (thread class per transform
+        length, CTAs per SM, Gram tile schedule) by timing candidates on its
+        own buffers; returns what was chosen and measured as a dict."""
+        r = _lib.PlvTuneResult()
+        _lib.check(self.lib.plv_group_tune(self.h, _stream(self.device),
+                                           group.g, int(reps),
+                                           ctypes.byref(r)), self.h)
+        out = {name: getattr(r, name) for name, _ in r._fields_}
+        out["k1_per_sm"] = list(r.k1_per_sm)
+        out["gram_schedule"] = ("longest_first", "balanced_rounds")[
+            r.gram_schedule]
+        return out
+
+    def plv_group_configure(self, group, k1_widen=False, k1_per_sm=None,
+                            gram_schedule="longest_first", gram_tile_cost=0):
+        """Pin one of the tuner's candidate launch shapes without timing."""
+        ps = (ctypes.c_int * 4)(*(k1_per_sm or (0, 0, 0, 0)))
+        sched = {"longest_first": 0, "balanced_rounds": 1}[gram_schedule]
+        _lib.check(self.lib.plv_group_configure(
+            self.h, _stream(self.device), group.g, int(bool(k1_widen)), ps,
+            sched, int(gram_tile_cost)), self.h)
+
     def plv_trial_operands(self, V, E, N, ldv, l0, L, mode="asis", P=None):
         """Operands of the Gram over trials (Eq. 1 / 8 with mode "asis",
         Eq. 12 with mode "rms") from FP32 planar rows V [E][N][2][ldv]:

@@ -67,6 +67,8 @@ SIGNATURES = {
     "plv_dft_bins": (_i, [_vp, _vp, _vp, _i, _i, _i, _i64, _i, _i, _vp, _i64]),
     "plv_gram_windows": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _u, _vp, _vp, _vp,
                               _vp, _vp]),
+    "plv_group_tune": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "plv_group_configure": (_i, [_vp, _vp, _vp, _i, _vp, _i, _i]),
     "plv_group_destroy": (_i, [_vp]),
     "plv_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
 }
@@ -109,6 +111,20 @@ def check(status: int, handle=None):
     if status != PLV_OK:
         msg = load().plv_last_error(handle)
         raise PlvError(status, msg.decode() if msg else "")
+
+
+class PlvTuneResult(ctypes.Structure):
+    """Mirror of plv_tune_result (include/plv.h)."""
+    _fields_ = [("k1_ms_default", ctypes.c_float),
+                ("k1_ms_tuned", ctypes.c_float),
+                ("gram_ms_default", ctypes.c_float),
+                ("gram_ms_tuned", ctypes.c_float),
+                ("k1_lengths", ctypes.c_int), ("k1_widened", ctypes.c_int),
+                ("k1_per_sm", ctypes.c_int * 4),
+                ("k1_launches", ctypes.c_int),
+                ("gram_schedule", ctypes.c_int),
+                ("gram_tile_cost", ctypes.c_int),
+                ("timed_configs", ctypes.c_int), ("cached", ctypes.c_int)]
 
 
 class PlvProblem(ctypes.Structure):

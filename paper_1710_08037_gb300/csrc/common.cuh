@@ -90,6 +90,24 @@ __host__ __device__ constexpr size_t conv_smem(int M) {
     return (size_t)(M + M / 32) * sizeof(float2);
 }
 
+// Orders of the grouped Gram's tile list.  The persistent launch hands item
+// t to CTA t mod G (G = its grid), so an order is a schedule.
+enum GramSchedule : int {
+    kSchedLongestFirst = 0,  // by K blocks, descending (plan default)
+    kSchedBalanced = 1,      // longest first, each round of G items dealt to
+                             // the least-loaded CTAs (greedy LPT per round)
+};
+
+// Launch configuration of a plan, as chosen by the autotuner (defaults:
+// every transform length in its own thread class, occupancy-limited grids,
+// longest-first tiles).
+struct GroupConfig {
+    std::map<int, int> k1_class;        // transform length M -> thread class
+    int k1_per_sm[kConvClasses] = {0, 0, 0, 0};  // 0: occupancy limit
+    int gram_schedule = kSchedLongestFirst;
+    int gram_tile_cost = 0;             // per-tile fixed cost, in K blocks
+};
+
 struct Handle {
     int device = 0;
     plv_precision prec = PLV_PREC_FP32;
@@ -105,6 +123,8 @@ struct Handle {
     std::map<int, ConvPlan> conv;      // by T (lengths that are not handled directly)
     std::map<int, float2 *> conv_tw;   // twiddle tables by M
     std::map<int, float *> conv_S;     // kernel spectra by T
+    // autotuned configurations of grouped plans, by the plan's work signature
+    std::map<std::string, GroupConfig> tuned;
     std::mutex mu;
 };
 
@@ -165,6 +185,7 @@ struct K1Group {
     const int2 *items;       // device: (problem, row pair)
     int64_t begin[kConvClasses], count[kConvClasses];
     int max_M[kConvClasses];
+    int per_sm[kConvClasses];  // CTAs per SM of each class launch; 0: occupancy limit
 };
 // K1 of every problem of a group: one persistent launch per non-empty class.
 cudaError_t launch_analytic_group(const Handle *h, cudaStream_t s, plv_dtype dt,

@@ -82,6 +82,7 @@ cudaError_t launch_group_class(const Handle *h, cudaStream_t s, const K1Group &g
     const int c = C;
     const int64_t n = g.count[c];
     if (n == 0) return cudaSuccess;
+    if (g.per_sm[c] > 0 && g.per_sm[c] < per_sm) per_sm = g.per_sm[c];
     int64_t grid = (int64_t)per_sm * h->num_sms;
     if (grid > n) grid = n;
     kern<<<(unsigned)grid, THREADS, conv_smem(g.max_M[c]), s>>>(g.descs, g.items + g.begin[c],

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "group.cuh"
 
 namespace plv {
 
@@ -38,21 +39,6 @@ plv_status check_cuda(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return PLV_OK;
     return fail(PLV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
-
-// Makes the handle's device current for the scope and restores the caller's.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
-            cudaSetDevice(prev);
-    }
-};
 
 static int log2_exact(int T) {
     if (T <= 0 || (T & (T - 1))) return -1;
@@ -389,23 +375,6 @@ plv_status plv_gram_windows(plv_handle *hp, void *stream, const void *P, int bat
 
 }  // extern "C"
 
-struct plv_group {
-    int device = 0;
-    plv_precision prec = PLV_PREC_FP32;
-    std::vector<plv_problem> host;   // validated problems (FP32 path)
-    unsigned mask = 0;
-    plv::TcProblem *probs = nullptr;  // device descriptors (split paths)
-    int4 *items = nullptr;            // device tile list, longest first
-    int nprob = 0, nitems = 0;
-    bool any_diag = false;
-    // analytic-signal plan (problems with an input x)
-    bool has_k1 = false;
-    plv_dtype k1_dtype = PLV_F32;
-    plv::K1Desc *k1_descs = nullptr;  // device
-    int2 *k1_items = nullptr;         // device
-    plv::K1Group k1{};
-};
-
 namespace {
 
 // The analytic-signal part of a plan: descriptors, (problem, pair) items by
@@ -453,26 +422,9 @@ plv_status plan_k1(Handle &h, const plv_problem *probs, int nprob, plv_group *g)
     }
     if (descs.empty()) return PLV_OK;
     // items: by class, then decreasing M, then problem order
-    std::vector<int> order(descs.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const int ca = conv_class(descs[a].plan.M), cb = conv_class(descs[b].plan.M);
-        if (ca != cb) return ca < cb;
-        return descs[a].plan.M > descs[b].plan.M;
-    });
     std::vector<int2> items;
     K1Group kg{};
-    for (int c = 0; c < kConvClasses; ++c) {
-        kg.begin[c] = (int64_t)items.size();
-        kg.max_M[c] = 0;
-        for (int i : order) {
-            if (conv_class(descs[i].plan.M) != c) continue;
-            kg.max_M[c] = std::max(kg.max_M[c], descs[i].plan.M);
-            const int64_t pairs = (descs[i].rows + 1) / 2;
-            for (int64_t pr = 0; pr < pairs; ++pr) items.push_back(make_int2(i, (int)pr));
-        }
-        kg.count[c] = (int64_t)items.size() - kg.begin[c];
-    }
+    k1_layout(descs, g->cfg.k1_class, items, kg);
     plv_status st = check_cuda(cudaMalloc(&g->k1_descs, sizeof(K1Desc) * descs.size()),
                                "plv_group_create: analytic descriptors");
     if (st == PLV_OK)
@@ -502,6 +454,7 @@ plv_status plan_k1(Handle &h, const plv_problem *probs, int nprob, plv_group *g)
     kg.descs = g->k1_descs;
     kg.items = g->k1_items;
     g->k1 = kg;
+    g->k1_host = std::move(descs);
     g->has_k1 = true;
     return PLV_OK;
 }
@@ -578,6 +531,8 @@ plv_status plv_group_create(plv_handle *hp, const plv_problem *probs, int nprob,
     std::stable_sort(items.begin(), items.end(), [&](const int4 &a, const int4 &b) {
         return dp[a.x].nkb > dp[b.x].nkb;
     });
+    g->dp_host = dp;
+    g->items_host = items;
     g->nprob = (int)dp.size();
     g->nitems = (int)items.size();
     if (h.prec != PLV_PREC_FP32 && g->nprob > 0) {
@@ -643,11 +598,14 @@ plv_status plv_group_destroy(plv_group *g) {
     if (!g) return PLV_OK;
     {
         DeviceGuard guard(g->device);
-        if (g->probs || g->items || g->k1_descs || g->k1_items) cudaDeviceSynchronize();
+        if (g->probs || g->items || g->k1_descs || g->k1_items || !g->retired.empty())
+            cudaDeviceSynchronize();
         if (g->probs) cudaFree(g->probs);
         if (g->items) cudaFree(g->items);
         if (g->k1_descs) cudaFree(g->k1_descs);
         if (g->k1_items) cudaFree(g->k1_items);
+        for (void *p : g->retired)
+            if (p) cudaFree(p);
     }
     delete g;
     return PLV_OK;

@@ -66,29 +66,47 @@ def test_null_handle_is_rejected_without_a_device(lib):
     assert rc == _lib.PLV_ERR_INVALID
 
 
-def test_problem_struct_layout_matches_header(tmp_path):
-    """The ctypes mirror of plv_problem has the C compiler's size and field
-    offsets for the struct declared in include/plv.h."""
-    import ctypes
+def _c_layout(tmp_path, ctype_name, names):
+    """sizeof and offsetof of a struct of include/plv.h, by the C compiler."""
     import shutil
     import subprocess
-    from paper_1710_08037_gb300 import _lib
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
     inc = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
-    names = [f[0] for f in _lib.PlvProblem._fields_]
-    src = tmp_path / "layout.c"
+    src = tmp_path / f"layout_{ctype_name}.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "plv.h"\n'
         "int main(void) {\n"
-        '  printf("%zu\\n", sizeof(plv_problem));\n' +
-        "".join(f'  printf("%zu\\n", offsetof(plv_problem, {n}));\n' for n in names) +
+        f'  printf("%zu\\n", sizeof({ctype_name}));\n' +
+        "".join(f'  printf("%zu\\n", offsetof({ctype_name}, {n}));\n' for n in names) +
         "  return 0;\n}\n")
-    exe = tmp_path / "layout"
+    exe = tmp_path / f"layout_{ctype_name}"
     subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
-    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
-                                          text=True).stdout.split()]
-    want = [ctypes.sizeof(_lib.PlvProblem)] + [
-        getattr(_lib.PlvProblem, n).offset for n in names]
+    return [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                           text=True).stdout.split()]
+
+
+@pytest.mark.parametrize("ctype_name, mirror", [("plv_problem", _lib.PlvProblem),
+                                                ("plv_tune_result", _lib.PlvTuneResult)])
+def test_struct_layout_matches_header(tmp_path, ctype_name, mirror):
+    """The ctypes mirrors of the header's structs have the C compiler's size
+    and field offsets."""
+    names = [f[0] for f in mirror._fields_]
+    got = _c_layout(tmp_path, ctype_name, names)
+    want = [ctypes.sizeof(mirror)] + [getattr(mirror, n).offset for n in names]
     assert got == want
+
+
+def test_tuner_validates_on_the_host(lib):
+    """The autotuner and the configuration call reject NULL plans and
+    out-of-range values before any CUDA call."""
+    f = lib.plv_group_tune
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
+    assert f(None, None, None, 3, None) == _lib.PLV_ERR_INVALID
+    g = lib.plv_group_configure
+    g.restype = ctypes.c_int
+    g.argtypes = ([ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.c_int])
+    assert g(None, None, None, 0, None, 0, 0) == _lib.PLV_ERR_INVALID
