@@ -294,6 +294,16 @@ def run_ours(args):
                "ms_per_step": ems / args.steps,
                "pipeline": f"{nch} epoch chunks on {len(streams)} streams"}
 
+    # sampled outputs of epoch 0 for the comparison with the FP64 oracle
+    sub = sample_channels(N, seed, args.cpu_sample)
+    sub_t = torch.as_tensor(sub, device=dev)
+
+    def sampled(o):
+        return {k: o[k][0].index_select(0, sub_t).index_select(1, sub_t)
+                .double().cpu().numpy() for k in ("plv", "iplv", "ciplv")}
+
+    samp = {args.precision: sampled(out)}
+
     # the plain FP32 path on the same input: time and agreement
     fp32 = None
     if args.precision != "fp32" and not args.no_fp32_compare:
@@ -318,6 +328,7 @@ def run_ours(args):
         step()  # refresh the split-precision outputs for the comparison
         torch.cuda.synchronize(dev)
         agree = {k: float((out[k] - out32[k]).abs().max()) for k in out}
+        samp["fp32"] = sampled(out32)
         fp32 = {"ms_per_step": ms32, "value": job_value(units, world, ms32),
                 "speedup_of_split_path": ms32 / ms_step,
                 "max_abs_diff_vs_split_path": agree, "steps": n32}
@@ -354,8 +365,11 @@ def run_ours(args):
     k1["frac"] = k1["achieved"] / k1["peak"]
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(E, N, T, seed, args.cpu_sample)
+        ref = {}
+        cpu = cpu_baseline(E, N, T, seed, args.cpu_sample, x=x, values=ref)
+        accuracy = oracle_errors(samp, ref, len(sub), N)
 
     if rank == 0:
         line = {
@@ -379,6 +393,7 @@ def run_ours(args):
             "roofline": roof,
             "k1_roofline": k1,
             "cpu_baseline": cpu,
+            "accuracy_vs_oracle": accuracy,
             "fp32_path": fp32,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
@@ -932,26 +947,59 @@ def run_bands(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(E, N, T, seed, nsub):
+def oracle_errors(samp, ref, nsub, N):
+    """Per-metric max / mean absolute error of each GPU path against the
+    FP64 oracle on the sampled |S| x |S| pairs of epoch 0.  ciPLV is also
+    given over the pairs whose Eq. 14 denominator sqrt(1 - Re^2) is at least
+    0.05 (its error grows as 1 / sqrt(1 - Re^2))."""
+    import numpy as np
+    d = 1.0 - ref["plv"] ** 2 + ref["iplv"] ** 2  # 1 - Re^2 = 1 - |C|^2 + Im^2
+    well = np.sqrt(np.maximum(d, 0.0)) >= 0.05
+    out = {"sample": f"epoch 0, {nsub} of {N} channels, all {nsub}^2 ordered "
+                     f"pairs (diagonal included)",
+           "ciplv_well_conditioned_pairs": int(well.sum())}
+    for path, got in samp.items():
+        e = {}
+        for k in ("plv", "iplv", "ciplv"):
+            err = np.abs(got[k] - ref[k])
+            e[k] = {"max": float(err.max()), "mean": float(err.mean())}
+        err = np.abs(got["ciplv"] - ref["ciplv"])[well]
+        e["ciplv_well_conditioned"] = {"max": float(err.max()) if err.size else 0.0,
+                                       "mean": float(err.mean()) if err.size else 0.0}
+        out[path] = e
+    return out
+
+
+def sample_channels(N, seed, nsub):
+    """The channel subset S the oracle legs use: ``nsub`` of N, seeded."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(N, size=min(nsub, N), replace=False))
+
+
+def cpu_baseline(E, N, T, seed, nsub, x=None, values=None):
     """The FP64 oracle as it stands, on a bounded sample of the same
     workload: one epoch, a random subset S of ``nsub`` channels; direct-DFT
     analytic signal of S, then the pairwise loop over all |S|^2 pairs.  The
     per-epoch time is extrapolated as t_hilbert * N/|S| + t_pairs * (N/|S|)^2
-    (both parts are linear in rows resp. pairs)."""
-    import numpy as np
+    (both parts are linear in rows resp. pairs).  ``x``: the workload's
+    input (epoch 0 is used), else it is generated; ``values``: a dict that
+    receives the oracle's PLV / iPLV / ciPLV of the sample."""
     import torch
     import oracle
     from paper_1710_08037_gb300 import synth
-    x = synth.bandlimited(1, N, T, seed=seed, device="cpu"
-                          if not torch.cuda.is_available() else "cuda")
-    rng = np.random.default_rng(seed)
-    sub = np.sort(rng.choice(N, size=min(nsub, N), replace=False))
+    if x is None:
+        x = synth.bandlimited(1, N, T, seed=seed, device="cpu"
+                              if not torch.cuda.is_available() else "cuda")
+    sub = sample_channels(N, seed, nsub)
     xs = x[0][torch.as_tensor(sub, device=x.device)].double().cpu().numpy()
     t0 = time.perf_counter()
     z = oracle.analytic(xs)
     t1 = time.perf_counter()
-    oracle.pairwise(z)
+    ref = oracle.pairwise(z)
     t2 = time.perf_counter()
+    if values is not None:
+        values.update({k: ref[k] for k in ("plv", "iplv", "ciplv")})
     r = N / len(sub)
     t_epoch = (t1 - t0) * r + (t2 - t1) * r * r
     value = float(N) * N * T / t_epoch
