@@ -1000,6 +1000,14 @@ def cpu_baseline(E, N, T, seed, nsub, x=None, values=None):
     t2 = time.perf_counter()
     if values is not None:
         values.update({k: ref[k] for k in ("plv", "iplv", "ciplv")})
+    # context: the paper's reformulation on the same sample and host,
+    # unit phasors once, then one complex FP64 matrix product (numpy's BLAS)
+    import numpy as np
+    t3 = time.perf_counter()
+    az = np.abs(z)
+    Pz = np.where(az > 0, z / np.where(az > 0, az, 1.0), 0.0)
+    _ = (Pz @ Pz.conj().T) / z.shape[1]
+    t4 = time.perf_counter()
     r = N / len(sub)
     t_epoch = (t1 - t0) * r + (t2 - t1) * r * r
     value = float(N) * N * T / t_epoch
@@ -1008,7 +1016,15 @@ def cpu_baseline(E, N, T, seed, nsub, x=None, values=None):
             "sample": f"1 of {E} epochs, {len(sub)} of {N} channels: "
                       f"direct-DFT analytic signal {t1 - t0:.2f} s, pairwise "
                       f"loop over {len(sub)}^2 pairs {t2 - t1:.2f} s; "
-                      f"extrapolated to one full epoch ({t_epoch:.1f} s)"}
+                      f"extrapolated to one full epoch ({t_epoch:.1f} s)",
+            "context_gram_vs_pairwise": {
+                "pairwise_loop_s": t2 - t1, "gram_fp64_blas_s": t4 - t3,
+                "speedup": (t2 - t1) / max(t4 - t3, 1e-9),
+                "note": "the paper's reformulation (unit phasors once, one "
+                        "complex matrix product; numpy BLAS) against the "
+                        "pairwise loop on the same sample and host; the paper "
+                        "reports ~100x for its Gram over its vectorised loop "
+                        "(MATLAB, CPU not stated)"}}
 
 
 def run_reference(args):
