@@ -508,10 +508,20 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                 const TcProblem &pb = *pbp;
                 const int N = pb.N;
                 const int j0 = J * TN + cq * 32;
-                // warp-uniform: interior off-diagonal tiles without C take the
-                // staged stores; edges, diagonal tiles and C the element path
-                const bool staged = I != J && !pb.out.C && (I + 1) * TM <= N && j0 + 32 <= N;
-                if (staged)
+                // warp-uniform, per 32 x 32 block of the warp: blocks strictly
+                // above the diagonal (every block of an off-diagonal tile; those
+                // with q < cq of a diagonal tile) whose rows and columns are all
+                // in range take the staged stores, without C; blocks strictly
+                // below the diagonal of a diagonal tile store nothing (the
+                // mirror of block (cq, q) writes them); the rest (the diagonal's
+                // blocks, partial edge blocks, C) take the element path
+                const bool above = I != J || q < cq;
+                const bool below = I == J && q > cq;
+                const bool staged = above && !pb.out.C && I * TM + q * 32 + 32 <= N &&
+                                    j0 + 32 <= N;
+                if (below) {
+                    // nothing to store
+                } else if (staged)
                     store_tile_staged(pb.out, (int64_t)e * N * N, N, I * TM + q * 32, j0, lane,
                                       sre, sim, pb.invT,
                                       stage_tiles + (warp - 2) * STAGE_TILE_FLOATS,
