@@ -129,6 +129,41 @@ __device__ __forceinline__ float metric_of(int m, float re, float im) {
     return d > 0.0f ? im / sqrtf(d) : 0.0f;
 }
 
+// One metric m of one 8-column quarter (columns j0 .. j0+7, values re[c],
+// im[c] unscaled) of a warp's 32 x 32 block: the mirrored and the staged
+// row-wise stores described below.
+__device__ __forceinline__ void store_block8(const GramOut &o, int m, int64_t eNN, int N,
+                                             int i0, int j0, int lane, const float *re,
+                                             const float *im, float invT, float *S, bool vec) {
+    float *out = m == 0 ? o.plv : (m == 1 ? o.iplv : o.ciplv);
+    if (!out) return;
+    const float sgn = m == 2 ? -1.0f : 1.0f;  // ciPLV is antisymmetric
+    float v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = metric_of(m, re[c] * invT, im[c] * invT);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) out[eNN + (int64_t)(j0 + c) * N + i0 + lane] = sgn * v[c];
+    __syncwarp();  // the previous round's reads of S are done
+    const int sw = (lane >> 2) & 1;
+    *(float4 *)(S + lane * 8 + 4 * sw) = make_float4(v[0], v[1], v[2], v[3]);
+    *(float4 *)(S + lane * 8 + 4 * (1 ^ sw)) = make_float4(v[4], v[5], v[6], v[7]);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int r = 16 * k + (lane >> 1), qq = lane & 1;
+        const float4 w = *(const float4 *)(S + r * 8 + 4 * (qq ^ ((r >> 2) & 1)));
+        float *d = out + eNN + (int64_t)(i0 + r) * N + j0 + 4 * qq;
+        if (vec) {
+            *(float4 *)d = w;
+        } else {
+            d[0] = w.x;
+            d[1] = w.y;
+            d[2] = w.z;
+            d[3] = w.w;
+        }
+    }
+}
+
 // The store of one warp's 32 x 32 block of an interior off-diagonal tile:
 // lane l holds row i0 + l, columns j0 .. j0+31 (unscaled sums).  Every row
 // and column of the block is in range (the caller checks; the condition is
@@ -147,38 +182,10 @@ __device__ __forceinline__ void store_tile_staged(const GramOut &o, int64_t eNN,
                                                   float *S, bool vec) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        float *out = m == 0 ? o.plv : (m == 1 ? o.iplv : o.ciplv);
-        if (!out) continue;
-        const float sgn = m == 2 ? -1.0f : 1.0f;  // ciPLV is antisymmetric
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            float v[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                v[c] = metric_of(m, sre[8 * h + c] * invT, sim[8 * h + c] * invT);
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                out[eNN + (int64_t)(j0 + 8 * h + c) * N + i0 + lane] = sgn * v[c];
-            __syncwarp();  // the previous round's reads of S are done
-            const int sw = (lane >> 2) & 1;
-            *(float4 *)(S + lane * 8 + 4 * sw) = make_float4(v[0], v[1], v[2], v[3]);
-            *(float4 *)(S + lane * 8 + 4 * (1 ^ sw)) = make_float4(v[4], v[5], v[6], v[7]);
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int r = 16 * k + (lane >> 1), qq = lane & 1;
-                const float4 w = *(const float4 *)(S + r * 8 + 4 * (qq ^ ((r >> 2) & 1)));
-                float *d = out + eNN + (int64_t)(i0 + r) * N + j0 + 8 * h + 4 * qq;
-                if (vec) {
-                    *(float4 *)d = w;
-                } else {
-                    d[0] = w.x;
-                    d[1] = w.y;
-                    d[2] = w.z;
-                    d[3] = w.w;
-                }
-            }
-        }
+        for (int h = 0; h < 4; ++h)
+            store_block8(o, m, eNN, N, i0, j0 + 8 * h, lane, sre + 8 * h, sim + 8 * h, invT, S,
+                         vec);
     }
 }
 

@@ -459,6 +459,62 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                 pbp = &item_of(args, t, e, I, J);
                 nkb = pbp->nkb;
             }
+            if constexpr (!GEMM) {
+                if (nkb <= Chunk<FMT>::CH) {
+                    // The whole K range is one chunk (short windows, Grams over
+                    // trials): stream the accumulators from TMEM eight columns
+                    // at a time straight into the stores, instead of holding
+                    // all 32 columns in registers, and release the buffer after
+                    // the stores.  Same values as the running-sum path (its sums
+                    // start from +0 and add this one chunk).
+                    if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const TcProblem &pb = *pbp;
+                    const int N = pb.N;
+                    const int i = I * TM + row;
+                    const int j0 = J * TN + cq * 32;
+                    const bool above = I != J || q < cq;
+                    const bool below = I == J && q > cq;
+                    const bool staged = above && !pb.out.C && I * TM + q * 32 + 32 <= N &&
+                                        j0 + 32 <= N;
+                    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + buf * ACC_COLS +
+                                        cq * 32;
+                    if (!below) {
+#pragma unroll 1
+                        for (int h = 0; h < 4; ++h) {
+                            uint32_t ur[8], ui[8];
+                            tmem_ld8(tq + 8 * h, ur);
+                            tmem_ld8(tq + TN + 8 * h, ui);
+                            tmem_ld_wait8(ur, ui);
+                            float re[8], im[8];
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                re[c] = 0.f + __uint_as_float(ur[c]);
+                                im[c] = 0.f + __uint_as_float(ui[c]);
+                            }
+                            if (staged) {
+#pragma unroll
+                                for (int m = 0; m < 3; ++m)
+                                    store_block8(pb.out, m, (int64_t)e * N * N, N, I * TM + q * 32,
+                                                 j0 + 8 * h, lane, re, im, pb.invT,
+                                                 stage_tiles + (warp - 2) * STAGE_TILE_FLOATS,
+                                                 pb.out.vec_ok);
+                            } else {
+                                store_tile_row<8>(pb.out, (int64_t)e * N * N, N, i, j0 + 8 * h,
+                                                  I == J, re, im, pb.invT, pb.invT_d,
+                                                  pb.out.diag ? pb.out.diag + e : nullptr);
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    mbar_arrive(TEMPTY(buf));
+                    if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
+                    continue;
+                }
+            }
             float sre[32], sim[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
