@@ -848,6 +848,8 @@ def run_windows(args):
 
 
 BANDS_WL = "bands-5-N2048-T4096-E8"
+# the same with a length that is not a power of two (any-length band engine)
+BANDS_WL_ANY = "bands-5-N2048-T4000-E8"
 
 
 def run_bands(args):
@@ -869,7 +871,7 @@ def run_bands(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    E, N, T = 8, 2048, 4096
+    E, N, T = 8, 2048, (4000 if args.workload == BANDS_WL_ANY else 4096)
     nb = len(BANDS)
     h = plv.Handle(precision=args.precision, device=local)
     x = synth.bandlimited(E, N, T, seed=rank_seed(1008, rank), band=(1.0, 120.0), device=dev)
@@ -933,9 +935,10 @@ def run_bands(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": BANDS_WL, "E": E, "N": N, "T": T, "bands": BANDS},
+            "config": {"workload": args.workload, "E": E, "N": N, "T": T, "bands": BANDS},
             "roofline": roof,
-            "front_end": {"kernel": "k_hilbert_bands", "ms": fe_ms, "bound": "hbm",
+            "front_end": {"kernel": ("k_hilbert_bands" if T & (T - 1) == 0
+                                     else "k_hilbert_conv_bands"), "ms": fe_ms, "bound": "hbm",
                           "achieved_GBps": fe_bytes / (fe_ms / 1e3) / 1e9,
                           "peak": float(peaks["hbm_gbs"]),
                           "five_plain_analytic_ms": five_hilbert_ms},
@@ -1069,7 +1072,8 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the split one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED, BACKWARD, TIMERES,
-                                                               WINDOWS, BANDS_WL],
+                                                               WINDOWS, BANDS_WL,
+                                                               BANDS_WL_ANY],
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--subjects", type=int, default=256,
                     help="subjects of the grouped workload")
@@ -1096,7 +1100,7 @@ def main():
         run_time_resolved(args)
     elif args.workload == WINDOWS:
         run_windows(args)
-    elif args.workload == BANDS_WL:
+    elif args.workload in (BANDS_WL, BANDS_WL_ANY):
         run_bands(args)
     else:
         run_ours(args)

@@ -137,14 +137,27 @@ plv_status plv_analytic(plv_handle *h, void *stream, const void *x,
 /* The band-pass and Eq. 3 in one transform, for several bands (the
  * band-pass then analytic signal of Section III.A), fused with Eq. 4: for
  * band b, z_b = IFFT(h B_b FFT(x)) with a real band mask B_b, then
- * P_b = z_b / |z_b| in the handle's operand layout.  One forward FFT per
- * pair of rows serves every band.
+ * P_b = z_b / |z_b| in the handle's operand layout.
  *   x     : real [batch][N][ldx] (ldx >= T), F32 or F64, broadband.
- *   masks : float [nbands][T/2 + 1]: B_b at the bins 0 .. T/2 (the mask of
- *           bin -k is that of k; h zeroes the negative frequencies).
+ *   masks : float [nbands][T/2 + 1] on the device: B_b at the bins
+ *           0 .. T/2 (the mask of bin -k is that of k; h zeroes the negative
+ *           frequencies).
  *   P     : nbands operand buffers back to back, each
  *           plv_phasor_bytes(h, batch, N, T) bytes (written completely).
- * T: powers of two from 128 to 8192 (others: PLV_ERR_UNSUPPORTED). */
+ * T from 2 to 12288:
+ *   - powers of two from 128 to 8192: one forward FFT per pair of rows
+ *     serves every band; asynchronous, can be captured in a CUDA graph;
+ *   - every other T: the circular convolution of each row with the band's
+ *     kernel IDFT_T(h B_b) through one zero-padded transform of length
+ *     M >= 2T - 1, one row per transform (the kernel is complex), the
+ *     forward spectrum kept in the handle's scratch for all bands.  The
+ *     kernels' spectra are computed on the host in FP64 from the mask
+ *     values, which are read back: the call synchronises the stream,
+ *     allocates on first use of a (T, masks) pair (cached by the mask
+ *     values) and fails with PLV_ERR_INVALID inside a stream capture.  A
+ *     sample with |z_b|^2 below 2^-40 of the row's mean x^2 counts as
+ *     |z_b| = 0.
+ * Others: PLV_ERR_UNSUPPORTED. */
 plv_status plv_analytic_bands(plv_handle *h, void *stream, const void *x,
                               plv_dtype dtype, int batch, int N, int T, int64_t ldx,
                               const float *masks, int nbands, void *P);

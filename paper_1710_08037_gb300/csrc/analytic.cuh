@@ -58,6 +58,27 @@ PLV_BANDS_EXTERN(float, kK1Fp16)
 PLV_BANDS_EXTERN(double, kK1Fp16)
 #undef PLV_BANDS_EXTERN
 
+// The multi-band analytic signal for any other T up to kMaxConvM / 2
+// (k_bands.cu): one row per transform of length M, the forward spectrum kept
+// in `scratch` (per CTA, M complex values), per band a multiply by K_b
+// ([nbands][M]) and an inverse transform.  scratch must hold
+// bands_conv_scratch(h, M) complex values.
+template <typename Tin, int PREC>
+cudaError_t launch_bands_conv(const Handle *h, cudaStream_t st, const Tin *x, int64_t ldx,
+                              int N, int64_t rows, int T, const ConvPlan &plan, const float2 *K,
+                              int nbands, void *P, int64_t band_bytes, float2 *scratch);
+#define PLV_BANDS_CONV_EXTERN(TIN, KIND)                                                      \
+    extern template cudaError_t launch_bands_conv<TIN, KIND>(                                 \
+        const Handle *, cudaStream_t, const TIN *, int64_t, int, int64_t, int,                \
+        const ConvPlan &, const float2 *, int, void *, int64_t, float2 *);
+PLV_BANDS_CONV_EXTERN(float, kK1Fp32)
+PLV_BANDS_CONV_EXTERN(double, kK1Fp32)
+PLV_BANDS_CONV_EXTERN(float, kK1Bf16)
+PLV_BANDS_CONV_EXTERN(double, kK1Bf16)
+PLV_BANDS_CONV_EXTERN(float, kK1Fp16)
+PLV_BANDS_CONV_EXTERN(double, kK1Fp16)
+#undef PLV_BANDS_CONV_EXTERN
+
 #define PLV_K1_EXTERN(TIN, KIND)                                                              \
     extern template cudaError_t k1_pow2<TIN, KIND>(const Handle *, cudaStream_t,              \
                                                    const K1Args &);                           \

@@ -89,6 +89,12 @@ __host__ __device__ constexpr int conv_threads(int M) {
 __host__ __device__ constexpr size_t conv_smem(int M) {
     return (size_t)(M + M / 32) * sizeof(float2);
 }
+// Persistent CTAs of one any-length launch of transform length M (the
+// occupancy the class's register budget allows, on every SM).
+inline int64_t conv_grid(int num_sms, int M) {
+    const int per_sm = 65536 / (kConvRegs * conv_class_threads(conv_class(M)));
+    return (int64_t)(per_sm > 0 ? per_sm : 1) * num_sms;
+}
 
 // Orders of the grouped Gram's tile list.  The persistent launch hands item
 // t to CTA t mod G (G = its grid), so an order is a schedule.
@@ -123,6 +129,9 @@ struct Handle {
     std::map<int, ConvPlan> conv;      // by T (lengths that are not handled directly)
     std::map<int, float2 *> conv_tw;   // twiddle tables by M
     std::map<int, float *> conv_S;     // kernel spectra by T
+    // band-limited analytic-signal kernel spectra ([nbands][M] complex), by a
+    // hash of (T, nbands, mask values)
+    std::map<uint64_t, float2 *> band_K;
     // autotuned configurations of grouped plans, by the plan's work signature
     std::map<std::string, GroupConfig> tuned;
     std::mutex mu;
@@ -158,12 +167,25 @@ inline cudaError_t setup_once(LaunchSetup &ls, Kern kern, int threads, size_t sm
 
 // The any-length plan for T (built and cached on first use: allocates).
 plv_status get_conv_plan(Handle &h, int T, const ConvPlan **plan);
+// The any-length plan for T plus, for each of the nbands device masks
+// [nbands][T/2 + 1], the spectrum K_b (divided by M, in the transform's
+// output order) of the band-limited analytic-signal kernel IDFT_T(h B_b):
+// reads the masks back (synchronises s), cached by their values.
+plv_status get_band_plan(Handle &h, cudaStream_t s, int T, const float *masks, int nbands,
+                         const ConvPlan **plan, const float2 **K);
 void free_conv_plans(Handle &h);
 // The multi-band analytic signal for T = 2^log2T (k_bands.cu): nbands
 // operand buffers band_bytes apart.
 cudaError_t launch_analytic_bands(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
                                   int64_t rows, int N, int log2T, int64_t ldx, const float *masks,
                                   int nbands, void *P, int64_t band_bytes);
+// The multi-band analytic signal for lengths other than the power-of-two
+// band kernel's: one row per transform, the spectrum kept in scratch
+// (conv_grid(num_sms, M) slots of M complex values), nbands kernel spectra K.
+cudaError_t launch_analytic_bands_conv(const Handle *h, cudaStream_t s, const void *x,
+                                       plv_dtype dt, int64_t rows, int N, int T, int64_t ldx,
+                                       const ConvPlan &plan, const float2 *K, int nbands,
+                                       void *P, int64_t band_bytes, float2 *scratch);
 // K1 for lengths the direct FFT does not take (any T up to kMaxConvM / 2).
 cudaError_t launch_analytic_conv(const Handle *h, cudaStream_t s, const void *x,
                                  plv_dtype dt, int64_t rows, int N, int T, int64_t ldx,

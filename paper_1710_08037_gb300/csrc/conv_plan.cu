@@ -5,6 +5,7 @@
 // lands in the device's output order.  Tables are cached per handle.
 #include <math.h>
 
+#include <algorithm>
 #include <complex>
 #include <vector>
 
@@ -159,12 +160,127 @@ plv_status get_conv_plan(Handle &h, int T, const ConvPlan **out) {
     return PLV_OK;
 }
 
+namespace {
+
+// In-place radix-2 FFT of length n (a power of two), sign -1 (forward) or +1.
+void fft_pow2(std::vector<cd> &a, int sign) {
+    const int n = (int)a.size();
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        for (int i = 0; i < n; i += len)
+            for (int k = 0; k < len / 2; ++k) {
+                const cd w = std::polar(1.0, sign * 2.0 * M_PI * (double)k / len);
+                const cd u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+// Inverse DFT of any length T in FP64 by Bluestein's chirp-z identity:
+// with kn = (k^2 + n^2 - (n - k)^2) / 2,
+//   y[n] = (1/T) c[n] sum_k (Y[k] c[k]) conj(c[n - k]),  c[j] = exp(i pi j^2 / T),
+// a linear convolution done with power-of-two FFTs (j^2 taken mod 2T, so the
+// chirp's angle stays exact).
+std::vector<cd> idft_any(const std::vector<cd> &Y) {
+    const int T = (int)Y.size();
+    std::vector<cd> c(T);
+    for (int j = 0; j < T; ++j) {
+        const long long q = ((long long)j * j) % (2LL * T);
+        c[j] = std::polar(1.0, M_PI * (double)q / T);
+    }
+    int L = 1;
+    while (L < 2 * T - 1) L <<= 1;
+    std::vector<cd> a(L, 0.0), b(L, 0.0);
+    for (int k = 0; k < T; ++k) a[k] = Y[k] * c[k];
+    b[0] = std::conj(c[0]);
+    for (int j = 1; j < T; ++j) b[j] = b[L - j] = std::conj(c[j]);
+    fft_pow2(a, -1);
+    fft_pow2(b, -1);
+    for (int i = 0; i < L; ++i) a[i] *= b[i];
+    fft_pow2(a, +1);
+    std::vector<cd> y(T);
+    for (int n = 0; n < T; ++n) y[n] = c[n] * a[n] / ((double)L * T);
+    return y;
+}
+
+uint64_t fnv1a(const void *p, size_t n, uint64_t hsh) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) hsh = (hsh ^ b[i]) * 1099511628211ULL;
+    return hsh;
+}
+
+}  // namespace
+
+plv_status get_band_plan(Handle &h, cudaStream_t s, int T, const float *masks, int nbands,
+                         const ConvPlan **plan, const float2 **K) {
+    plv_status st = get_conv_plan(h, T, plan);
+    if (st != PLV_OK) return st;
+    const int M = (*plan)->M;
+    const int nb = T / 2 + 1;
+    std::vector<float> hm((size_t)nbands * nb);
+    cudaError_t e = cudaMemcpyAsync(hm.data(), masks, sizeof(float) * hm.size(),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return check_cuda(e, "plv_analytic_bands: read the band masks");
+    uint64_t key = fnv1a(&T, sizeof T, 1469598103934665603ULL);
+    key = fnv1a(&nbands, sizeof nbands, key);
+    key = fnv1a(hm.data(), sizeof(float) * hm.size(), key);
+    auto it = h.band_K.find(key);
+    if (it != h.band_K.end()) {
+        *K = it->second;
+        return PLV_OK;
+    }
+    std::vector<int> radix((*plan)->radix, (*plan)->radix + (*plan)->nstages);
+    std::vector<float2> Kf((size_t)nbands * M);
+    for (int b = 0; b < nbands; ++b) {
+        // spectrum h B of the band-limited analytic signal on the T-point grid:
+        // h[0] = 1, h[k] = 2 for 0 < k < T/2, h[T/2] = 1 (even T), 0 above;
+        // the real, even mask B given at the bins 0 .. T/2
+        const float *B = hm.data() + (size_t)b * nb;
+        std::vector<cd> Y(T, 0.0);
+        for (int k = 0; 2 * k <= T; ++k) {
+            const double hk = (k == 0 || 2 * k == T) ? 1.0 : 2.0;
+            Y[k] = hk * (double)B[k];
+        }
+        // its kernel k_b = IDFT_T(h B); z_b = x (*)_T k_b, placed for the
+        // zero-padded length-M transform as for the Hilbert kernel
+        const std::vector<cd> kt = idft_any(Y);
+        std::vector<cd> kc(M, 0.0);
+        for (int m = 0; m < T; ++m) kc[m] = kt[m];
+        for (int j = 1; j < T; ++j) kc[M - j] = kt[T - j];
+        host_dif(kc, M, radix);  // the device's digit-reversed order
+        for (int p = 0; p < M; ++p)
+            Kf[(size_t)b * M + p] =
+                make_float2((float)(kc[p].real() / M), (float)(kc[p].imag() / M));
+    }
+    float2 *d = nullptr;
+    e = cudaMalloc(&d, sizeof(float2) * Kf.size());
+    if (e != cudaSuccess) return check_cuda(e, "plv_analytic_bands: band kernels");
+    e = cudaMemcpy(d, Kf.data(), sizeof(float2) * Kf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return check_cuda(e, "plv_analytic_bands: band kernels upload");
+    }
+    h.band_K[key] = d;
+    h.workspace_used += sizeof(float2) * Kf.size();
+    *K = d;
+    return PLV_OK;
+}
+
 void free_conv_plans(Handle &h) {
     for (auto &kv : h.conv_tw) cudaFree(kv.second);
     for (auto &kv : h.conv_S) cudaFree(kv.second);
+    for (auto &kv : h.band_K) cudaFree(kv.second);
     h.conv_tw.clear();
     h.conv_S.clear();
     h.conv.clear();
+    h.band_K.clear();
 }
 
 }  // namespace plv

@@ -78,6 +78,15 @@ struct Bands {
     }
 };
 template <typename Tin, int KIND>
+struct BandsConv {
+    static cudaError_t run(const Handle *h, cudaStream_t s, const void *x, int64_t ldx, int N,
+                           int64_t rows, int T, const ConvPlan &plan, const float2 *K,
+                           int nbands, void *P, int64_t band_bytes, float2 *scratch) {
+        return launch_bands_conv<Tin, KIND>(h, s, (const Tin *)x, ldx, N, rows, T, plan, K,
+                                            nbands, P, band_bytes, scratch);
+    }
+};
+template <typename Tin, int KIND>
 struct Group {
     static cudaError_t run(const Handle *h, cudaStream_t s, const K1Group &g) {
         return k1_conv_group<Tin, KIND>(h, s, g);
@@ -115,6 +124,14 @@ cudaError_t launch_analytic_bands(const Handle *h, cudaStream_t s, const void *x
                                   int nbands, void *P, int64_t band_bytes) {
     return by_kind<Bands>(h->prec, dt, h, s, x, ldx, N, rows, log2T, masks, nbands, P,
                           band_bytes);
+}
+
+cudaError_t launch_analytic_bands_conv(const Handle *h, cudaStream_t s, const void *x,
+                                       plv_dtype dt, int64_t rows, int N, int T, int64_t ldx,
+                                       const ConvPlan &plan, const float2 *K, int nbands,
+                                       void *P, int64_t band_bytes, float2 *scratch) {
+    return by_kind<BandsConv>(h->prec, dt, h, s, x, ldx, N, rows, T, plan, K, nbands, P,
+                              band_bytes, scratch);
 }
 
 cudaError_t launch_analytic_group(const Handle *h, cudaStream_t s, plv_dtype dt,

@@ -161,7 +161,202 @@ cudaError_t launch_bands_l(const Handle *h, cudaStream_t st, const Tin *x, int64
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Any other length T: z_b = x (*)_T k_b with the complex kernel
+// k_b = IDFT_T(h B_b), by the zero-padded transform of length M of the
+// any-length engine (fft.cuh).  A complex kernel mixes the real and imaginary
+// parts, so each transform carries one row (c = x + 0i).  Per row: the
+// forward stages, the last one writing the spectrum to the CTA's scratch
+// slot; per band: spectrum times K_b (from scratch, in registers) fused with
+// the first inverse stage, the inverse stages, and the last one storing the
+// band's unit phasors.  The last forward stage and the first inverse stage
+// have the same butterflies (R consecutive values at base = b R) on the same
+// threads, so a thread only reads scratch values it wrote and smem values it
+// overwrites itself: no barrier is needed between them.
+
+// One row of x in, the unit phasors of band `band` out.
+template <typename Tin, int PREC>
+struct BandRowTask {
+    const Tin *x;
+    int64_t ldx;
+    uint8_t *P;  // band 0's operand buffer; band b at P + b band_bytes
+    int N;
+    int64_t ld;
+    int64_t band_bytes;
+    int band;
+    struct Rows {
+        const Tin *x0;
+        RowAddr<PREC> a0;
+    };
+    __device__ Rows rows(int64_t r0, bool, int64_t, bool) const {
+        Rows rs;
+        rs.x0 = x + r0 * ldx;
+        rs.a0 = row_addr<PREC>(r0, N, ld);
+        return rs;
+    }
+    __device__ float2 load(const Rows &rs, int m) const {
+        return make_float2(ldx_f(rs.x0 + m), 0.f);
+    }
+    __device__ void finish(const Rows &rs, int m, float zr, float zi, float floor2) const {
+        store_phasor<PREC>(P + band * band_bytes, rs.a0, ld, m, unit_phasor(zr, zi, floor2));
+    }
+    __device__ void pad(const Rows &rs, int m) const {
+        store_phasor<PREC>(P + band * band_bytes, rs.a0, ld, m, make_float2(0.f, 0.f));
+    }
+};
+
+// The last forward stage (sub = 1) from smem to the scratch slot.
+template <int R>
+__device__ __forceinline__ void last_fwd_to_scratch(const float2 *s, int M, float2 *scr) {
+    for (int b = threadIdx.x; b < M / R; b += blockDim.x) {
+        const int base = b * R;
+        float2 a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = s[padi(base + q)];
+        dft_any<R>(a);
+#pragma unroll
+        for (int q = 0; q < R; ++q) scr[base + q] = a[q];
+    }
+}
+
+// Spectrum times K (complex), conjugated for the inverse, and the first
+// inverse stage (sub = 1) into smem; the store conjugates back, as the
+// engine's fused middle stage does.
+template <int R>
+__device__ __forceinline__ void band_first_inv(float2 *s, int M, const float2 *scr,
+                                               const float2 *__restrict__ K) {
+    for (int b = threadIdx.x; b < M / R; b += blockDim.x) {
+        const int base = b * R;
+        float2 a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const float2 v = scr[base + q], k = __ldg(&K[base + q]);
+            const float2 w = cmul(v, k);
+            a[q] = make_float2(w.x, -w.y);
+        }
+        dft_any<R>(a);
+#pragma unroll
+        for (int q = 0; q < R; ++q) s[padi(base + q)] = make_float2(a[q].x, -a[q].y);
+    }
+}
+
+__device__ __forceinline__ void last_fwd_to_scratch_any(const float2 *s, int M, int R,
+                                                        float2 *scr) {
+    switch (R) {
+        case 8: last_fwd_to_scratch<8>(s, M, scr); break;
+        case 5: last_fwd_to_scratch<5>(s, M, scr); break;
+        case 4: last_fwd_to_scratch<4>(s, M, scr); break;
+        case 3: last_fwd_to_scratch<3>(s, M, scr); break;
+        default: last_fwd_to_scratch<2>(s, M, scr); break;
+    }
+}
+__device__ __forceinline__ void band_first_inv_any(float2 *s, int M, int R, const float2 *scr,
+                                                   const float2 *K) {
+    switch (R) {
+        case 8: band_first_inv<8>(s, M, scr, K); break;
+        case 5: band_first_inv<5>(s, M, scr, K); break;
+        case 4: band_first_inv<4>(s, M, scr, K); break;
+        case 3: band_first_inv<3>(s, M, scr, K); break;
+        default: band_first_inv<2>(s, M, scr, K); break;
+    }
+}
+
+// Persistent over rows; CTA b uses scratch slot b (M complex values).
+template <typename Tin, int PREC, int THREADS>
+__global__ void __launch_bounds__(THREADS, 65536 / (kConvRegs * THREADS))
+k_hilbert_conv_bands(const BandRowTask<Tin, PREC> task, const ConvPlan plan, int T,
+                     int64_t rows, const float2 *__restrict__ K, int nbands,
+                     float2 *__restrict__ scratch) {
+    extern __shared__ __align__(16) float2 smem[];
+    __shared__ float s_pow;
+    const int M = plan.M;
+    const int ns = plan.nstages;
+    const int64_t ld = task.ld;
+    float2 *scr = scratch + (int64_t)blockIdx.x * M;
+    if (threadIdx.x == 0) s_pow = 0.f;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        __syncthreads();  // the previous row is done with smem; s_pow is 0
+        const auto rs = task.rows(r, true, 0, false);
+        int span = M;
+        float pw = 0.f, floor2 = 0.f;
+        for (int st = 0; st < ns - 1; ++st) {
+            const int R = plan.radix[st];
+            const int lsub = ilog2(span / R);
+            if (st == 0)
+                conv_stage<kDifFirst>(smem, M, R, lsub, plan, task, rs, T, ld, &pw, 0.f);
+            else
+                conv_stage<kDifSmem>(smem, M, R, lsub, plan, task, rs, T, ld, nullptr, 0.f);
+            if (st == 0) {
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1)
+                    pw += __shfl_xor_sync(0xffffffffu, pw, off);
+                if ((threadIdx.x & 31) == 0) atomicAdd(&s_pow, pw);
+            }
+            __syncthreads();
+            // |z_b|^2 below 2^-40 of the row's mean power |x|^2 counts as 0
+            if (st == 0) floor2 = 0x1p-40f * (s_pow / (float)T);
+            span /= R;
+        }
+        const int Rl = plan.radix[ns - 1];
+        last_fwd_to_scratch_any(smem, M, Rl, scr);
+        for (int b = 0; b < nbands; ++b) {
+            band_first_inv_any(smem, M, Rl, scr, K + (int64_t)b * M);
+            __syncthreads();
+            if (b == 0 && threadIdx.x == 0) s_pow = 0.f;  // every thread has read it
+            BandRowTask<Tin, PREC> tb = task;
+            tb.band = b;
+            span = Rl;
+            for (int st = ns - 2; st >= 0; --st) {
+                const int R = plan.radix[st];
+                const int lsub = ilog2(span);
+                if (st > 0) {
+                    conv_stage<kDitSmem>(smem, M, R, lsub, plan, tb, rs, T, ld, nullptr, 0.f);
+                    __syncthreads();
+                } else {
+                    conv_stage<kDitLast>(smem, M, R, lsub, plan, tb, rs, T, ld, nullptr,
+                                         floor2);
+                }
+                span *= R;
+            }
+            __syncthreads();  // the last stage's smem reads are done before the next band
+        }
+    }
+}
+
+template <typename Tin, int PREC, int C>
+cudaError_t launch_bands_conv_c(const Handle *h, cudaStream_t st,
+                                const BandRowTask<Tin, PREC> &task, const ConvPlan &plan, int T,
+                                int64_t rows, const float2 *K, int nbands, float2 *scratch) {
+    constexpr int THREADS = conv_class_threads(C);
+    auto kern = k_hilbert_conv_bands<Tin, PREC, THREADS>;
+    static LaunchSetup ls;
+    int per_sm = 0;
+    cudaError_t e = setup_once(ls, kern, THREADS, conv_smem(conv_class_max_M(C)), per_sm);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (int64_t)per_sm * h->num_sms;
+    const int64_t slots = conv_grid(h->num_sms, plan.M);  // scratch slots the caller sized
+    if (grid > slots) grid = slots;
+    if (grid > rows) grid = rows;
+    if (grid <= 0) return cudaSuccess;
+    kern<<<(unsigned)grid, THREADS, conv_smem(plan.M), st>>>(task, plan, T, rows, K, nbands,
+                                                             scratch);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+template <typename Tin, int PREC>
+cudaError_t launch_bands_conv(const Handle *h, cudaStream_t st, const Tin *x, int64_t ldx,
+                              int N, int64_t rows, int T, const ConvPlan &plan, const float2 *K,
+                              int nbands, void *P, int64_t band_bytes, float2 *scratch) {
+    const BandRowTask<Tin, PREC> task{x, ldx, (uint8_t *)P, N, padded_len(T), band_bytes, 0};
+    switch (conv_class(plan.M)) {
+        case 0: return launch_bands_conv_c<Tin, PREC, 0>(h, st, task, plan, T, rows, K, nbands, scratch);
+        case 1: return launch_bands_conv_c<Tin, PREC, 1>(h, st, task, plan, T, rows, K, nbands, scratch);
+        case 2: return launch_bands_conv_c<Tin, PREC, 2>(h, st, task, plan, T, rows, K, nbands, scratch);
+        default: return launch_bands_conv_c<Tin, PREC, 3>(h, st, task, plan, T, rows, K, nbands, scratch);
+    }
+}
 
 template <typename Tin, int PREC>
 cudaError_t launch_bands(const Handle *h, cudaStream_t st, const Tin *x, int64_t ldx, int N,
@@ -188,10 +383,16 @@ cudaError_t launch_bands(const Handle *h, cudaStream_t st, const Tin *x, int64_t
 template cudaError_t launch_bands<double, PLV_K1_KIND>(const Handle *, cudaStream_t,
                                                         const double *, int64_t, int, int64_t,
                                                         int, const float *, int, void *, int64_t);
+template cudaError_t launch_bands_conv<double, PLV_K1_KIND>(
+    const Handle *, cudaStream_t, const double *, int64_t, int, int64_t, int, const ConvPlan &,
+    const float2 *, int, void *, int64_t, float2 *);
 #else
 template cudaError_t launch_bands<float, PLV_K1_KIND>(const Handle *, cudaStream_t,
                                                        const float *, int64_t, int, int64_t, int,
                                                        const float *, int, void *, int64_t);
+template cudaError_t launch_bands_conv<float, PLV_K1_KIND>(
+    const Handle *, cudaStream_t, const float *, int64_t, int, int64_t, int, const ConvPlan &,
+    const float2 *, int, void *, int64_t, float2 *);
 #endif
 
 #endif  // PLV_K1_KIND != 3

@@ -247,9 +247,10 @@ plv_status plv_analytic_bands(plv_handle *hp, void *stream, const void *x, plv_d
         return fail(PLV_ERR_INVALID, "plv_analytic_bands: unknown dtype %d", (int)dtype);
     if (ldx < T) return fail(PLV_ERR_INVALID, "plv_analytic_bands: ldx < T");
     const int L = log2_exact(T);
-    if (L < kMinLog2Bands || L > kMaxLog2Direct)
-        return fail(PLV_ERR_UNSUPPORTED, "plv_analytic_bands: T = %d (powers of two %d .. %d)", T,
-                    1 << kMinLog2Bands, 1 << kMaxLog2Direct);
+    const bool direct = L >= kMinLog2Bands && L <= kMaxLog2Direct;
+    if (!direct && (T < 2 || 2 * T - 1 > kMaxConvM))
+        return fail(PLV_ERR_UNSUPPORTED, "plv_analytic_bands: T = %d (2 .. %d)", T,
+                    kMaxConvM / 2);
     if (batch == 0 || N == 0 || nbands == 0) return PLV_OK;
     if (!x || !masks || !P) return fail(PLV_ERR_INVALID, "plv_analytic_bands: NULL pointer");
     const size_t esz = dtype == PLV_F32 ? 4 : 8;
@@ -258,6 +259,14 @@ plv_status plv_analytic_bands(plv_handle *hp, void *stream, const void *x, plv_d
     PLV_GUARD(&hp->h);
     const size_t band_bytes = plv_phasor_bytes(hp, batch, N, T);
     cudaStream_t s = (cudaStream_t)stream;
+    if (!direct) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            return fail(PLV_ERR_INVALID,
+                        "plv_analytic_bands: T = %d is not a power of two from %d to %d, which "
+                        "reads the masks back: not inside a capture",
+                        T, 1 << kMinLog2Bands, 1 << kMaxLog2Direct);
+    }
     if (hp->h.prec != PLV_PREC_FP32)
         for (int b = 0; b < nbands; ++b) {
             plv_status st = check_cuda(
@@ -265,8 +274,25 @@ plv_status plv_analytic_bands(plv_handle *hp, void *stream, const void *x, plv_d
                 "plv_analytic_bands: pad rows");
             if (st != PLV_OK) return st;
         }
-    return check_cuda(launch_analytic_bands(&hp->h, s, x, dtype, (int64_t)batch * N, N, L, ldx,
-                                            masks, nbands, P, (int64_t)band_bytes),
+    if (direct)
+        return check_cuda(launch_analytic_bands(&hp->h, s, x, dtype, (int64_t)batch * N, N, L,
+                                                ldx, masks, nbands, P, (int64_t)band_bytes),
+                          "plv_analytic_bands launch");
+    // any other length: the band kernels' spectra are built on the host from
+    // the mask values (read back, so the stream is synchronised) and cached;
+    // the forward spectrum of each row is kept in the handle's scratch
+    Handle &h = hp->h;
+    const ConvPlan *plan = nullptr;
+    const float2 *K = nullptr;
+    std::lock_guard<std::mutex> lock(h.mu);  // the scratch stays as sized through the launch
+    plv_status st = get_band_plan(h, s, T, masks, nbands, &plan, &K);
+    if (st != PLV_OK) return st;
+    st = ensure_workspace(h, s, sizeof(float2) * (size_t)conv_grid(h.num_sms, plan->M) *
+                                    (size_t)plan->M);
+    if (st != PLV_OK) return st;
+    return check_cuda(launch_analytic_bands_conv(&h, s, x, dtype, (int64_t)batch * N, N, T, ldx,
+                                                 *plan, K, nbands, P, (int64_t)band_bytes,
+                                                 (float2 *)h.ws),
                       "plv_analytic_bands launch");
 }
 
