@@ -25,7 +25,7 @@ __device__ __forceinline__ void emit(const GramOut &o, int64_t eNN, int N,
     float p, ip, cp;
     if (i == j) {
         im = 0.f;
-        p = sqrtf(fmaf(re, re, im * im));
+        p = plv_of(re, im);
         ip = 0.f;
         cp = 0.f;
     } else {
@@ -78,7 +78,7 @@ __device__ __forceinline__ void store_tile_row(const GramOut &o, int64_t eNN, in
             if (i == j) {
                 if (valid[u] && diag) diag_check(diag, sre[jj], sim[jj], invT_d);
                 im = 0.f;
-                p[u] = sqrtf(fmaf(re, re, im * im));
+                p[u] = plv_of(re, im);
                 ip[u] = 0.f;
                 cp[u] = 0.f;
             } else {
@@ -123,10 +123,9 @@ __device__ __forceinline__ void store_tile_row(const GramOut &o, int64_t eNN, in
 // One metric of an off-diagonal Gram entry (re, im already scaled): the same
 // arithmetic as readout(), so both store paths give identical bits.
 __device__ __forceinline__ float metric_of(int m, float re, float im) {
-    if (m == 0) return sqrtf(fmaf(re, re, im * im));
+    if (m == 0) return plv_of(re, im);
     if (m == 1) return fabsf(im);
-    const float d = ciplv_den(re);
-    return d > 0.0f ? im / sqrtf(d) : 0.0f;
+    return ciplv_of(re, im);
 }
 
 // One metric m of one 8-column quarter (columns j0 .. j0+7, values re[c],

@@ -141,7 +141,7 @@ __global__ void k_metrics(const float2 *__restrict__ C, int64_t total, int N,
         const bool diag = (w / N) == (w % N);
         float p, ip, cp;
         if (diag) {
-            p = sqrtf(fmaf(c.x, c.x, c.y * c.y));
+            p = plv_of(c.x, c.y);
             ip = 0.f;
             cp = 0.f;
         } else {

@@ -18,16 +18,33 @@ __device__ __forceinline__ float ciplv_den(float r) {
     return (1.0f - r) * (1.0f + r);
 }
 
+// The square root and the division of the read-outs go through the
+// special-function unit's reciprocal square root (rsqrtf, a few ulp) rather
+// than IEEE sqrtf and division: the read-outs already carry the Gram's own
+// error (about 1e-6 absolute), far above either rounding, and the epilogue
+// spends most of its instructions here.
+
+// |C| = sqrt(re^2 + im^2), 0 at C = 0.
+__device__ __forceinline__ float plv_of(float re, float im) {
+    const float r2 = fmaf(re, re, im * im);
+    return r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+}
+
+// Im C / sqrt(d) for d = ciplv_den(Re C), 0 where d is not positive.
+__device__ __forceinline__ float ciplv_of(float re, float im) {
+    const float d = ciplv_den(re);
+    return d > 0.0f ? im * rsqrtf(d) : 0.0f;
+}
+
 // PLV = |C| (Eq. 7), iPLV = |Im C| (Eq. 13, in absolute value) and
 // ciPLV = Im C / sqrt((1 - Re C)(1 + Re C)) (Eq. 14) of one off-diagonal
 // Gram entry C = re + i im already scaled by 1/T; ciPLV = 0 where the
 // denominator is not positive.
 __device__ __forceinline__ void readout(float re, float im, float &plv,
                                         float &iplv, float &ciplv) {
-    plv = sqrtf(fmaf(re, re, im * im));
+    plv = plv_of(re, im);
     iplv = fabsf(im);
-    const float d = ciplv_den(re);
-    ciplv = d > 0.0f ? im / sqrtf(d) : 0.0f;
+    ciplv = ciplv_of(re, im);
 }
 
 }  // namespace plv
