@@ -251,7 +251,8 @@ plv_status plv_gram_grouped(plv_handle *h, void *stream, const plv_group *group)
 plv_status plv_analytic_grouped(plv_handle *h, void *stream, const plv_group *group);
 
 /* What plv_group_tune chose and measured.  Times are medians of `reps`
- * launches in milliseconds (0 where nothing was timed). */
+ * launches in milliseconds (0 where nothing was timed); "default" is the
+ * plan's configuration when the call began. */
 typedef struct {
     float k1_ms_default, k1_ms_tuned;      /* plv_analytic_grouped's launches */
     float gram_ms_default, gram_ms_tuned;  /* plv_gram_grouped's launch (split precisions) */

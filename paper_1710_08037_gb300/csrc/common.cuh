@@ -112,6 +112,12 @@ struct GroupConfig {
     int k1_per_sm[kConvClasses] = {0, 0, 0, 0};  // 0: occupancy limit
     int gram_schedule = kSchedLongestFirst;
     int gram_tile_cost = 0;             // per-tile fixed cost, in K blocks
+    bool operator==(const GroupConfig &o) const {
+        for (int c = 0; c < kConvClasses; ++c)
+            if (k1_per_sm[c] != o.k1_per_sm[c]) return false;
+        return k1_class == o.k1_class && gram_schedule == o.gram_schedule &&
+               gram_tile_cost == o.gram_tile_cost;
+    }
 };
 
 struct Handle {

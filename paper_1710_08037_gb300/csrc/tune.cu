@@ -176,8 +176,10 @@ int k1_default_per_sm(int c) {
     return v > 0 ? v : 1;
 }
 
-// Make cfg the plan's configuration: new device lists, the old ones retired.
+// Make cfg the plan's configuration: new device lists, the old ones retired
+// (nothing to do when the plan already runs cfg).
 plv_status apply_config(const Handle &h, plv_group &g, const GroupConfig &cfg, cudaStream_t s) {
+    if (cfg == g.cfg) return PLV_OK;
     if (g.has_k1) {
         std::vector<int2> items;
         K1Group kg = g.k1;
