@@ -49,6 +49,13 @@ MUTATIONS = {
                           "double h = hmask(k, T);"),
     "coh_conjugate": ("si += x_im[qi] * x_re[qj] - x_re[qi] * x_im[qj];",
                       "si += x_im[qi] * x_re[qj] + x_re[qi] * x_im[qj];"),
+    # the analytic mask and the inverse transform
+    "nyquist_weight": ("if (k == T / 2) return 1.0;", "if (k == T / 2) return 2.0;"),
+    "odd_last_bin_dropped": ("return (k <= (T - 1) / 2) ? 2.0 : 0.0;",
+                             "return (k < (T - 1) / 2) ? 2.0 : 0.0;"),
+    "inverse_twiddle_sign": ("double c = twc[idx], s = -tws[idx];",
+                             "double c = twc[idx], s = tws[idx];"),
+    "iplv_signed": ("*iplv = fabs(ci);", "*iplv = ci;"),
 }
 
 PIN_CALLS = [
