@@ -15,11 +15,8 @@
 // timing.  Every candidate computes the same values with the same
 // arithmetic per transform and per tile; only the assignment of work to CTAs
 // changes.
-#include <stdio.h>
-
 #include <algorithm>
 #include <map>
-#include <new>
 #include <string>
 #include <tuple>
 #include <vector>
