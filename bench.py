@@ -763,6 +763,111 @@ def run_time_resolved(args):
         dist.destroy_process_group()
 
 
+COHERENCY = "coherency-E64-N1024-T1000-F64"
+
+
+def run_coherency(args):
+    """Coherency across trials (Eq. 12) from raw trials: the DFT of every
+    trial's rows at 64 consecutive bins (4-67 Hz at fs = 1000 Hz, T = 1000),
+    the RMS-normalised trial operands of every bin, and one Gram per bin
+    with K = trials (coherence, imaginary coherency, lagged coherence)."""
+    import torch
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    E, N, T, f0, F = 64, 1024, 1000, 4, 64
+    h = plv.Handle(precision=args.precision, device=local)
+    x = synth.bandlimited(E, N, T, seed=rank_seed(1009, rank), band=(2.0, 120.0), device=dev)
+    ldF = plv.phasor_ld(F)
+    V = torch.empty((E, N, 2, ldF), dtype=torch.float32, device=dev)
+    P = h.empty_phasors(F, N, E)
+    out = {k: torch.empty((F, N, N), dtype=torch.float32, device=dev)
+           for k in ("plv", "iplv", "ciplv")}
+    s = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(e=None):
+        if e:
+            e[0].record(s)
+        h.plv_dft_bins(x, f0, F, V)
+        if e:
+            e[1].record(s)
+        h.plv_trial_operands(V, E, N, ldF, 0, F, "rms", P)
+        if e:
+            e[2].record(s)
+        h.plv_gram(P, F, N, E, out=out)
+        if e:
+            e[3].record(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    per = [[ev(), ev(), ev(), ev()] for _ in range(args.steps)]
+    for p in per:
+        step(p)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(p[0].elapsed_time(p[3]) for p in per), dist, dev)
+    dft_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in per)
+    tr_ms = statistics.mean(p[1].elapsed_time(p[2]) for p in per)
+    gram_ms = statistics.mean(p[2].elapsed_time(p[3]) for p in per)
+    ms_step = ms / args.steps
+    units = float(N) * N * E * F  # channel pairs x trials x bins
+    peaks, peak_kind = _peaks()
+    # the DFT at F bins is a thin real GEMM on the CUDA cores: 4 flops per
+    # (row, sample, bin), against the FP32 FMA peak at the maximum SM clock
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    dft = {"kernel": "k_dft_bins", "bound": "alu", "ms": dft_ms,
+           "achieved": 4.0 * E * N * T * F / (dft_ms / 1e3) / 1e12, "peak": alu_peak,
+           "unit": "TFLOP/s"}
+    dft["frac"] = dft["achieved"] / dft["peak"]
+    # the Gram over K = 64 trials is output-bound: operands read once, three
+    # full N x N outputs per bin
+    ldE = plv.phasor_ld(E)
+    gram_bytes = F * ((N + 127) // 128 * 128) * ldE * 8 + 3 * 4 * F * N * N
+    roof = {"bound": "hbm", "kernel": "k_gram_tc (batch = bins, K = trials)",
+            "achieved": gram_bytes / (gram_ms / 1e3) / 1e9,
+            "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+            "peak_source": f"{peak_kind} HBM copy", "traffic": None,
+            "launch_ms": gram_ms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    if rank == 0:
+        line = {
+            "metric": "channel-pair·trial·bins/s (N²·E·F/s), coherence, imaginary "
+                      "coherency and lagged coherence across trials",
+            "value": job_value(units, world, ms_step),
+            "unit": "channel-pair·trial·bins/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": COHERENCY, "E_trials": E, "N": N, "T": T,
+                       "bins": [f0, f0 + F - 1],
+                       "outputs": "3 x F x N x N FP32 (0.8 GB per step)"},
+            "roofline": roof, "dft": dft,
+            "parts_ms": {"dft_bins": dft_ms, "trial_operands_rms": tr_ms,
+                         "gram": gram_ms},
+            "gpu_launches": 3 * args.steps, "clocks": clk,
+            "device_status": h.plv_sync_status()}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 WINDOWS = "sliding-N1024-T4096-W512-hop256-E8"
 
 
@@ -1072,6 +1177,7 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the split one")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + [GROUPED, BACKWARD, TIMERES,
+                                                               COHERENCY,
                                                                WINDOWS, BANDS_WL,
                                                                BANDS_WL_ANY],
                     default=DEFAULT_WORKLOAD)
@@ -1098,6 +1204,8 @@ def main():
         run_backward(args)
     elif args.workload == TIMERES:
         run_time_resolved(args)
+    elif args.workload == COHERENCY:
+        run_coherency(args)
     elif args.workload == WINDOWS:
         run_windows(args)
     elif args.workload in (BANDS_WL, BANDS_WL_ANY):
