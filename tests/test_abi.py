@@ -110,3 +110,47 @@ def test_tuner_validates_on_the_host(lib):
     g.argtypes = ([ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                            ctypes.c_int])
     assert g(None, None, None, 0, None, 0, 0) == _lib.PLV_ERR_INVALID
+
+
+def test_every_entry_point_validates_before_touching_a_device(lib):
+    """Every status-returning entry point, called with a NULL handle (or,
+    without one, an invalid size) and zero arguments, fails with
+    PLV_ERR_INVALID from its host-side checks; the destroy calls accept
+    NULL.  No CUDA call is made, so this runs without a GPU."""
+    ok_on_null = {"plv_destroy", "plv_group_destroy"}
+    not_status = {"plv_last_error", "plv_get_precision", "plv_phasor_ld",
+                  "plv_phasor_bytes"}
+    for name, (res, args) in _lib.SIGNATURES.items():
+        if name in not_status:
+            continue
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+        zeros = [None if a is ctypes.c_void_p or isinstance(a, type(ctypes.POINTER(ctypes.c_int)))
+                 else 0 for a in args]
+        rc = f(*zeros)
+        want = _lib.PLV_OK if name in ok_on_null else _lib.PLV_ERR_INVALID
+        assert rc == want, (name, rc)
+    lib.plv_get_precision.restype = ctypes.c_int
+    lib.plv_get_precision.argtypes = [ctypes.c_void_p]
+    assert lib.plv_get_precision(None) == _lib.PLV_PREC_FP32
+
+
+def test_noalloc_backward_rejects_on_the_host(lib):
+    """The allocation-free backward checks sizes, the supported lengths and
+    its fixed scratch limit before any CUDA call."""
+    name = "plv_backward_noalloc"
+    res, args = _lib.SIGNATURES[name]
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: rejected first
+    common = (None, fake, _lib.PLV_F32)
+    # a length that is not a power of two in range: unsupported
+    rc = f(*common, 1, 4, 300, 300, fake, None, None, None, fake)
+    assert rc == _lib.PLV_ERR_UNSUPPORTED
+    # more scratch than the fixed array holds
+    rc = f(*common, 64, 4096, 8192, 8192, fake, None, None, None, fake)
+    assert rc == _lib.PLV_ERR_INVALID
+    lib.plv_last_error.restype = ctypes.c_char_p
+    assert b"scratch" in lib.plv_last_error(None)
