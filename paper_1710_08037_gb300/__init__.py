@@ -108,9 +108,11 @@ class Handle:
 
     def plv_analytic_bands(self, x, masks, P=None):
         """Band-pass and Eq. 3 + 4 for every band of ``masks`` (nbands,
-        T//2 + 1) float32 on the device, from one forward FFT per row pair:
-        returns the phasors of the bands, (nbands, bytes of one buffer)
-        uint8 (buffer b is P[b])."""
+        T//2 + 1) float32 on the device: returns the phasors of the bands,
+        (nbands, bytes of one buffer) uint8 (buffer b is P[b]).  Powers of
+        two from 128 to 8192 take one forward FFT per row pair; any other T
+        up to 12288 the any-length engine, which reads the masks back
+        (synchronising the stream; not inside a graph capture)."""
         assert x.is_cuda and x.dim() == 3
         B, N, T = x.shape
         if not (x.stride(-1) == 1 and (N == 1 or x.stride(0) == N * x.stride(1))):
