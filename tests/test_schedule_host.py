@@ -1,0 +1,141 @@
+"""The autotuner's host-side work lists on CPU: a small C++ program linked
+against the built library calls plv::gram_order (the grouped Gram's tile
+schedules) and plv::k1_layout (the grouped analytic signal's items by thread
+class) and checks their invariants.  Pure host functions: no GPU needed."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+from paper_1710_08037_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PROGRAM = r"""
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <tuple>
+#include <vector>
+#include <algorithm>
+#include "group.cuh"
+using namespace plv;
+
+#define CHECK(c) do { if (!(c)) { std::printf("FAIL %s:%d %s\n", __FILE__, __LINE__, #c); \
+    return 1; } } while (0)
+
+static std::vector<long> loads(const std::vector<TcProblem> &dp, const std::vector<int4> &v,
+                               int G, int cost) {
+    std::vector<long> l(G, 0);
+    for (size_t t = 0; t < v.size(); ++t) l[t % G] += dp[v[t].x].nkb + cost;
+    return l;
+}
+
+int main() {
+    // grouped Gram: problems of different K lengths, tiles longest first
+    const int nkb[5] = {313, 160, 40, 16, 3}, cnt[5] = {300, 200, 517, 100, 37};
+    std::vector<TcProblem> dp(5);
+    std::vector<int4> items;
+    for (int p = 0; p < 5; ++p) {
+        dp[p] = TcProblem{};
+        dp[p].nkb = nkb[p];
+        for (int c = 0; c < cnt[p]; ++c) items.push_back(make_int4(p, c, 0, 0));
+    }
+    auto key = [](const int4 &a) { return std::make_tuple(a.x, a.y, a.z, a.w); };
+    auto sorted = [&](std::vector<int4> v) {
+        std::sort(v.begin(), v.end(), [&](const int4 &a, const int4 &b) { return key(a) < key(b); });
+        return v;
+    };
+    const std::vector<int4> ref = sorted(items);
+    for (int G : {1, 7, 152, 2000}) {
+        CHECK(gram_order(dp, items, 0, G, 0).size() == items.size());
+        const std::vector<long> base = loads(dp, gram_order(dp, items, 0, G, 0), G, 0);
+        for (int cost : {0, 8, 32}) {
+            const std::vector<int4> o = gram_order(dp, items, 1, G, cost);
+            // a permutation of the tile list
+            const std::vector<int4> s = sorted(o);
+            CHECK(s.size() == ref.size());
+            for (size_t i = 0; i < s.size(); ++i) CHECK(key(s[i]) == key(ref[i]));
+            // no CTA's K-block load is further from the mean than under longest first
+            const std::vector<long> lb = loads(dp, o, G, 0);
+            const long spread = *std::max_element(lb.begin(), lb.end()) -
+                                *std::min_element(lb.begin(), lb.end());
+            const long spread0 = *std::max_element(base.begin(), base.end()) -
+                                 *std::min_element(base.begin(), base.end());
+            if (cost == 0) CHECK(spread <= spread0);
+            // each round of G slots holds the tiles of one longest-first round
+            for (size_t r = 0; r * G < o.size(); ++r) {
+                const size_t b = r * G, e = std::min(o.size(), b + (size_t)G);
+                std::vector<int4> a(o.begin() + b, o.begin() + e), c(items.begin() + b, items.begin() + e);
+                a = sorted(a);
+                c = sorted(c);
+                for (size_t i = 0; i < a.size(); ++i) CHECK(key(a[i]) == key(c[i]));
+            }
+        }
+    }
+    // longest first is the list as given
+    {
+        const std::vector<int4> o = gram_order(dp, items, 0, 152, 0);
+        for (size_t i = 0; i < o.size(); ++i) CHECK(key(o[i]) == key(items[i]));
+    }
+    // grouped analytic signal: problems with transform lengths in all classes
+    const int Ms[6] = {1280, 20480, 4096, 1280, 10240, 768};
+    const long rows[6] = {70, 40, 201, 1, 130, 9};
+    std::vector<K1Desc> descs(6);
+    for (int i = 0; i < 6; ++i) {
+        descs[i] = K1Desc{};
+        descs[i].plan.M = Ms[i];
+        descs[i].rows = rows[i];
+    }
+    for (int widen = 0; widen < 2; ++widen) {
+        std::map<int, int> cls;
+        if (widen)
+            for (int i = 0; i < 6; ++i)
+                if (conv_class(Ms[i]) < kConvClasses - 1) cls[Ms[i]] = conv_class(Ms[i]) + 1;
+        std::vector<int2> it;
+        K1Group kg{};
+        k1_layout(descs, cls, it, kg);
+        long total = 0;
+        for (int i = 0; i < 6; ++i) total += (rows[i] + 1) / 2;
+        CHECK((long)it.size() == total);
+        long seen = 0;
+        for (int c = 0; c < kConvClasses; ++c) {
+            CHECK(kg.begin[c] == seen);
+            int prevM = 1 << 30, maxM = 0;
+            for (long k = kg.begin[c]; k < kg.begin[c] + kg.count[c]; ++k) {
+                const int M = descs[it[k].x].plan.M;
+                const int want = cls.count(M) ? cls[M] : conv_class(M);
+                CHECK(want == c);                       // in its assigned class
+                CHECK(M <= prevM);                      // longest transform first
+                CHECK(M <= conv_class_max_M(c));        // fits the class's buffer
+                CHECK(it[k].y >= 0 && it[k].y < (rows[it[k].x] + 1) / 2);
+                prevM = M;
+                maxM = std::max(maxM, M);
+            }
+            CHECK(kg.max_M[c] == maxM);
+            seen += kg.count[c];
+        }
+        CHECK(seen == total);
+    }
+    std::printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_tuner_work_lists(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    lib = build.build()
+    src = tmp_path / "schedule_check.cu"
+    src.write_text(PROGRAM)
+    exe = tmp_path / "schedule_check"
+    csrc = os.path.join(ROOT, "paper_1710_08037_gb300", "csrc")
+    subprocess.run([nvcc, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"), "-I", csrc,
+                    str(src), "-o", str(exe), "-L", os.path.dirname(lib), "-lplv",
+                    "-Xlinker", "-rpath", "-Xlinker", os.path.dirname(lib)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
