@@ -217,6 +217,15 @@ uint64_t fnv1a(const void *p, size_t n, uint64_t hsh) {
 
 }  // namespace
 
+// The host helpers of the any-length plans under external names, so that
+// CPU tests can link against them: the transform length for T, its radix
+// order, and the FP64 inverse DFT of any length.
+int conv_length(int T) { return choose_M(T); }
+std::vector<int> conv_radix_order(int M) { return schedule(M); }
+std::vector<std::complex<double>> inverse_dft_any(const std::vector<std::complex<double>> &Y) {
+    return idft_any(Y);
+}
+
 plv_status get_band_plan(Handle &h, cudaStream_t s, int T, const float *masks, int nbands,
                          const ConvPlan **plan, const float2 **K) {
     plv_status st = get_conv_plan(h, T, plan);

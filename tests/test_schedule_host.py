@@ -1,7 +1,11 @@
-"""The autotuner's host-side work lists on CPU: a small C++ program linked
-against the built library calls plv::gram_order (the grouped Gram's tile
-schedules) and plv::k1_layout (the grouped analytic signal's items by thread
-class) and checks their invariants.  Pure host functions: no GPU needed."""
+"""Host-side logic of the library on CPU, through small C++ programs linked
+against the built library (pure host functions: no GPU needed):
+- the autotuner's work lists: plv::gram_order (the grouped Gram's tile
+  schedules) and plv::k1_layout (the grouped analytic signal's items by
+  thread class);
+- the any-length plans: the transform length for T, its radix order, and
+  the FP64 inverse DFT of any length that builds the band kernels, against
+  a direct sum."""
 import os
 import shutil
 import subprocess
@@ -124,14 +128,80 @@ int main() {
 """
 
 
-def test_tuner_work_lists(tmp_path):
+PLAN_PROGRAM = r"""
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+#include "common.cuh"
+namespace plv {
+int conv_length(int T);
+std::vector<int> conv_radix_order(int M);
+std::vector<std::complex<double>> inverse_dft_any(const std::vector<std::complex<double>> &Y);
+}
+using namespace plv;
+typedef std::complex<double> cd;
+
+#define CHECK(c) do { if (!(c)) { std::printf("FAIL %s:%d %s\n", __FILE__, __LINE__, #c); \
+    return 1; } } while (0)
+
+int main() {
+    for (int T = 2; T <= kMaxConvM / 2; T += (T < 300 ? 1 : 97)) {
+        const int M = conv_length(T);
+        // the smallest 2^a, 3 2^a or 5 2^a (>= 32) that holds 2T - 1
+        CHECK(M >= 2 * T - 1 && M >= 32 && M <= kMaxConvM);
+        int odd = M;
+        while (odd % 2 == 0) odd /= 2;
+        CHECK(odd == 1 || odd == 3 || odd == 5);
+        for (int f : {1, 3, 5})
+            for (int p = 32; f * p < M; p *= 2) CHECK(f * p < 2 * T - 1);
+        // radix order: stages of at most kConvMaxRadix whose product is M, the
+        // odd factor (if any) first so that every later span is a power of two
+        const std::vector<int> r = conv_radix_order(M);
+        CHECK(!r.empty() && (int)r.size() <= 8);
+        long prod = 1;
+        for (size_t k = 0; k < r.size(); ++k) {
+            CHECK(r[k] >= 2 && r[k] <= kConvMaxRadix);
+            if (k > 0) CHECK((r[k] & (r[k] - 1)) == 0);
+            prod *= r[k];
+        }
+        CHECK(prod == M);
+        if (odd != 1) CHECK(r[0] == odd);
+    }
+    // FP64 inverse DFT of any length against the direct sum
+    for (int T : {1, 2, 3, 5, 7, 31, 100, 333, 1000, 4097, 12288}) {
+        std::vector<cd> Y(T);
+        std::srand(T);
+        for (int k = 0; k < T; ++k)
+            Y[k] = cd(std::rand() / (double)RAND_MAX - 0.5, std::rand() / (double)RAND_MAX - 0.5);
+        const std::vector<cd> y = inverse_dft_any(Y);
+        CHECK((int)y.size() == T);
+        double err = 0.0;
+        for (int n = 0; n < T; n += (T > 2000 ? 61 : 1)) {
+            cd sum = 0.0;
+            for (int k = 0; k < T; ++k) {
+                const long long q = ((long long)k * n) % T;
+                sum += Y[k] * std::polar(1.0, 2.0 * M_PI * (double)q / T);
+            }
+            err = std::fmax(err, std::abs(sum / (double)T - y[n]));
+        }
+        CHECK(err < 1e-14);
+    }
+    std::printf("ok\n");
+    return 0;
+}
+"""
+
+
+def _run_program(tmp_path, name, program):
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
     lib = build.build()
-    src = tmp_path / "schedule_check.cu"
-    src.write_text(PROGRAM)
-    exe = tmp_path / "schedule_check"
+    src = tmp_path / f"{name}.cu"
+    src.write_text(program)
+    exe = tmp_path / name
     csrc = os.path.join(ROOT, "paper_1710_08037_gb300", "csrc")
     subprocess.run([nvcc, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "include"), "-I", csrc,
                     str(src), "-o", str(exe), "-L", os.path.dirname(lib), "-lplv",
@@ -139,3 +209,11 @@ def test_tuner_work_lists(tmp_path):
                    check=True, capture_output=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
+def test_tuner_work_lists(tmp_path):
+    _run_program(tmp_path, "schedule_check", PROGRAM)
+
+
+def test_any_length_plan_helpers(tmp_path):
+    _run_program(tmp_path, "plan_check", PLAN_PROGRAM)
