@@ -154,3 +154,19 @@ def test_noalloc_backward_rejects_on_the_host(lib):
     assert rc == _lib.PLV_ERR_INVALID
     lib.plv_last_error.restype = ctypes.c_char_p
     assert b"scratch" in lib.plv_last_error(None)
+
+
+def test_no_cpu_path_without_a_gpu():
+    """Without a CUDA device the binding refuses to run instead of falling
+    back to the CPU (the oracle is never on the product path)."""
+    import torch
+    import paper_1710_08037_gb300 as plv
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(plv.PlvError):
+        plv.Handle(precision="bf16x3")
+    import sys
+    assert "oracle" not in {m.split(".")[0] for m in sys.modules
+                            if m.startswith("paper_1710_08037_gb300")}
+    src = open(os.path.join(ROOT, "paper_1710_08037_gb300", "__init__.py")).read()
+    assert "import oracle" not in src and "from oracle" not in src
