@@ -5,16 +5,20 @@ One step = the whole hot path over one batch: analytic signal + unit phasors
 (K1) and the Hermitian Gram with the fused read-outs (Gram kernel) for every
 epoch of the workload, inputs already resident in HBM.  Prints ONE JSON line.
 
-Workload (default): N = 4096 sources, T = 4096 samples, 30 epochs of
+Workload (default): N = 8192 sources, T = 8192 samples, 20 epochs of
 band-limited (8-12 Hz, 4th-order Butterworth, fs = 1000 Hz) noise with 5 % of
 pairs coupled at 5-40 ms lags and 20 % of channels as zero-lag leakage
-mixtures -- synthetic stand-in for whole-brain MEG source-space data.
+mixtures -- synthetic stand-in for whole-brain MEG source-space data -- on
+the BF16x3 split-precision tensor-core Gram, with the plain FP32 path timed
+on the same input beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
   python bench.py --impl reference      # FP64 CPU oracle on a sample
 
 Multi-GPU: epochs are independent problems; every rank runs its own copy of
 the workload on its own GPU (weak scaling, no collective on the data path).
+``--gpus N`` without a process group spawns the N ranks itself (one process
+per GPU, torch.distributed.run on 127.0.0.1).
 """
 from __future__ import annotations
 
@@ -38,10 +42,11 @@ WORKLOADS = {
     # name: (E, N, T, seed)
     "bandlimited-N4096-T4096-E30": (30, 4096, 4096, 1002),
     "bandlimited-N8192-T8192-E20": (20, 8192, 8192, 1003),
-    # small case of the first, for ncu captures (still larger than L2)
+    # small cases of the two, for ncu captures (still larger than L2)
     "bandlimited-N4096-T4096-E4": (4, 4096, 4096, 1002),
+    "bandlimited-N8192-T8192-E2": (2, 8192, 8192, 1003),
 }
-DEFAULT_WORKLOAD = "bandlimited-N4096-T4096-E30"
+DEFAULT_WORKLOAD = "bandlimited-N8192-T8192-E20"
 # uneven batch: 256 subjects, N ~ U{68..2000}, T ~ U{500..10000} per subject,
 # 5 frequency bands each (1280 problems of one epoch), fs = 1000 Hz
 GROUPED = "grouped-256subj-5bands-N68to2000-T500to10000"
@@ -154,17 +159,24 @@ class ClockSampler:
 
 
 # DRAM traffic per launch of the dominant kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel build,
-# workload and precision.  Captured on the 4-epoch case and scaled to the
-# launch by epochs (profiles/k_gram_tc_and_k_hilbert_pairs_bandlimited-N4096-T4096-E4.md).
-# An entry is removed when the kernel changes after its capture.
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a smaller case of the same
+# N and T, scaled to the timed launch by epochs (the Gram's traffic is per
+# epoch: its tiles never span epochs).  Keyed by kernel, workload and
+# precision; an entry is removed when the kernel changes after its capture.
 TRAFFIC = {
-    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_gram_tc launch
-    # on bandlimited-N4096-T4096-E4 (per-block staged stores, one-chunk
-    # streaming epilogue, rsqrt read-outs), scaled by epochs
-    ("k_gram_tc", "bandlimited-N4096-T4096-E30", "bf16x3"): (2.076357e9 + 0.909070e9) * 30 / 4,
-
 }
+
+
+def workload_config(workload, N, T, E, prec, world, in_bytes=4):
+    """The ``config`` object of a bench line for the N x N x T x E workload:
+    the same dict in both arms, so that they name the same job."""
+    return {"workload": workload, "N": N, "T": T, "epochs_per_gpu": E,
+            "precision": prec, "input_dtype": "f32",
+            "l2": "inputs larger than L2 (x %.1f GB, phasors %.1f GB, "
+                  "outputs %.1f GB per step)" % (
+                      E * N * T * in_bytes / 1e9, E * N * T * 8 / 1e9,
+                      3 * E * N * N * 4 / 1e9),
+            "parallelism": f"weak: {world} independent replicas"}
 
 
 def gram_flops(N, T, E, prec):
@@ -339,6 +351,11 @@ def run_ours(args):
     peaks, peak_kind = _peaks()
     prec = args.precision
     flops = gram_flops(N, T, E, prec)
+    # the Gram runs inside a timed region of back-to-back steps; beyond about
+    # a second of it the power cap sets the clock, which the sustained peak
+    # (a seconds-long cuBLAS loop) is measured under
+    timed_s = ms / 1e3
+    sustained = args.peak == "sustained" or (args.peak == "auto" and timed_s >= 1.0)
     if prec == "fp32":
         # plain-ALU bound: FP32 FMA pipes, 152 SMs x 128 lanes x 2 flop x clock
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -349,20 +366,23 @@ def run_ours(args):
                 "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x "
                                f"{sm_mhz:.0f} MHz (max SM clock, {peak_kind})"}
     else:
-        peak = float(peaks["bf16_tflops_sustained" if args.sustained
-                           else "bf16_tflops"])
+        burst = float(peaks["bf16_tflops"])
+        peak = float(peaks["bf16_tflops_sustained"]) if sustained else burst
         roof = {"bound": "tensor", "kernel": "k_gram_tc",
                 "achieved": flops / (gram_ms / 1e3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s",
                 "peak_source": f"{peak_kind} bf16 dense "
-                               f"({'sustained' if args.sustained else 'burst'})"}
+                               f"({'sustained: the Gram is timed inside %.1f s of back-to-back steps' % timed_s if sustained else 'burst'})",
+                "frac_of_burst": flops / (gram_ms / 1e3) / 1e12 / burst}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = TRAFFIC.get((roof["kernel"], args.workload, prec))
     roof["launch_ms"] = gram_ms
+    roof["flops_per_launch"] = flops
+    roof["algorithmic_bytes_per_launch"] = E * N * T * 8.0 + 3 * 4.0 * E * N * N
     k1b = k1_bytes(N, T, E, x.element_size())
-    k1 = {"kernel": "k_analytic_pow2", "bound": "hbm", "launch_ms": k1_ms,
+    k1 = {"kernel": "k_hilbert_pairs", "bound": "hbm", "launch_ms": k1_ms,
           "achieved": k1b / (k1_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
-          "unit": "GB/s"}
+          "unit": "GB/s", "bytes_per_launch": k1b}
     k1["frac"] = k1["achieved"] / k1["peak"]
 
     cpu = None
@@ -383,14 +403,8 @@ def run_ours(args):
                       "accumulate)"}[prec],
             "data": "synthetic (seeded band-limited noise, coupled pairs, "
                     "leakage mixtures; MEG recording not available)",
-            "config": {"workload": args.workload, "N": N, "T": T,
-                       "epochs_per_gpu": E, "precision": prec,
-                       "input_dtype": "f32",
-                       "l2": "inputs larger than L2 (x %.1f GB, phasors "
-                             "%.1f GB, outputs %.1f GB per step)" % (
-                                 E * N * T * 4 / 1e9, E * N * T * 8 / 1e9,
-                                 3 * E * N * N * 4 / 1e9),
-                       "parallelism": f"weak: {world} independent replicas"},
+            "config": workload_config(args.workload, N, T, E, prec, world,
+                                      x.element_size()),
             "roofline": roof,
             "k1_roofline": k1,
             "cpu_baseline": cpu,
@@ -1086,49 +1100,77 @@ def sample_channels(N, seed, nsub):
     return np.sort(rng.choice(N, size=min(nsub, N), replace=False))
 
 
-def cpu_baseline(E, N, T, seed, nsub, x=None, values=None):
-    """The FP64 oracle as it stands, on a bounded sample of the same
-    workload: one epoch, a random subset S of ``nsub`` channels; direct-DFT
-    analytic signal of S, then the pairwise loop over all |S|^2 pairs.  The
-    per-epoch time is extrapolated as t_hilbert * N/|S| + t_pairs * (N/|S|)^2
-    (both parts are linear in rows resp. pairs).  ``x``: the workload's
-    input (epoch 0 is used), else it is generated; ``values``: a dict that
-    receives the oracle's PLV / iPLV / ciPLV of the sample."""
+def _epoch0(N, T, seed, x=None):
+    """Epoch 0 of the workload's input: from ``x`` if given, else generated
+    (epoch 0 of an E-epoch draw equals a one-epoch draw of the same seed)."""
     import torch
-    import oracle
     from paper_1710_08037_gb300 import synth
     if x is None:
         x = synth.bandlimited(1, N, T, seed=seed, device="cpu"
                               if not torch.cuda.is_available() else "cuda")
-    sub = sample_channels(N, seed, nsub)
-    xs = x[0][torch.as_tensor(sub, device=x.device)].double().cpu().numpy()
+    return x[0]
+
+
+def oracle_step(x0, sub):
+    """One bounded step of the FP64 oracle: the direct-DFT analytic signal of
+    the channel subset ``sub`` of epoch-0 rows ``x0``, then the pairwise
+    loop over all |sub|^2 ordered pairs.  Returns (outputs, z, seconds of
+    the analytic signal, seconds of the pairwise loop)."""
+    import torch
+    import oracle
+    xs = x0[torch.as_tensor(sub, device=x0.device)].double().cpu().numpy()
     t0 = time.perf_counter()
     z = oracle.analytic(xs)
     t1 = time.perf_counter()
     ref = oracle.pairwise(z)
     t2 = time.perf_counter()
+    return ref, z, t1 - t0, t2 - t1
+
+
+def extrapolated_epoch_s(N, nsub, t_hilbert, t_pairs):
+    """Seconds the oracle would take for one full epoch of N channels: its
+    analytic signal is linear in rows, its pairwise loop in pairs."""
+    r = N / nsub
+    return t_hilbert * r + t_pairs * r * r
+
+
+def cpu_baseline(E, N, T, seed, nsub, x=None, values=None):
+    """The FP64 oracle as it stands, on a bounded sample of the same
+    workload: one epoch, a random subset S of ``nsub`` channels; direct-DFT
+    analytic signal of S, then the pairwise loop over all |S|^2 pairs.
+    ``value`` is the measured rate on that sample, |S|^2 T per second of
+    oracle time; the rate extrapolated to a full epoch (analytic signal
+    linear in rows, pairs quadratic) is given beside it.  ``x``: the
+    workload's input (epoch 0 is used), else it is generated; ``values``: a
+    dict that receives the oracle's PLV / iPLV / ciPLV of the sample."""
+    import numpy as np
+    import oracle
+    sub = sample_channels(N, seed, nsub)
+    ref, z, th, tp = oracle_step(_epoch0(N, T, seed, x), sub)
     if values is not None:
         values.update({k: ref[k] for k in ("plv", "iplv", "ciplv")})
     # context: the paper's reformulation on the same sample and host,
     # unit phasors once, then one complex FP64 matrix product (numpy's BLAS)
-    import numpy as np
     t3 = time.perf_counter()
     az = np.abs(z)
     Pz = np.where(az > 0, z / np.where(az > 0, az, 1.0), 0.0)
     _ = (Pz @ Pz.conj().T) / z.shape[1]
     t4 = time.perf_counter()
-    r = N / len(sub)
-    t_epoch = (t1 - t0) * r + (t2 - t1) * r * r
-    value = float(N) * N * T / t_epoch
-    return {"value": value, "unit": UNIT, "cores": oracle.threads(),
-            "kind": "oracle",
+    t_epoch = extrapolated_epoch_s(N, len(sub), th, tp)
+    return {"value": float(len(sub)) ** 2 * T / (th + tp), "unit": UNIT,
+            "cores": oracle.threads(), "kind": "oracle",
             "sample": f"1 of {E} epochs, {len(sub)} of {N} channels: "
-                      f"direct-DFT analytic signal {t1 - t0:.2f} s, pairwise "
-                      f"loop over {len(sub)}^2 pairs {t2 - t1:.2f} s; "
-                      f"extrapolated to one full epoch ({t_epoch:.1f} s)",
+                      f"direct-DFT analytic signal {th:.2f} s, pairwise "
+                      f"loop over {len(sub)}^2 pairs {tp:.2f} s; value = "
+                      f"{len(sub)}^2 x {T} channel-pair samples / {th + tp:.2f} s",
+            "sample_s": th + tp,
+            "extrapolated_full_epoch": {
+                "value": float(N) * N * T / t_epoch, "unit": UNIT,
+                "epoch_s": t_epoch,
+                "how": "analytic signal x N/|S|, pairwise loop x (N/|S|)^2"},
             "context_gram_vs_pairwise": {
-                "pairwise_loop_s": t2 - t1, "gram_fp64_blas_s": t4 - t3,
-                "speedup": (t2 - t1) / max(t4 - t3, 1e-9),
+                "pairwise_loop_s": tp, "gram_fp64_blas_s": t4 - t3,
+                "speedup": tp / max(t4 - t3, 1e-9),
                 "note": "the paper's reformulation (unit phasors once, one "
                         "complex matrix product; numpy BLAS) against the "
                         "pairwise loop on the same sample and host; the paper "
@@ -1137,33 +1179,71 @@ def cpu_baseline(E, N, T, seed, nsub, x=None, values=None):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores.
+    Each step is one bounded sample of the workload (epoch 0, the seeded
+    channel subset the GPU arm's cpu_baseline uses, all its ordered pairs);
+    ms_per_step is that step's measured wall time and value the sample's
+    channel-pair samples per second of it.  Under torchrun only rank 0
+    runs."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
     E, N, T, seed = WORKLOADS[args.workload]
-    steps = []
-    cpu = None
+    x0 = _epoch0(N, T, seed)
+    sub = sample_channels(N, seed, args.cpu_sample)
     for _ in range(args.warmup):
-        cpu_baseline(E, N, T, seed, args.ref_sample)
+        oracle_step(x0, sub)
+    walls, parts = [], []
     for _ in range(args.steps):
-        cpu = cpu_baseline(E, N, T, seed, args.ref_sample)
-        steps.append(cpu["value"])
-    value = statistics.median(steps)
-    cpu["value"] = value
+        t0 = time.perf_counter()
+        _, _, th, tp = oracle_step(x0, sub)
+        walls.append(time.perf_counter() - t0)
+        parts.append((th, tp))
+    ms_step = 1e3 * sum(walls) / len(walls)
+    units = float(len(sub)) ** 2 * T
+    value = units / (ms_step / 1e3)
+    th = statistics.mean(p[0] for p in parts)
+    tp = statistics.mean(p[1] for p in parts)
+    t_epoch = extrapolated_epoch_s(N, len(sub), th, tp)
+    cpu = {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+           "sample": f"per step: epoch 0 of {E}, {len(sub)} of {N} channels "
+                     f"(seeded), direct-DFT analytic signal {th:.2f} s + "
+                     f"pairwise loop over {len(sub)}^2 pairs {tp:.2f} s",
+           "extrapolated_full_epoch": {
+               "value": float(N) * N * T / t_epoch, "unit": UNIT, "epoch_s": t_epoch,
+               "how": "analytic signal x N/|S|, pairwise loop x (N/|S|)^2"}}
     line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": float(N) * N * T / value * 1e3,
+            "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "N": N, "T": T,
-                       "epochs_per_gpu": 1,
-                       "note": "each step: the FP64 oracle on a channel "
-                               "sample of one epoch, extrapolated"},
+            "config": workload_config(args.workload, N, T, E, args.precision,
+                                      int(os.environ.get("WORLD_SIZE", "1"))),
+            "units_per_step": units,
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _free_port():
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
+def spawn_replicas(n, argv, script=None):
+    """Run ``script`` (this file by default) as n ranks of one node, one
+    process per GPU, through torch.distributed.run on 127.0.0.1; returns
+    its exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={n}", "--master-addr=127.0.0.1",
+           f"--master-port={_free_port()}", script or os.path.abspath(__file__),
+           *argv]
+    return subprocess.call(cmd)
 
 
 def main():
@@ -1183,8 +1263,9 @@ def main():
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--subjects", type=int, default=256,
                     help="subjects of the grouped workload")
-    ap.add_argument("--sustained", action="store_true",
-                    help="roofline against the sustained tensor peak")
+    ap.add_argument("--peak", choices=["auto", "burst", "sustained"], default="auto",
+                    help="tensor peak of the Gram's roofline: burst, sustained, or "
+                         "(auto) sustained when the timed region lasts a second or more")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="grouped workload: keep the plan's default launch shapes")
@@ -1192,8 +1273,14 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=384)
     ap.add_argument("--e2e-chunks", type=int, default=6)
     ap.add_argument("--e2e-streams", type=int, default=2)
-    ap.add_argument("--ref-sample", type=int, default=192)
     args = ap.parse_args()
+    world_env = os.environ.get("WORLD_SIZE")
+    if world_env is None and args.gpus > 1:
+        # no process group yet: launch the N ranks here
+        sys.exit(spawn_replicas(args.gpus, sys.argv[1:]))
+    if world_env is not None and int(world_env) != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world_env}", file=sys.stderr)
+        sys.exit(2)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -264,9 +264,22 @@ struct FwdTask {
     __device__ float2 load(const Rows &rs, int m) const {
         return make_float2(rs.x0 ? ldx_f(rs.x0 + m) : 0.f, rs.x1 ? ldx_f(rs.x1 + m) : 0.f);
     }
+    // L2 prefetch of rows r0, r1 (the power-of-two engine issues it one
+    // pair's work ahead)
+    static constexpr bool kPrefetch = true;
+    __device__ void prefetch(int64_t r0, bool v0, int64_t r1, bool v1) const {
+        const uint32_t bytes = (uint32_t)(ld * sizeof(Tin)) <= (uint32_t)(ldx * sizeof(Tin))
+                                   ? (uint32_t)(ld * sizeof(Tin)) : (uint32_t)(ldx * sizeof(Tin));
+        if (v0) prefetch_l2(x + r0 * ldx, bytes);
+        if (v1) prefetch_l2(x + r1 * ldx, bytes);
+    }
+    // one Newton step on 1/|z| except for the BF16 split
+    static constexpr bool kNewton = PREC != PLV_PREC_BF16X3;
     __device__ void finish(const Rows &rs, int m, float h0, float h1, float floor2) const {
-        if (rs.x0) store_phasor<PREC>(P, rs.a0, ld, m, unit_phasor(ldx_f(rs.x0 + m), h0, floor2));
-        if (rs.x1) store_phasor<PREC>(P, rs.a1, ld, m, unit_phasor(ldx_f(rs.x1 + m), h1, floor2));
+        if (rs.x0)
+            store_phasor<PREC>(P, rs.a0, ld, m, unit_phasor<kNewton>(ldx_f(rs.x0 + m), h0, floor2));
+        if (rs.x1)
+            store_phasor<PREC>(P, rs.a1, ld, m, unit_phasor<kNewton>(ldx_f(rs.x1 + m), h1, floor2));
     }
     // finish() for eight consecutive samples m0 .. m0+7 < ld (m0 % 8 == 0)
     static constexpr bool kFinish8 = true;
@@ -276,7 +289,7 @@ struct FwdTask {
         load_x8(xr + m0, xv);
         float2 p[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) p[k] = unit_phasor(xv[k], h[k], floor2);
+        for (int k = 0; k < 8; ++k) p[k] = unit_phasor<kNewton>(xv[k], h[k], floor2);
         store_phasor8<PREC>(P, ra, ld, m0, p);
     }
     __device__ void finish8(const Rows &rs, int m0, const float (&h0)[8], const float (&h1)[8],

@@ -201,7 +201,11 @@ __device__ __forceinline__ void middle_passes(float2 *const (&buf)[2], const flo
 
 // Unit phasor of z = a + i b (Eq. 4); |z|^2 <= floor2 (|z| = 0 by default)
 // gives 0.  Very small or very large magnitudes are rescaled by a power of
-// two first so the squared norm neither underflows nor overflows.
+// two first so the squared norm neither underflows nor overflows.  1/|z| is
+// the hardware reciprocal-square-root estimate (a few ulp), refined by one
+// Newton step unless NEWTON is false: the BF16 hi + lo split keeps 2^-17 of
+// a component, far coarser than the estimate's error.
+template <bool NEWTON = true>
 __device__ __forceinline__ float2 unit_phasor(float a, float b, float floor2 = 0.0f) {
     float r2 = fmaf(a, a, b * b);
     if (!(r2 > floor2)) return make_float2(0.f, 0.f);
@@ -211,9 +215,8 @@ __device__ __forceinline__ float2 unit_phasor(float a, float b, float floor2 = 0
         b *= sc;
         r2 = fmaf(a, a, b * b);
     }
-    // 1/sqrt(r2): hardware estimate refined by one Newton step
     float inv = rsqrtf(r2);
-    inv = inv * fmaf(-0.5f * r2 * inv, inv, 1.5f);
+    if (NEWTON) inv = inv * fmaf(-0.5f * r2 * inv, inv, 1.5f);
     return make_float2(a * inv, b * inv);
 }
 
@@ -246,20 +249,165 @@ struct HasFinish8<Task, decltype((void)Task::kFinish8)> {
     static constexpr bool value = Task::kFinish8;
 };
 
+// ---------------------------------------------------------------------------
+// The power-of-two engine's kernel.
+//
+// Per row pair: forward passes 0 .. NP-1, then inverse passes 0 .. NP-1 (the
+// inverse as a forward FFT of the conjugated, masked spectrum), then the
+// task's finish.  The last forward pass (radix 16, NS = T/16, one butterfly
+// per thread at j = lt) and the first inverse pass (radix 16, NS = 1, j = lt)
+// touch the same 16 elements lt + r T/16 on the same thread, so for T >= 256
+// they run fused in registers with the analytic mask between them: one
+// shared-memory round trip and one barrier fewer per pair.  The mask
+// conj(-i sgn(m) C[m]) / T = sgn(m) (Im C, Re C) / T also carries the 1/T of
+// the inverse transform.
+//
+// The twiddles of every pass p >= 1 come from a table in shared memory,
+// filled once per (persistent) CTA from the FP64-rounded global table:
+// for each twiddle position k < NS and s < R/2 the pair
+// (w^(2s ts), w^((2s+1) ts)), w = exp(-2 pi i / T), ts = k T / (NS R),
+// as one float4 at tab_off(L, p) + s NS + k.  Consecutive k sit 16 bytes
+// apart, so a warp's 16-byte reads are conflict-free.
+
+__host__ __device__ constexpr int tab_len(int L, int p) {
+    return (radix_of(L, p) / 2) * ns_of(L, p);
+}
+__host__ __device__ constexpr int tab_off(int L, int p) {
+    return p <= 1 ? 0 : tab_off(L, p - 1) + tab_len(L, p - 1);
+}
+
 template <int L>
 struct K1Cfg {
     static constexpr int T = 1 << L;
+    static constexpr int NP = npasses(L);
     static constexpr int Q = T / kPow2EPT;            // threads / sequence
     static constexpr int SEQ = Q >= 256 ? 1 : 256 / Q;  // sequences / CTA
     static constexpr int THREADS = Q * SEQ;
     static constexpr int SMEM_SEQ = T + T / 32;         // padded elements
-    // two ping-pong buffers per sequence, then the per-sequence power
-    static constexpr size_t SMEM =
-        (size_t)SEQ * 2 * SMEM_SEQ * sizeof(float2) + (size_t)SEQ * sizeof(float);
+    static constexpr int TAB = tab_off(L, NP);          // float4 entries
+    // two ping-pong buffers per sequence, the twiddle table, the per-sequence
+    // power
+    static constexpr size_t SMEM = (size_t)SEQ * 2 * SMEM_SEQ * sizeof(float2) +
+                                   (size_t)TAB * sizeof(float4) +
+                                   (size_t)SEQ * sizeof(float);
     // resident CTAs per SM the register budget is sized for
     static constexpr int MIN_BLOCKS = 65536 / (kPow2Regs * THREADS) > 0
                                           ? 65536 / (kPow2Regs * THREADS) : 1;
+    // the last forward pass fuses with the first inverse pass
+    static constexpr bool FUSED = NP >= 2 && radix_of(L, NP - 1) == kPow2EPT;
 };
+
+template <int L, int P, int NP>
+__device__ __forceinline__ void fill_twiddles(float4 *tab, const float2 *__restrict__ tw) {
+    if constexpr (P < NP) {
+        constexpr int T = 1 << L, R = radix_of(L, P), NS = ns_of(L, P);
+        constexpr int step = T / (NS * R), n = tab_len(L, P), off = tab_off(L, P);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int sidx = i / NS, k = i & (NS - 1);
+            const int ts = k * step;  // (2 sidx + 1) ts < R NS step = T
+            const float2 a = __ldg(&tw[2 * sidx * ts]), b = __ldg(&tw[(2 * sidx + 1) * ts]);
+            tab[off + i] = make_float4(a.x, a.y, b.x, b.y);
+        }
+        fill_twiddles<L, P + 1, NP>(tab, tw);
+    }
+}
+
+// Pass P's inputs of this thread (B = 16/R butterflies at j = lt + q Q) from
+// shared buffer src, twiddled: a[q][r] = src[j + r T/R] w^(r ts).
+template <int L, int P>
+__device__ __forceinline__ void pass_load(const float2 *src, const float4 *tab, int lt,
+                                          float2 (&a)[kPow2EPT / radix_of(L, P)][radix_of(L, P)]) {
+    constexpr int T = 1 << L, R = radix_of(L, P), NS = ns_of(L, P), B = kPow2EPT / R;
+    constexpr int Q = T / kPow2EPT;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int j = lt + q * Q;
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[q][r] = src[padi(j + r * (T / R))];
+        if constexpr (NS > 1) {
+            const float4 *t = tab + tab_off(L, P) + (j & (NS - 1));
+#pragma unroll
+            for (int s2 = 0; s2 < R / 2; ++s2) {
+                const float4 v = t[s2 * NS];
+                if (s2 > 0) a[q][2 * s2] = cmul(a[q][2 * s2], make_float2(v.x, v.y));
+                a[q][2 * s2 + 1] = cmul(a[q][2 * s2 + 1], make_float2(v.z, v.w));
+            }
+        }
+    }
+}
+
+// Pass P's outputs: element base + r NS, base = (j - k) R + k, k = j mod NS.
+template <int L, int P>
+__device__ __forceinline__ void pass_store(float2 *dst, int lt,
+                                           const float2 (&a)[kPow2EPT / radix_of(L, P)][radix_of(L, P)]) {
+    constexpr int T = 1 << L, R = radix_of(L, P), NS = ns_of(L, P), B = kPow2EPT / R;
+    constexpr int Q = T / kPow2EPT;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int j = lt + q * Q;
+        const int k = j & (NS - 1);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[padi(base + r * NS)] = a[q][r];
+    }
+}
+
+// The analytic mask with the inverse's 1/T, on output element m:
+// conj(-i sgn(m) C) / T = sgn(m) (Im C, Re C) / T.
+template <int T>
+__device__ __forceinline__ float2 hilbert_mask(float2 c, int m) {
+    constexpr float invT = 1.0f / (float)T;
+    const float sg = (m == 0 || m == T / 2) ? 0.f : (m < T / 2 ? invT : -invT);
+    return make_float2(sg * c.y, sg * c.x);
+}
+
+// A smem-to-smem pass; MASK applies the analytic mask to its outputs (the
+// last forward pass when it is not fused).
+template <int L, int P, bool MASK = false>
+__device__ __forceinline__ void pass_smem(const float2 *src, float2 *dst, const float4 *tab,
+                                          int lt) {
+    constexpr int R = radix_of(L, P), B = kPow2EPT / R, NS = ns_of(L, P);
+    float2 a[B][R];
+    pass_load<L, P>(src, tab, lt, a);
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        Dft<R>::run(a[q]);
+        if constexpr (MASK) {
+            constexpr int Q = (1 << L) / kPow2EPT;
+            const int j = lt + q * Q, k = j & (NS - 1), base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[q][r] = hilbert_mask<(1 << L)>(a[q][r], base + r * NS);
+        }
+    }
+    pass_store<L, P>(dst, lt, a);
+    __syncthreads();
+}
+
+// Passes P .. PEND-1 between the two buffers: pass P reads buf[P & 1].
+template <int L, int P, int PEND>
+__device__ __forceinline__ void passes(float2 *const (&buf)[2], const float4 *tab, int lt) {
+    if constexpr (P < PEND) {
+        pass_smem<L, P>(buf[P & 1], buf[(P & 1) ^ 1], tab, lt);
+        passes<L, P + 1, PEND>(buf, tab, lt);
+    }
+}
+
+// Optional task hook: issue an L2 prefetch of the inputs of rows (r0, r1).
+template <class Task, class = void>
+struct HasPrefetch {
+    static constexpr bool value = false;
+};
+template <class Task>
+struct HasPrefetch<Task, decltype((void)Task::kPrefetch)> {
+    static constexpr bool value = Task::kPrefetch;
+};
+
+// Bulk prefetch of `bytes` at p into L2 (a hint: skipped unless p and bytes
+// are multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    if (p == nullptr || ((uintptr_t)p & 15) != 0 || (bytes & 15) != 0 || bytes == 0) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // The Hilbert transform of real rows, two rows per complex FFT, for any
 // Task providing
@@ -269,53 +417,94 @@ struct K1Cfg {
 //       the complex sample c[m] = u0[m] + i u1[m] of rows r0, r1;
 //   void finish(const Rows &, int m, float h0, float h1, float floor2):
 //       consumes H{u0}[m], H{u1}[m]; floor2 is 2^-40 of the pair's mean
-//       |c|^2 (the rounding floor of the transform).
-// With c = u0 + i u1: w = IFFT(-i sgn(k) FFT(c)) = H{u0} + i H{u1}, computed
-// as conj(FFT(conj(W))) / T with conj(W) folded into the last forward pass.
+//       |c|^2 (the rounding floor of the transform);
+// and optionally finish8 (eight consecutive samples) and prefetch(r0, v0,
+// r1, v1) (an L2 prefetch of a later pair's inputs).
 template <int L, class Task>
 __global__ void __launch_bounds__(K1Cfg<L>::THREADS, K1Cfg<L>::MIN_BLOCKS)
 k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
                 int64_t nbatch) {
     using C = K1Cfg<L>;
     constexpr int T = C::T;
-    constexpr int NP = npasses(L);
+    constexpr int NP = C::NP;
     extern __shared__ __align__(16) float2 smem[];
     const int lt = threadIdx.x % C::Q;
     const int sq = threadIdx.x / C::Q;
     float2 *const buf[2] = {smem + (2 * sq) * C::SMEM_SEQ, smem + (2 * sq + 1) * C::SMEM_SEQ};
-    float *s_pow = (float *)(smem + 2 * C::SEQ * C::SMEM_SEQ);
-    constexpr float invT = 1.0f / (float)T;
-    // pass p writes buffer ((p & 1) ^ 1); FWD_OUT holds the masked spectrum
-    constexpr int FWD_OUT = ((NP - 1) & 1) ^ 1;
+    float4 *const tab = reinterpret_cast<float4 *>(smem + 2 * C::SEQ * C::SMEM_SEQ);
+    float *const s_pow = reinterpret_cast<float *>(tab + C::TAB);
+    fill_twiddles<L, 1, NP>(tab, tw);  // ordered before use by the loop's first barriers
 
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
         const int64_t pair = b * C::SEQ + sq;
         const int64_t r0 = 2 * pair, r1 = 2 * pair + 1;
         const bool v0 = r0 < rows, v1 = r1 < rows;
-        // the previous pair's final stage is done with the buffers and s_pow
+        if constexpr (HasPrefetch<Task>::value) {
+            // the inputs of this CTA's next pair, one pair's work ahead
+            if (lt == 0 && b + gridDim.x < nbatch) {
+                const int64_t nr0 = 2 * (pair + (int64_t)gridDim.x * C::SEQ);
+                task.prefetch(nr0, nr0 < rows, nr0 + 1, nr0 + 1 < rows);
+            }
+        }
+        // the previous pair's finish is done with the buffers and s_pow
         __syncthreads();
         if (lt == 0) s_pow[sq] = 0.f;  // ordered before the adds by pass 0's barrier
-        float pw;
         const auto rs = task.rows(r0, v0, r1, v1);
-        auto load = [&](int m) { return task.load(rs, m); };
-        stockham<T, radix_of(L, 0), 1, kFromX>(nullptr, buf[1], tw, lt, load, &pw);
-        // sum of |c|^2 over the sequence (its lanes are an aligned group of Q
-        // threads, or whole warps when Q >= 32)
+        // forward pass 0 from the rows, summing |c|^2
+        {
+            constexpr int R = radix_of(L, 0), B = kPow2EPT / R;
+            float2 a[B][R];
+            float pw = 0.f;
 #pragma unroll
-        for (int off = 1; off < (C::Q < 32 ? C::Q : 32); off <<= 1)
-            pw += __shfl_xor_sync(0xffffffffu, pw, off);
-        if ((lt & 31) == 0) atomicAdd(&s_pow[sq], pw);
-        middle_passes<L, 1, NP - 1>(buf, tw, lt);
-        stockham<T, radix_of(L, NP - 1), ns_of(L, NP - 1), kToHilbert>(
-            buf[(NP - 1) & 1], buf[FWD_OUT], tw, lt, NoLoad{});
-        float2 *const ibuf[2] = {buf[FWD_OUT], buf[FWD_OUT ^ 1]};
-        stockham<T, radix_of(L, 0), 1, kSmem>(ibuf[0], ibuf[1], tw, lt, NoLoad{});
-        middle_passes<L, 1, NP - 1>(ibuf, tw, lt);
-        stockham<T, radix_of(L, NP - 1), ns_of(L, NP - 1), kSmem>(
-            ibuf[(NP - 1) & 1], ibuf[((NP - 1) & 1) ^ 1], tw, lt, NoLoad{});
-        const float2 *w_out = ibuf[((NP - 1) & 1) ^ 1];
+            for (int q = 0; q < B; ++q) {
+                const int j = lt + q * C::Q;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float2 c = task.load(rs, j + r * (T / R));
+                    a[q][r] = c;
+                    pw = fmaf(c.x, c.x, fmaf(c.y, c.y, pw));
+                }
+                Dft<R>::run(a[q]);
+            }
+            pass_store<L, 0>(buf[1], lt, a);
+            __syncthreads();
+            // sum of |c|^2 over the sequence (its lanes are an aligned group
+            // of Q threads, or whole warps when Q >= 32)
+#pragma unroll
+            for (int off = 1; off < (C::Q < 32 ? C::Q : 32); off <<= 1)
+                pw += __shfl_xor_sync(0xffffffffu, pw, off);
+            if ((lt & 31) == 0) atomicAdd(&s_pow[sq], pw);
+        }
+        passes<L, 1, NP - 1>(buf, tab, lt);
+        // the spectrum's last forward pass, the mask and the first inverse
+        // pass; FB is the buffer the first inverse pass leaves its output in
+        constexpr int FB = ((NP - 1) & 1) ^ 1;
+        if constexpr (C::FUSED) {
+            float2 a[1][kPow2EPT];
+            pass_load<L, NP - 1>(buf[(NP - 1) & 1], tab, lt, a);
+            Dft<kPow2EPT>::run(a[0]);
+            // element m = lt + r T/16: m < T/2 for r < 8; m = 0, T/2 at lt = 0
+            constexpr float invT = 1.0f / (float)T;
+#pragma unroll
+            for (int r = 0; r < kPow2EPT; ++r) {
+                const float sg = (lt == 0 && (r & 7) == 0) ? 0.f : (r < 8 ? invT : -invT);
+                a[0][r] = make_float2(sg * a[0][r].y, sg * a[0][r].x);
+            }
+            Dft<kPow2EPT>::run(a[0]);
+            pass_store<L, 0>(buf[FB], lt, a);
+            __syncthreads();
+        } else {
+            pass_smem<L, NP - 1, true>(buf[(NP - 1) & 1], buf[FB], tab, lt);
+            pass_smem<L, 0>(buf[FB], buf[FB ^ 1], tab, lt);
+        }
+        // inverse passes 1 .. NP-1: inverse pass 0 left its output in buf[O],
+        // and pass p reads pbuf[p & 1]
+        constexpr int O = C::FUSED ? FB : FB ^ 1;
+        float2 *const pbuf[2] = {buf[O ^ 1], buf[O]};
+        passes<L, 1, NP>(pbuf, tab, lt);
+        const float2 *w_out = pbuf[NP & 1];
 
-        const float floor2 = 0x1p-40f * (s_pow[sq] * invT);
+        const float floor2 = 0x1p-40f * (s_pow[sq] * (1.0f / (float)T));
         if constexpr (HasFinish8<Task>::value) {
             // eight consecutive samples per call (vector loads and stores)
 #pragma unroll
@@ -325,8 +514,8 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const float2 w = w_out[padi(m0 + k)];
-                    h0[k] = w.x * invT;
-                    h1[k] = -w.y * invT;
+                    h0[k] = w.x;
+                    h1[k] = -w.y;
                 }
                 task.finish8(rs, m0, h0, h1, floor2);
             }
@@ -335,7 +524,7 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
             for (int u = 0; u < kPow2EPT; ++u) {
                 const int m = lt + u * C::Q;
                 const float2 w = w_out[padi(m)];
-                task.finish(rs, m, w.x * invT, -w.y * invT, floor2);
+                task.finish(rs, m, w.x, -w.y, floor2);
             }
         }
     }
@@ -353,7 +542,8 @@ cudaError_t launch_hilbert_pairs(int num_sms, cudaStream_t st, const Task &task,
     const int64_t pairs = (rows + 1) / 2;
     const int64_t nbatch = (pairs + C::SEQ - 1) / C::SEQ;
     if (nbatch == 0) return cudaSuccess;
-    int64_t grid = (int64_t)per_sm * num_sms * 4;
+    // one wave of persistent CTAs (each fills its twiddle table once)
+    int64_t grid = (int64_t)per_sm * num_sms;
     if (grid > nbatch) grid = nbatch;
     kern<<<(unsigned)grid, C::THREADS, C::SMEM, st>>>(task, tw, rows, nbatch);
     return cudaGetLastError();

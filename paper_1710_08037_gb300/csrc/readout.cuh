@@ -7,14 +7,21 @@
 
 namespace plv {
 
-// Denominator of Eq. 14, d = 1 - (Re C)^2, formed as (1 - r)(1 + r) in
-// FP32, which does not cancel: for |r| >= 1/2 the factor 1 - |r| is exact
-// (Sterbenz's lemma: 1 and |r| are within a factor of two) and the other
-// factor lies in [3/2, 2) with at most half an ulp of rounding; below 1/2
-// both factors lie in (1/2, 3/2).  So d carries about one ulp of relative
-// rounding in every range, far below the effect of the input's own error
-// (2 |r| dr).  Forming it in FP64 changes d by at most that ulp.
+// Denominator of Eq. 14, d = 1 - (Re C)^2, formed as (1 - r)(1 + r).  Where
+// the plain 1 - r^2 would cancel, |r| > 1 - 2^-6 (d < 2^-5), the factors and
+// their product are taken in FP64, so d is the exactly rounded FP32 value of
+// the FP32 input's true denominator.  Below that threshold the FP32 factored
+// form already carries about one ulp: for |r| >= 1/2 the factor 1 - |r| is
+// exact (Sterbenz's lemma) and the other lies in [3/2, 2) with at most half
+// an ulp of rounding; below 1/2 both factors lie in (1/2, 3/2).  Either way
+// the rounding of d is far below the effect of the Gram's own error in r
+// (2 |r| dr).
+constexpr float kCiplvFp64Above = 1.0f - 0x1p-6f;
 __device__ __forceinline__ float ciplv_den(float r) {
+    if (fabsf(r) > kCiplvFp64Above) {
+        const double rd = (double)r;
+        return (float)((1.0 - rd) * (1.0 + rd));
+    }
     return (1.0f - r) * (1.0f + r);
 }
 

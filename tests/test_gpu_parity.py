@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from paper_1710_08037_gb300 import synth
-from tests.helpers import DIAG_TOL, PHASOR_TOL, TOL, compare, unpack_phasors
+from tests.helpers import DIAG_TOL, PHASOR_TOL, TOL, ciplv_bound, compare, unpack_phasors
 
 pytestmark = pytest.mark.gpu
 
@@ -168,6 +168,70 @@ def test_metrics_kernel_matches_fused_epilogue(handles, prec):
     m = h.plv_metrics(res["C"])
     for k in ("plv", "iplv", "ciplv"):
         assert torch.equal(m[k], res[k]), k
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_ciplv_near_zero_lag_tones(handles, prec):
+    """Eq. 14 where it is ill-conditioned: on-bin tone pairs at lags of
+    1e-1, 1e-2 and 3e-3 rad (1 - Re^2 = sin^2 lag down to ~1e-5), whole path
+    from x, ciPLV element by element against the oracle within the
+    first-order conditioned bound of the path's tolerance; the closed form
+    (Section II.C: a pure lag gives ciPLV = sign(sin lag)) must survive where
+    the bound is below 1."""
+    h = handles[prec]
+    T, k0 = 2048, 40
+    lags = [1e-1, -1e-1, 1e-2, -1e-2, 3e-3, -3e-3]
+    t = np.arange(T)
+    rows, pairs = [], []
+    rng = np.random.default_rng(7)
+    for lag in lags:
+        th = rng.uniform(0, 2 * np.pi)
+        rows.append(np.cos(2 * np.pi * k0 * t / T + th))
+        rows.append(np.cos(2 * np.pi * k0 * t / T + th - lag))
+        pairs.append((len(rows) - 2, len(rows) - 1, lag))
+    x = np.stack(rows)[None]
+    res = _to_np(h.connectivity(torch.tensor(x, device="cuda"), C=True))
+    ref = oracle.connectivity(x[0])
+    gpu = {k: res[k][0] for k in ("plv", "iplv", "ciplv")}
+    compare(gpu, ref, TOL[prec])
+    for a, b, lag in pairs:
+        # oracle: the closed form, to FP64 rounding amplified by 1/|sin lag|
+        assert abs(ref["ciplv"][a, b] - math.copysign(1.0, math.sin(lag))) < 1e-9 / abs(lag)
+        bound = float(ciplv_bound(np.asarray(ref["c"][a, b]), TOL[prec]))
+        if bound < 0.5:
+            assert np.sign(gpu["ciplv"][a, b]) == np.sign(math.sin(lag))
+            assert np.sign(gpu["ciplv"][b, a]) == -np.sign(math.sin(lag))
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_ciplv_denominator_near_unit_real_part(handles, prec):
+    """Eq. 14's denominator (1 - Re)(1 + Re) on given FP32 values of C with
+    |Re C| from 0.3 to 1 - 2^-24 (both sides of the FP64 threshold 1 - 2^-6):
+    ciPLV against the FP64 value of the same FP32 inputs to a few ulp
+    (the reciprocal square root's error), and 0 where Re^2 >= 1."""
+    h = handles[prec]
+    n = 64
+    rng = np.random.default_rng(11)
+    C = (rng.uniform(-0.5, 0.5, (1, n, n)) + 1j * rng.uniform(-0.5, 0.5, (1, n, n)))
+    C = C.astype(np.complex64)
+    re = np.concatenate([
+        np.float32(1.0) - np.float32(2.0 ** -24) * np.arange(1, 9, dtype=np.float32),
+        np.float32(1.0) - np.float32(2.0 ** -6) * np.array([0.5, 1.0, 1.5, 2.0], np.float32),
+        np.float32(1.0) - np.float32(2.0 ** -12) * np.arange(1, 5, dtype=np.float32),
+        np.array([0.3, 0.5, 0.75, 0.9, 1.0, 1.0 + 2 ** -23], np.float32)]).astype(np.float32)
+    re = np.concatenate([re, -re])
+    im = (rng.uniform(1e-4, 1e-2, re.size) * rng.choice([-1, 1], re.size)).astype(np.float32)
+    ii = np.arange(re.size) % n
+    jj = (ii + 1 + np.arange(re.size) // n) % n  # off the diagonal
+    C[0, ii, jj] = re + 1j * im
+    m = h.plv_metrics(torch.tensor(C, device="cuda"))
+    got = m["ciplv"][0].double().cpu().numpy()[ii, jj]
+    r64, i64 = re.astype(np.float64), im.astype(np.float64)
+    d = (1.0 - r64) * (1.0 + r64)
+    want = np.where(d > 0, i64 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
+    rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-30)
+    assert np.all(rel[d > 0] < 1e-6), float(rel[d > 0].max())
+    assert np.all(got[d <= 0] == 0.0)
 
 
 @pytest.mark.parametrize("prec", PRECISIONS)

@@ -66,6 +66,39 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
         workload = "bandlimited-N4096-T4096-E30"
         steps = 1
         warmup = 0
-        ref_sample = 8
+        cpu_sample = 8
+        precision = "bf16x3"
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+def test_gpus_flag_spawns_the_ranks():
+    """``bench.py --gpus 2`` without a process group launches two ranks
+    itself (torch.distributed.run on 127.0.0.1); on the reference arm rank 0
+    alone prints the line and rank 1 exits without work."""
+    import json
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                        "--impl", "reference", "--workload", "bandlimited-N4096-T4096-E4",
+                        "--steps", "1", "--warmup", "0", "--cpu-sample", "8"],
+                       capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+    # the step time is the measured sample time, and value is its rate
+    assert line["value"] == pytest.approx(line["units_per_step"] / (line["ms_per_step"] / 1e3))
+
+
+def test_gpus_flag_must_match_the_process_group():
+    import subprocess
+    import sys
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                        "--impl", "reference"], capture_output=True, text=True, env=env,
+                       timeout=300)
+    assert r.returncode == 2 and "WORLD_SIZE" in r.stderr
