@@ -94,6 +94,16 @@ const char *plv_last_error(const plv_handle *h);
 /* Gram arithmetic the handle was created with. */
 plv_precision plv_get_precision(const plv_handle *h);
 
+/* Tile order of the tensor-core Gram of later plv_gram / plv_gram_windows
+ * calls on this handle (no counterpart in the paper: a schedule of the
+ * Eq. 7 tiles, which changes which CTA computes a tile, never its value).
+ * The 128 x 128 upper-triangle tiles of each epoch go by super-columns of
+ * `width` 128-row blocks, so that the tiles running at the same time share
+ * their row panels in L2.  width 0 restores the default (16); a width of at
+ * least ceil(N / 128) gives the plain column-major triangle.  FP32 handles
+ * accept and ignore it.  PLV_ERR_INVALID for a NULL handle or width < 0. */
+plv_status plv_set_gram_raster(plv_handle *h, int width);
+
 /* Row length (in elements) of the phasor operand layout for T samples: T
  * rounded up to a multiple of 32; the padding samples are zero. */
 int64_t plv_phasor_ld(int T);
@@ -340,7 +350,11 @@ plv_status plv_metrics(plv_handle *h, void *stream, const void *C, int batch,
  * scratch of batch*N*ld*20 bytes plus, on an FP32 handle, batch*N*N*8, or,
  * on a split handle, batch*(ceil(N/128) + ceil(ld/128))*128*ceil(N/32)*32*8;
  * allocated on first use for a size (cudaMalloc; fails with PLV_ERR_INVALID
- * if that first use is inside a stream capture). */
+ * if that first use is inside a stream capture).  A CUDA graph captured
+ * with this call keeps using the scratch it was captured with: when a later,
+ * larger call (outside capture) grows the scratch, a buffer that a capture
+ * used is kept, still counted against the workspace limit, until
+ * plv_destroy, so replaying the older graph stays valid. */
 plv_status plv_backward(plv_handle *h, void *stream, const void *x,
                         plv_dtype dtype, int batch, int N, int T, int64_t ldx,
                         const void *C, const float *g_plv, const float *g_iplv,

@@ -383,6 +383,11 @@ class Handle:
         P = self.plv_trial_operands(V, E, N, ldv, 0, L, "rms")
         return self.plv_gram(P, L, N, E, C=C, out=out)
 
+    def set_gram_raster(self, width: int = 0):
+        """Tile order of the tensor-core Gram (plv_set_gram_raster): super-
+        columns of ``width`` 128-row blocks; 0 restores the default."""
+        _lib.check(self.lib.plv_set_gram_raster(self.h, int(width)), self.h)
+
     def plv_sync_status(self) -> int:
         v = ctypes.c_int(0)
         _lib.check(self.lib.plv_sync_status(self.h, _stream(self.device),

@@ -47,6 +47,7 @@ SIGNATURES = {
     "plv_destroy": (_i, [_vp]),
     "plv_last_error": (ctypes.c_char_p, [_vp]),
     "plv_get_precision": (_i, [_vp]),
+    "plv_set_gram_raster": (_i, [_vp, _i]),
     "plv_phasor_ld": (_i64, [_i]),
     "plv_phasor_bytes": (_sz, [_vp, _i, _i, _i]),
     "plv_prepare": (_i, [_vp, _i]),

@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "plv.h"
 
@@ -120,8 +121,12 @@ struct GroupConfig {
     }
 };
 
+// Default raster width of the single-problem Gram's tile order (k_gram_tc.cu).
+constexpr int kDefaultRaster = 16;
+
 struct Handle {
     int device = 0;
+    int gram_raster = kDefaultRaster;  // tile raster width of single-problem Grams
     plv_precision prec = PLV_PREC_FP32;
     size_t workspace_limit = 0;
     size_t workspace_used = 0;
@@ -132,6 +137,10 @@ struct Handle {
     int *status = nullptr;  // device status word
     void *ws = nullptr;     // scratch for the backward pass (grows on demand)
     size_t ws_bytes = 0;
+    // a stream capture used ws, so a graph may still hold its address: on
+    // growth it is kept (retired) until plv_destroy rather than freed
+    bool ws_in_graph = false;
+    std::vector<void *> ws_retired;
     std::map<int, ConvPlan> conv;      // by T (lengths that are not handled directly)
     std::map<int, float2 *> conv_tw;   // twiddle tables by M
     std::map<int, float *> conv_S;     // kernel spectra by T
@@ -278,6 +287,7 @@ struct TcProblem {
     int kb_stride, nw, kb0, hop_kb;
     float invT;
     double invT_d;
+    int raster;  // tile raster width in row blocks (single-problem launches)
     GramOut out;
 };
 TcProblem make_tc_problem(const void *P, int batch, int N, int T, GramOut out);

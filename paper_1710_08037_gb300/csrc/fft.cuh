@@ -435,14 +435,30 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
     float *const s_pow = reinterpret_cast<float *>(tab + C::TAB);
     fill_twiddles<L, 1, NP>(tab, tw);  // ordered before use by the loop's first barriers
 
+    // Pass 0's inputs come from registers loaded one pair ahead: the loads of
+    // the next pair are issued after the fused middle pass, so their latency
+    // hides behind the inverse passes and the finish.
+    constexpr int R0 = radix_of(L, 0), B0 = kPow2EPT / R0;
+    float2 xin[B0][R0];
+    auto load_inputs = [&](int64_t bb) {
+        const int64_t p = bb * C::SEQ + sq;
+        const auto r = task.rows(2 * p, 2 * p < rows, 2 * p + 1, 2 * p + 1 < rows);
+#pragma unroll
+        for (int q = 0; q < B0; ++q)
+#pragma unroll
+            for (int k = 0; k < R0; ++k) xin[q][k] = task.load(r, lt + q * C::Q + k * (T / R0));
+    };
+    if (blockIdx.x < nbatch) load_inputs(blockIdx.x);
+
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
         const int64_t pair = b * C::SEQ + sq;
         const int64_t r0 = 2 * pair, r1 = 2 * pair + 1;
         const bool v0 = r0 < rows, v1 = r1 < rows;
         if constexpr (HasPrefetch<Task>::value) {
-            // the inputs of this CTA's next pair, one pair's work ahead
-            if (lt == 0 && b + gridDim.x < nbatch) {
-                const int64_t nr0 = 2 * (pair + (int64_t)gridDim.x * C::SEQ);
+            // L2 prefetch of the inputs two of this CTA's pairs ahead (the
+            // register loads take the next one)
+            if (lt == 0 && b + 2 * (int64_t)gridDim.x < nbatch) {
+                const int64_t nr0 = 2 * (pair + 2 * (int64_t)gridDim.x * C::SEQ);
                 task.prefetch(nr0, nr0 < rows, nr0 + 1, nr0 + 1 < rows);
             }
         }
@@ -452,21 +468,15 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
         const auto rs = task.rows(r0, v0, r1, v1);
         // forward pass 0 from the rows, summing |c|^2
         {
-            constexpr int R = radix_of(L, 0), B = kPow2EPT / R;
-            float2 a[B][R];
             float pw = 0.f;
 #pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const int j = lt + q * C::Q;
+            for (int q = 0; q < B0; ++q) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float2 c = task.load(rs, j + r * (T / R));
-                    a[q][r] = c;
-                    pw = fmaf(c.x, c.x, fmaf(c.y, c.y, pw));
-                }
-                Dft<R>::run(a[q]);
+                for (int k = 0; k < R0; ++k)
+                    pw = fmaf(xin[q][k].x, xin[q][k].x, fmaf(xin[q][k].y, xin[q][k].y, pw));
+                Dft<R0>::run(xin[q]);
             }
-            pass_store<L, 0>(buf[1], lt, a);
+            pass_store<L, 0>(buf[1], lt, xin);
             __syncthreads();
             // sum of |c|^2 over the sequence (its lanes are an aligned group
             // of Q threads, or whole warps when Q >= 32)
@@ -497,6 +507,8 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
             pass_smem<L, NP - 1, true>(buf[(NP - 1) & 1], buf[FB], tab, lt);
             pass_smem<L, 0>(buf[FB], buf[FB ^ 1], tab, lt);
         }
+        // the next pair's inputs, in flight during the inverse passes
+        if (b + gridDim.x < nbatch) load_inputs(b + gridDim.x);
         // inverse passes 1 .. NP-1: inverse pass 0 left its output in buf[O],
         // and pass p reads pbuf[p & 1]
         constexpr int O = C::FUSED ? FB : FB ^ 1;

@@ -231,15 +231,13 @@ __device__ __forceinline__ void tile_of(int t, int &I, int &J) {
 // round-robin, so G consecutive items (G = the grid) run at about the same
 // time and stream their row panels through L2 together; an order whose G
 // consecutive tiles touch few distinct row blocks re-reads fewer panels from
-// DRAM.  Tiles go by super-columns of kRasterW block columns; in each, the
-// off-diagonal super-blocks (kRasterW rows x wj columns, column-major), then
-// the diagonal super-block's triangle (column-major).  With nrb <= kRasterW
-// this is the plain column-major triangle.  (A lockstep model of N = 8192,
-// 152 CTAs: 431 panel reads per epoch against 639 for the column-major
-// triangle.)
-constexpr int kRasterW = 16;
-__device__ __forceinline__ void tile_raster(int t, int nrb, int &I, int &J) {
-    constexpr int W = kRasterW;
+// DRAM.  Tiles go by super-columns of W block columns; in each, the
+// off-diagonal super-blocks (W rows x wj columns, column-major), then the
+// diagonal super-block's triangle (column-major).  With nrb <= W this is the
+// plain column-major triangle.  (A lockstep model of N = 8192, 152 CTAs:
+// 431 panel reads per epoch at W = 16 against 639 for the column-major
+// triangle.)  The order changes which CTA computes a tile, never its value.
+__device__ __forceinline__ void tile_raster(int t, int nrb, int W, int &I, int &J) {
     int SJ = 0, wj = nrb < W ? nrb : W;
     for (;;) {
         const int cnt = SJ * W * wj + wj * (wj + 1) / 2;  // tiles of super-column SJ
@@ -291,7 +289,7 @@ __device__ __forceinline__ const TcProblem &item_of(const TcArgs &a, int t, int 
         return a.probs[it.x];
     }
     e = t / a.single.tpe;
-    tile_raster(t - e * a.single.tpe, a.single.nrb, I, J);
+    tile_raster(t - e * a.single.tpe, a.single.nrb, a.single.raster, I, J);
     return a.single;
 }
 
@@ -650,6 +648,7 @@ TcProblem make_tc_problem(const void *P, int batch, int N, int T, GramOut out) {
     p.hop_kb = 0;
     p.invT = 1.0f / (float)T;
     p.invT_d = 1.0 / (double)T;
+    p.raster = kDefaultRaster;
     p.out = out;
     return p;
 }
@@ -687,6 +686,7 @@ cudaError_t launch_gram_tc_windows(const Handle *h, cudaStream_t s, const void *
                                    int N, int T, int t0, int W, int hop, int nw, GramOut out) {
     TcArgs a;
     a.single = make_tc_window_problem(P, batch, N, T, t0, W, hop, nw, out);
+    a.single.raster = h->gram_raster;
     a.probs = nullptr;
     a.items = nullptr;
     const int64_t total = (int64_t)a.single.tpe * a.single.batch;
@@ -722,6 +722,7 @@ cudaError_t launch_gram_tc(const Handle *h, cudaStream_t s, const void *P, int b
                            int N, int T, GramOut out) {
     TcArgs a;
     a.single = make_tc_problem(P, batch, N, T, out);
+    a.single.raster = h->gram_raster;
     a.probs = nullptr;
     a.items = nullptr;
     const int64_t total = (int64_t)a.single.tpe * batch;

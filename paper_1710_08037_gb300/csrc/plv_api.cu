@@ -48,24 +48,43 @@ static int log2_exact(int T) {
 }
 
 // Grow the handle's scratch to at least `bytes`.  Growing allocates, which
-// is refused while `s` is capturing a graph.
+// is refused while `s` is capturing a graph.  A scratch buffer that a capture
+// used may be referenced by a graph the caller still replays, so growth keeps
+// it (retired, still counted in the workspace) until plv_destroy; a buffer no
+// capture used is freed.
 static plv_status ensure_workspace(Handle &h, cudaStream_t s, size_t bytes) {
-    if (h.ws_bytes >= bytes) return PLV_OK;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    const bool capturing =
+        cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+    if (h.ws_bytes >= bytes) {
+        if (capturing) h.ws_in_graph = true;
+        return PLV_OK;
+    }
+    if (capturing)
         return fail(PLV_ERR_INVALID,
                     "scratch must grow to %zu bytes while the stream is capturing; "
                     "make one call of the same size outside the capture first", bytes);
-    const size_t others = h.workspace_used - h.ws_bytes;
+    const bool keep = h.ws && h.ws_in_graph;
+    const size_t others = h.workspace_used - (keep ? 0 : h.ws_bytes);
     if (h.workspace_limit && others + bytes > h.workspace_limit)
         return fail(PLV_ERR_ALLOC, "scratch of %zu bytes exceeds the workspace limit %zu",
                     bytes, h.workspace_limit);
     if (h.ws) {
-        cudaError_t e = cudaFree(h.ws);  // synchronises with work still using it
+        if (keep) {
+            h.ws_retired.push_back(h.ws);
+        } else {
+            cudaError_t e = cudaFree(h.ws);  // synchronises with work still using it
+            if (e != cudaSuccess) {
+                h.ws = nullptr;
+                h.workspace_used = others;
+                h.ws_bytes = 0;
+                return check_cuda(e, "cudaFree(scratch)");
+            }
+        }
         h.ws = nullptr;
-        h.workspace_used = others;
         h.ws_bytes = 0;
-        if (e != cudaSuccess) return check_cuda(e, "cudaFree(scratch)");
+        h.ws_in_graph = false;
+        h.workspace_used = others;
     }
     cudaError_t e = cudaMalloc(&h.ws, bytes);
     if (e != cudaSuccess) {
@@ -154,6 +173,7 @@ plv_status plv_destroy(plv_handle *hp) {
         if (h.twiddles) cudaFree(h.twiddles);
         if (h.status) cudaFree(h.status);
         if (h.ws) cudaFree(h.ws);
+        for (void *p : h.ws_retired) cudaFree(p);
         free_conv_plans(h);
     }
     delete hp;
@@ -164,6 +184,13 @@ const char *plv_last_error(const plv_handle *) { return g_err.c_str(); }
 
 plv_precision plv_get_precision(const plv_handle *hp) {
     return hp ? hp->h.prec : PLV_PREC_FP32;
+}
+
+plv_status plv_set_gram_raster(plv_handle *hp, int width) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_set_gram_raster: NULL handle");
+    if (width < 0) return fail(PLV_ERR_INVALID, "plv_set_gram_raster: width %d < 0", width);
+    hp->h.gram_raster = width == 0 ? kDefaultRaster : width;
+    return PLV_OK;
 }
 
 int64_t plv_phasor_ld(int T) { return T > 0 ? padded_len(T) : 0; }

@@ -165,3 +165,42 @@ def test_tensor_core_contraction_equals_fp32(h32, N, T):
     err = float((got - ref).abs().max() / ref.abs().max())
     assert rel < 2e-5 and err < 1e-4, (rel, err)
     hs.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_graph_keeps_its_scratch_after_growth(prec):
+    """A CUDA graph captured with plv_backward keeps the scratch it was
+    captured with: a later, larger eager call grows the handle's scratch,
+    and replaying the older graph still gives the eager gradient bit for
+    bit (the buffer it used is kept until the handle is destroyed)."""
+    import paper_1710_08037_gb300 as plv
+    h = plv.Handle(precision=prec)
+    rng = np.random.default_rng(21)
+    B, N, T = 2, 96, 256
+    x = synth.bandlimited(B, N, T, seed=31, device="cuda")
+    C = h.plv_gram(h.plv_analytic(x), B, N, T, plv=False, iplv=False, ciplv=False,
+                   C=True)["C"]
+    g3 = torch.tensor(rng.standard_normal((B, N, N)), device="cuda", dtype=torch.float32)
+    want = h.plv_backward(x, C, None, None, g3)  # sizes the scratch outside capture
+    grad = torch.empty_like(want)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            h.plv_backward(x, C, None, None, g3, grad_x=grad)
+    # a larger problem grows the scratch (eagerly)
+    B2, N2, T2 = 3, 300, 1024
+    x2 = synth.bandlimited(B2, N2, T2, seed=32, device="cuda")
+    C2 = h.plv_gram(h.plv_analytic(x2), B2, N2, T2, plv=False, iplv=False, ciplv=False,
+                    C=True)["C"]
+    g32 = torch.tensor(rng.standard_normal((B2, N2, N2)), device="cuda", dtype=torch.float32)
+    h.plv_backward(x2, C2, None, None, g32)
+    grad.zero_()
+    with torch.cuda.stream(s):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(grad, want)
+    assert h.plv_sync_status() == 0
+    del graph
+    h.close()

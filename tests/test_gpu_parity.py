@@ -325,3 +325,26 @@ def test_full_size_split_workload_sampled(prec):
                        n_cols=32)
     print(prec, "full-size worst errors", w)
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+def test_gram_raster_changes_no_bits(prec):
+    """plv_set_gram_raster reorders which CTA computes a tile, never its
+    value: outputs are identical for raster widths 1, 3, 16 and the plain
+    column-major triangle (width >= row blocks), with ragged N."""
+    import paper_1710_08037_gb300 as plv
+    h = plv.Handle(precision=prec)
+    x = synth.bandlimited(2, 1100, 512, seed=5, device="cuda")  # 9 row blocks
+    P = h.plv_analytic(x)
+    ref = None
+    for w in (0, 1, 3, 16, 9, 100):
+        h.set_gram_raster(w)
+        res = h.plv_gram(P, 2, 1100, 512, C=True)
+        if ref is None:
+            ref = res
+            continue
+        for k in ("plv", "iplv", "ciplv", "C"):
+            assert torch.equal(res[k], ref[k]), (w, k)
+    import ctypes
+    assert h.lib.plv_set_gram_raster(h.h, -1) != 0
+    h.close()
