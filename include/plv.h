@@ -104,6 +104,50 @@ plv_precision plv_get_precision(const plv_handle *h);
  * accept and ignore it.  PLV_ERR_INVALID for a NULL handle or width < 0. */
 plv_status plv_set_gram_raster(plv_handle *h, int width);
 
+/* Failure detection (no counterpart in the paper).  Every wait of the
+ * tensor-core Gram's pipeline (a stage of operands landing, an accumulator
+ * chunk being drained) is bounded: after `ns` nanoseconds of %globaltimer
+ * the CTA records PLV_ERR_TIMEOUT in the handle's device status word (read
+ * by plv_sync_status), stops issuing, lets the copies and MMAs it issued
+ * finish (each within its own fixed 0.1 s bound), frees its tensor memory
+ * and returns; outputs of that launch are then incomplete.  The bound
+ * applies to later plv_gram, plv_gram_windows, plv_gram_grouped and split-
+ * precision plv_backward calls on this handle.  ns = 0 restores the default
+ * of 4 s; a short bound (microseconds) exists for tests of this path.
+ * PLV_ERR_INVALID for a NULL handle. */
+plv_status plv_set_wait_limit(plv_handle *h, uint64_t ns);
+
+/* Host-side fault injection for tests of the error paths (no counterpart in
+ * the paper).  Process-wide; one fault is armed at a time, and it disarms
+ * itself when it fires.  Nothing here makes a GPU fault, trap or hang.
+ *   PLV_FAULT_ALLOC  the countdown-th next device allocation made by the
+ *                    library (handle tables, plans, scratch, group plans)
+ *                    fails as if cudaMalloc had: the call returns
+ *                    PLV_ERR_ALLOC and frees what it had allocated;
+ *   PLV_FAULT_LAUNCH the countdown-th next kernel launch made by an entry
+ *                    point is not made and is reported as a failed launch
+ *                    (PLV_ERR_CUDA);
+ *   PLV_FAULT_STALL  the next tensor-core Gram launch withholds the first
+ *                    operand copy of every CTA, so each CTA's bounded
+ *                    pipeline wait (plv_set_wait_limit) runs out: the call
+ *                    itself returns PLV_OK and the launch ends with
+ *                    PLV_ERR_TIMEOUT in the device status word;
+ *   PLV_FAULT_NONE   disarms.
+ * countdown >= 1 (1: the next event).  The environment variable PLV_FAULT,
+ * read when the library is loaded, arms the same faults: "alloc[:n]",
+ * "launch[:n]" or "timeout" (the stall).  PLV_ERR_INVALID for an unknown
+ * kind or countdown < 1. */
+enum {
+    PLV_FAULT_NONE = 0,
+    PLV_FAULT_ALLOC = 1,
+    PLV_FAULT_LAUNCH = 2,
+    PLV_FAULT_STALL = 3
+};
+plv_status plv_debug_fault(int kind, int countdown);
+/* The armed fault: its kind (PLV_FAULT_NONE when disarmed) and, if
+ * countdown is not NULL, the events left until it fires. */
+int plv_debug_fault_armed(int *countdown);
+
 /* Row length (in elements) of the phasor operand layout for T samples: T
  * rounded up to a multiple of 32; the padding samples are zero. */
 int64_t plv_phasor_ld(int T);

@@ -388,6 +388,11 @@ class Handle:
         columns of ``width`` 128-row blocks; 0 restores the default."""
         _lib.check(self.lib.plv_set_gram_raster(self.h, int(width)), self.h)
 
+    def set_wait_limit(self, ns: int = 0):
+        """Bound of the tensor-core Gram's pipeline waits in nanoseconds
+        (plv_set_wait_limit); 0 restores the default of 4 s."""
+        _lib.check(self.lib.plv_set_wait_limit(self.h, int(ns)), self.h)
+
     def plv_sync_status(self) -> int:
         v = ctypes.c_int(0)
         _lib.check(self.lib.plv_sync_status(self.h, _stream(self.device),

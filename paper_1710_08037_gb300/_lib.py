@@ -31,6 +31,10 @@ PLV_OUT_CIPLV = 4
 PLV_OUT_C = 8
 PLV_TRIAL_ASIS = 0
 PLV_TRIAL_RMS = 1
+PLV_FAULT_NONE = 0
+PLV_FAULT_ALLOC = 1
+PLV_FAULT_LAUNCH = 2
+PLV_FAULT_STALL = 3
 
 STATUS_NAMES = {0: "PLV_OK", 1: "PLV_ERR_INVALID", 2: "PLV_ERR_ALLOC",
                 3: "PLV_ERR_CUDA", 4: "PLV_ERR_UNSUPPORTED",
@@ -48,6 +52,9 @@ SIGNATURES = {
     "plv_last_error": (ctypes.c_char_p, [_vp]),
     "plv_get_precision": (_i, [_vp]),
     "plv_set_gram_raster": (_i, [_vp, _i]),
+    "plv_set_wait_limit": (_i, [_vp, ctypes.c_uint64]),
+    "plv_debug_fault": (_i, [_i, _i]),
+    "plv_debug_fault_armed": (_i, [ctypes.POINTER(_i)]),
     "plv_phasor_ld": (_i64, [_i]),
     "plv_phasor_bytes": (_sz, [_vp, _i, _i, _i]),
     "plv_prepare": (_i, [_vp, _i]),

@@ -123,10 +123,14 @@ struct GroupConfig {
 
 // Default raster width of the single-problem Gram's tile order (k_gram_tc.cu).
 constexpr int kDefaultRaster = 16;
+// Default bound of every wait of the tensor-core Gram's pipeline (4 s).  The
+// clean-up waits of an aborting CTA keep their own fixed bound (0.1 s).
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;
 
 struct Handle {
     int device = 0;
     int gram_raster = kDefaultRaster;  // tile raster width of single-problem Grams
+    uint64_t wait_ns = kDefaultWaitNs;  // pipeline wait bound of the tensor-core Gram
     plv_precision prec = PLV_PREC_FP32;
     size_t workspace_limit = 0;
     size_t workspace_used = 0;
@@ -232,6 +236,28 @@ cudaError_t launch_analytic_group(const Handle *h, cudaStream_t s, plv_dtype dt,
 void set_error(const char *fmt, ...);
 plv_status fail(plv_status s, const char *fmt, ...);
 plv_status check_cuda(cudaError_t e, const char *what);
+// As check_cuda for a device allocation: PLV_ERR_ALLOC on failure.
+plv_status check_alloc(cudaError_t e, const char *what);
+
+// Host-side fault injection (plv_debug_fault, env PLV_FAULT): true when the
+// armed fault is of `kind` and this event is the one it counts down to
+// (which disarms it).
+bool take_fault(int kind);
+// cudaMalloc through the allocation fault hook.
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    void *v = nullptr;
+    const cudaError_t e = dev_malloc_raw(&v, bytes);
+    *p = (T *)v;
+    return e;
+}
+// check_cuda of a kernel launch through the launch fault hook: an injected
+// fault returns PLV_ERR_CUDA without evaluating (launching) `expr`.
+#define PLV_CHECK_LAUNCH(expr, what)                                                      \
+    (::plv::take_fault(PLV_FAULT_LAUNCH)                                                  \
+         ? ::plv::fail(PLV_ERR_CUDA, "%s: injected launch failure", (what))              \
+         : ::plv::check_cuda((expr), (what)))
 
 inline const float2 *twiddle_table(const Handle *h, int log2T) {
     return h->twiddles + ((1 << log2T) - (1 << kMinLog2T));

@@ -129,8 +129,8 @@ plv_status get_conv_plan(Handle &h, int T, const ConvPlan **out) {
             tw[m] = make_float2((float)cos(a), (float)-sin(a));
         }
         float2 *d = nullptr;
-        cudaError_t e = cudaMalloc(&d, sizeof(float2) * M);
-        if (e != cudaSuccess) return check_cuda(e, "any-length plan: twiddles");
+        cudaError_t e = dev_malloc(&d, sizeof(float2) * M);
+        if (e != cudaSuccess) return check_alloc(e, "any-length plan: twiddles");
         e = cudaMemcpy(d, tw.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             cudaFree(d);
@@ -140,8 +140,8 @@ plv_status get_conv_plan(Handle &h, int T, const ConvPlan **out) {
         h.workspace_used += sizeof(float2) * M;
     }
     float *dS = nullptr;
-    cudaError_t e = cudaMalloc(&dS, sizeof(float) * M);
-    if (e != cudaSuccess) return check_cuda(e, "any-length plan: spectrum");
+    cudaError_t e = dev_malloc(&dS, sizeof(float) * M);
+    if (e != cudaSuccess) return check_alloc(e, "any-length plan: spectrum");
     e = cudaMemcpy(dS, S.data(), sizeof(float) * M, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(dS);
@@ -269,8 +269,8 @@ plv_status get_band_plan(Handle &h, cudaStream_t s, int T, const float *masks, i
                 make_float2((float)(kc[p].real() / M), (float)(kc[p].imag() / M));
     }
     float2 *d = nullptr;
-    e = cudaMalloc(&d, sizeof(float2) * Kf.size());
-    if (e != cudaSuccess) return check_cuda(e, "plv_analytic_bands: band kernels");
+    e = dev_malloc(&d, sizeof(float2) * Kf.size());
+    if (e != cudaSuccess) return check_alloc(e, "plv_analytic_bands: band kernels");
     e = cudaMemcpy(d, Kf.data(), sizeof(float2) * Kf.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(d);

@@ -75,7 +75,6 @@ template <uint32_t FMT>
 struct Chunk {
     static constexpr int CH = FMT == 1u ? 16 : 4;
 };
-constexpr uint64_t kWaitNs = 4000000000ull;   // 4 s bound on any wait
 // per epilogue warp, a 32-row x 8-column FP32 staging tile for the row-wise
 // stores (after the operand ring and the barriers)
 constexpr int STAGE_TILE_FLOATS = 32 * 8;
@@ -124,14 +123,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // timeout (which raises the CTA's abort flag and the device status) or when
 // another role already aborted.
 __device__ __noinline__ bool wait_bar(uint32_t bar, uint32_t parity,
-                                      volatile int *abort_flag, int *status) {
+                                      volatile int *abort_flag, int *status,
+                                      uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 127) == 0) {
             if (*abort_flag) return false;
-            if (gtimer() - t0 > kWaitNs) {
+            if (gtimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicExch(status, (int)kDevTimeout);
                 return false;
@@ -268,6 +268,8 @@ struct TcArgs {
     TcGemm gemm;              // GEMM mode: the contraction
     int total_items;
     int *status;
+    uint64_t wait_ns;  // bound of every pipeline wait (the handle's wait limit)
+    int stall;         // injected fault: each CTA withholds its first operand copy
 };
 
 // GEMM mode: item t is (epoch, I, J) with J fastest, so CTAs working at the
@@ -342,6 +344,9 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             uint32_t phase = 0;
             uint32_t pending = 0;        // stages with a copy issued
             uint32_t pend_parity = 0;    // FULL parity each pending copy completes
+            // PLV_FAULT_STALL: the first stage is armed but its copies are
+            // never issued, so the MMA issuer's wait for it runs into the bound
+            bool withhold = args.stall != 0;
             for (int t = blockIdx.x; t < args.total_items && !*abort_flag; t += gridDim.x) {
                 int e, I, J, nkb;
                 bool diag;
@@ -364,15 +369,19 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     pj = pb.P + (size_t)(((int64_t)b * pb.nrb + J) * pb.kb_stride + k0) * SIDE_BYTES;
                 }
                 for (int kb = 0; kb < nkb; ++kb) {
-                    if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status)) break;
+                    if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status, args.wait_ns)) break;
                     const uint32_t sa = base + stage * STAGE_BYTES;
                     mbar_expect_tx(FULL(stage), diag ? SIDE_BYTES : 2 * SIDE_BYTES);
-                    bulk_g2s(sa, pa + (size_t)kb * SIDE_BYTES, SIDE_BYTES, FULL(stage));
-                    if (!diag)
-                        bulk_g2s(sa + SIDE_BYTES, pj + (size_t)kb * SIDE_BYTES, SIDE_BYTES,
-                                 FULL(stage));
-                    pending |= 1u << stage;
-                    pend_parity = (pend_parity & ~(1u << stage)) | (phase << stage);
+                    if (withhold) {
+                        withhold = false;
+                    } else {
+                        bulk_g2s(sa, pa + (size_t)kb * SIDE_BYTES, SIDE_BYTES, FULL(stage));
+                        if (!diag)
+                            bulk_g2s(sa + SIDE_BYTES, pj + (size_t)kb * SIDE_BYTES, SIDE_BYTES,
+                                     FULL(stage));
+                        pending |= 1u << stage;
+                        pend_parity = (pend_parity & ~(1u << stage)) | (phase << stage);
+                    }
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -413,7 +422,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     nkb = pb.nkb;
                 }
                 for (int kb0 = 0; ok && kb0 < nkb; kb0 += Chunk<FMT>::CH) {
-                    if (!wait_bar(TEMPTY(buf), buf_phase ^ 1u, abort_flag, args.status)) {
+                    if (!wait_bar(TEMPTY(buf), buf_phase ^ 1u, abort_flag, args.status, args.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -422,7 +431,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     const uint32_t d_im = d_re + TN;
                     const int kb1 = kb0 + Chunk<FMT>::CH < nkb ? kb0 + Chunk<FMT>::CH : nkb;
                     for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!wait_bar(FULL(stage), phase, abort_flag, args.status)) {
+                        if (!wait_bar(FULL(stage), phase, abort_flag, args.status, args.wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -501,7 +510,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     // all 32 columns in registers, and release the buffer after
                     // the stores.  Same values as the running-sum path (its sums
                     // start from +0 and add this one chunk).
-                    if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status)) {
+                    if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status, args.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -553,7 +562,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
 #pragma unroll
             for (int c = 0; c < 32; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
             for (int kb0 = 0; kb0 < nkb; kb0 += Chunk<FMT>::CH) {
-                if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status)) {
+                if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status, args.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -669,8 +678,9 @@ TcProblem make_tc_window_problem(const void *P, int batch, int N, int T, int t0,
 
 
 
-static cudaError_t launch_tc(const Handle *h, cudaStream_t s, const TcArgs &a) {
+static cudaError_t launch_tc(const Handle *h, cudaStream_t s, TcArgs a) {
     if (a.total_items <= 0) return cudaSuccess;
+    a.stall = take_fault(PLV_FAULT_STALL) ? 1 : 0;
     const int grid = a.total_items < h->num_sms ? a.total_items : h->num_sms;
     const bool fp16 = h->prec == PLV_PREC_FP16X3;
     auto kern = fp16 ? k_gram_tc<0u, false> : k_gram_tc<1u, false>;
@@ -693,6 +703,8 @@ cudaError_t launch_gram_tc_windows(const Handle *h, cudaStream_t s, const void *
     if (total > 0x7fffffff) return cudaErrorInvalidConfiguration;
     a.total_items = (int)total;
     a.status = h->status;
+    a.wait_ns = h->wait_ns;
+    a.stall = 0;
     return launch_tc(h, s, a);
 }
 
@@ -706,7 +718,10 @@ cudaError_t launch_gemm_tc(const Handle *h, cudaStream_t s, const TcGemm &g, int
     if (total > 0x7fffffff) return cudaErrorInvalidConfiguration;
     a.total_items = (int)total;
     a.status = h->status;
+    a.wait_ns = h->wait_ns;
+    a.stall = 0;
     if (a.total_items <= 0) return cudaSuccess;
+    a.stall = take_fault(PLV_FAULT_STALL) ? 1 : 0;
     const int grid = a.total_items < h->num_sms ? a.total_items : h->num_sms;
     // the BF16 split: gradients can exceed the FP16 range
     auto kern = k_gram_tc<1u, true>;
@@ -729,6 +744,8 @@ cudaError_t launch_gram_tc(const Handle *h, cudaStream_t s, const void *P, int b
     if (total > 0x7fffffff) return cudaErrorInvalidConfiguration;
     a.total_items = (int)total;
     a.status = h->status;
+    a.wait_ns = h->wait_ns;
+    a.stall = 0;
     return launch_tc(h, s, a);
 }
 
@@ -754,6 +771,8 @@ cudaError_t launch_gram_tc_group(const Handle *h, cudaStream_t s, const TcProble
     a.items = items;
     a.total_items = nitems;
     a.status = h->status;
+    a.wait_ns = h->wait_ns;
+    a.stall = 0;
     return launch_tc(h, s, a);
 }
 

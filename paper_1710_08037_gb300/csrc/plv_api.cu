@@ -4,7 +4,11 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <stdlib.h>
+#include <string.h>
+
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -38,6 +42,55 @@ plv_status fail(plv_status s, const char *fmt, ...) {
 plv_status check_cuda(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return PLV_OK;
     return fail(PLV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---- host-side fault injection ---------------------------------------------
+static std::atomic<int> g_fault_kind{PLV_FAULT_NONE};
+static std::atomic<int> g_fault_left{0};
+
+bool take_fault(int kind) {
+    if (g_fault_kind.load() != kind) return false;
+    if (g_fault_left.fetch_sub(1) != 1) return false;
+    g_fault_kind.store(PLV_FAULT_NONE);
+    return true;
+}
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes) {
+    if (take_fault(PLV_FAULT_ALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+// PLV_FAULT = "alloc[:n]" | "launch[:n]" | "timeout", read at load time.
+static void arm_fault_from_env() {
+    const char *v = getenv("PLV_FAULT");
+    if (!v || !*v) return;
+    int kind = PLV_FAULT_NONE;
+    const char *rest = nullptr;
+    if (strncmp(v, "alloc", 5) == 0) { kind = PLV_FAULT_ALLOC; rest = v + 5; }
+    else if (strncmp(v, "launch", 6) == 0) { kind = PLV_FAULT_LAUNCH; rest = v + 6; }
+    else if (strcmp(v, "timeout") == 0) { kind = PLV_FAULT_STALL; rest = v + 7; }
+    else return;
+    int n = 1;
+    if (*rest == ':') {
+        char *end = nullptr;
+        const long k = strtol(rest + 1, &end, 10);
+        if (end == rest + 1 || *end != '\0' || k < 1 || k > 1000000) return;
+        n = (int)k;
+    } else if (*rest != '\0') {
+        return;
+    }
+    g_fault_left.store(n);
+    g_fault_kind.store(kind);
+}
+static const int g_fault_env_read = (arm_fault_from_env(), 0);
+
+plv_status check_alloc(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return PLV_OK;
+    cudaGetLastError();  // an allocation failure is not sticky
+    return fail(PLV_ERR_ALLOC, "%s: %s", what, cudaGetErrorString(e));
 }
 
 static int log2_exact(int T) {
@@ -86,7 +139,7 @@ static plv_status ensure_workspace(Handle &h, cudaStream_t s, size_t bytes) {
         h.ws_in_graph = false;
         h.workspace_used = others;
     }
-    cudaError_t e = cudaMalloc(&h.ws, bytes);
+    cudaError_t e = dev_malloc(&h.ws, bytes);
     if (e != cudaSuccess) {
         h.ws = nullptr;
         cudaGetLastError();
@@ -145,12 +198,12 @@ plv_status plv_create(plv_handle **out, int device, plv_precision prec,
         st = fail(PLV_ERR_ALLOC, "plv_create: workspace limit %zu below %zu bytes",
                   workspace_limit, need);
     if (st == PLV_OK)
-        st = check_cuda(cudaMalloc(&h.twiddles, ntw * sizeof(float2)), "cudaMalloc(twiddles)");
+        st = check_alloc(dev_malloc(&h.twiddles, ntw * sizeof(float2)), "cudaMalloc(twiddles)");
     if (st == PLV_OK)
         st = check_cuda(cudaMemcpy(h.twiddles, tw.data(), ntw * sizeof(float2),
                                    cudaMemcpyHostToDevice), "cudaMemcpy(twiddles)");
     if (st == PLV_OK)
-        st = check_cuda(cudaMalloc(&h.status, 256), "cudaMalloc(status)");
+        st = check_alloc(dev_malloc(&h.status, 256), "cudaMalloc(status)");
     if (st == PLV_OK)
         st = check_cuda(cudaMemset(h.status, 0, 256), "cudaMemset(status)");
     if (st != PLV_OK) {
@@ -191,6 +244,34 @@ plv_status plv_set_gram_raster(plv_handle *hp, int width) {
     if (width < 0) return fail(PLV_ERR_INVALID, "plv_set_gram_raster: width %d < 0", width);
     hp->h.gram_raster = width == 0 ? kDefaultRaster : width;
     return PLV_OK;
+}
+
+plv_status plv_set_wait_limit(plv_handle *hp, uint64_t ns) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_set_wait_limit: NULL handle");
+    hp->h.wait_ns = ns == 0 ? kDefaultWaitNs : ns;
+    return PLV_OK;
+}
+
+plv_status plv_debug_fault(int kind, int countdown) {
+    (void)g_fault_env_read;
+    if (kind == PLV_FAULT_NONE) {
+        g_fault_kind.store(PLV_FAULT_NONE);
+        g_fault_left.store(0);
+        return PLV_OK;
+    }
+    if (kind != PLV_FAULT_ALLOC && kind != PLV_FAULT_LAUNCH && kind != PLV_FAULT_STALL)
+        return fail(PLV_ERR_INVALID, "plv_debug_fault: unknown kind %d", kind);
+    if (countdown < 1) return fail(PLV_ERR_INVALID, "plv_debug_fault: countdown %d < 1", countdown);
+    g_fault_kind.store(PLV_FAULT_NONE);
+    g_fault_left.store(countdown);
+    g_fault_kind.store(kind);
+    return PLV_OK;
+}
+
+int plv_debug_fault_armed(int *countdown) {
+    const int k = g_fault_kind.load();
+    if (countdown) *countdown = k == PLV_FAULT_NONE ? 0 : g_fault_left.load();
+    return k;
 }
 
 int64_t plv_phasor_ld(int T) { return T > 0 ? padded_len(T) : 0; }
@@ -236,12 +317,12 @@ plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
         return fail(PLV_ERR_INVALID, "plv_analytic: P is not 16-byte aligned");
     PLV_GUARD(&hp->h);
     if (hp->h.prec != PLV_PREC_FP32) {
-        plv_status st = check_cuda(launch_zero_pad_rows((cudaStream_t)stream, P, batch, N, T),
+        plv_status st = PLV_CHECK_LAUNCH(launch_zero_pad_rows((cudaStream_t)stream, P, batch, N, T),
                                    "plv_analytic: pad rows");
         if (st != PLV_OK) return st;
     }
     if (direct)
-        return check_cuda(launch_analytic_pow2(&hp->h, (cudaStream_t)stream, x, dtype,
+        return PLV_CHECK_LAUNCH(launch_analytic_pow2(&hp->h, (cudaStream_t)stream, x, dtype,
                                                (int64_t)batch * N, N, L, ldx, P),
                           "plv_analytic launch");
     const ConvPlan *plan = nullptr;
@@ -258,7 +339,7 @@ plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
         plv_status st = get_conv_plan(hp->h, T, &plan);
         if (st != PLV_OK) return st;
     }
-    return check_cuda(launch_analytic_conv(&hp->h, (cudaStream_t)stream, x, dtype,
+    return PLV_CHECK_LAUNCH(launch_analytic_conv(&hp->h, (cudaStream_t)stream, x, dtype,
                                            (int64_t)batch * N, N, T, ldx, P, *plan),
                       "plv_analytic launch");
 }
@@ -296,13 +377,13 @@ plv_status plv_analytic_bands(plv_handle *hp, void *stream, const void *x, plv_d
     }
     if (hp->h.prec != PLV_PREC_FP32)
         for (int b = 0; b < nbands; ++b) {
-            plv_status st = check_cuda(
+            plv_status st = PLV_CHECK_LAUNCH(
                 launch_zero_pad_rows(s, (uint8_t *)P + (size_t)b * band_bytes, batch, N, T),
                 "plv_analytic_bands: pad rows");
             if (st != PLV_OK) return st;
         }
     if (direct)
-        return check_cuda(launch_analytic_bands(&hp->h, s, x, dtype, (int64_t)batch * N, N, L,
+        return PLV_CHECK_LAUNCH(launch_analytic_bands(&hp->h, s, x, dtype, (int64_t)batch * N, N, L,
                                                 ldx, masks, nbands, P, (int64_t)band_bytes),
                           "plv_analytic_bands launch");
     // any other length: the band kernels' spectra are built on the host from
@@ -317,7 +398,7 @@ plv_status plv_analytic_bands(plv_handle *hp, void *stream, const void *x, plv_d
     st = ensure_workspace(h, s, sizeof(float2) * (size_t)conv_grid(h.num_sms, plan->M) *
                                     (size_t)plan->M);
     if (st != PLV_OK) return st;
-    return check_cuda(launch_analytic_bands_conv(&h, s, x, dtype, (int64_t)batch * N, N, T, ldx,
+    return PLV_CHECK_LAUNCH(launch_analytic_bands_conv(&h, s, x, dtype, (int64_t)batch * N, N, T, ldx,
                                                  *plan, K, nbands, P, (int64_t)band_bytes,
                                                  (float2 *)h.ws),
                       "plv_analytic_bands launch");
@@ -338,11 +419,11 @@ plv_status plv_normalize(plv_handle *hp, void *stream, const void *z,
         return fail(PLV_ERR_INVALID, "plv_normalize: misaligned pointer");
     PLV_GUARD(&hp->h);
     if (hp->h.prec != PLV_PREC_FP32) {
-        plv_status st = check_cuda(launch_zero_pad_rows((cudaStream_t)stream, P, batch, N, T),
+        plv_status st = PLV_CHECK_LAUNCH(launch_zero_pad_rows((cudaStream_t)stream, P, batch, N, T),
                                    "plv_normalize: pad rows");
         if (st != PLV_OK) return st;
     }
-    return check_cuda(launch_normalize(&hp->h, (cudaStream_t)stream, z, dtype,
+    return PLV_CHECK_LAUNCH(launch_normalize(&hp->h, (cudaStream_t)stream, z, dtype,
                                        (int64_t)batch * N, N, T, ldz, P),
                       "plv_normalize launch");
 }
@@ -380,9 +461,9 @@ plv_status plv_gram(plv_handle *hp, void *stream, const void *P, int batch,
         if (st != PLV_OK) return st;
     }
     if (hp->h.prec == PLV_PREC_FP32)
-        return check_cuda(launch_gram_fp32(&hp->h, s, (const float *)P, batch, N, T, o),
+        return PLV_CHECK_LAUNCH(launch_gram_fp32(&hp->h, s, (const float *)P, batch, N, T, o),
                           "plv_gram launch");
-    return check_cuda(launch_gram_tc(&hp->h, s, P, batch, N, T, o), "plv_gram launch");
+    return PLV_CHECK_LAUNCH(launch_gram_tc(&hp->h, s, P, batch, N, T, o), "plv_gram launch");
 }
 
 plv_status plv_gram_windows(plv_handle *hp, void *stream, const void *P, int batch, int N,
@@ -419,10 +500,10 @@ plv_status plv_gram_windows(plv_handle *hp, void *stream, const void *P, int bat
         if (st != PLV_OK) return st;
     }
     if (hp->h.prec == PLV_PREC_FP32)
-        return check_cuda(launch_gram_fp32_windows(&hp->h, s, (const float *)P, batch, N, T, t0,
+        return PLV_CHECK_LAUNCH(launch_gram_fp32_windows(&hp->h, s, (const float *)P, batch, N, T, t0,
                                                    W, hop, nw, o),
                           "plv_gram_windows launch");
-    return check_cuda(launch_gram_tc_windows(&hp->h, s, P, batch, N, T, t0, W, hop, nw, o),
+    return PLV_CHECK_LAUNCH(launch_gram_tc_windows(&hp->h, s, P, batch, N, T, t0, W, hop, nw, o),
                       "plv_gram_windows launch");
 }
 
@@ -478,10 +559,10 @@ plv_status plan_k1(Handle &h, const plv_problem *probs, int nprob, plv_group *g)
     std::vector<int2> items;
     K1Group kg{};
     k1_layout(descs, g->cfg.k1_class, items, kg);
-    plv_status st = check_cuda(cudaMalloc(&g->k1_descs, sizeof(K1Desc) * descs.size()),
+    plv_status st = check_alloc(dev_malloc(&g->k1_descs, sizeof(K1Desc) * descs.size()),
                                "plv_group_create: analytic descriptors");
     if (st == PLV_OK)
-        st = check_cuda(cudaMalloc(&g->k1_items, sizeof(int2) * items.size()),
+        st = check_alloc(dev_malloc(&g->k1_items, sizeof(int2) * items.size()),
                         "plv_group_create: analytic items");
     if (st == PLV_OK)
         st = check_cuda(cudaMemcpy(g->k1_descs, descs.data(), sizeof(K1Desc) * descs.size(),
@@ -497,7 +578,7 @@ plv_status plan_k1(Handle &h, const plv_problem *probs, int nprob, plv_group *g)
         for (int p = 0; p < nprob && st == PLV_OK; ++p) {
             const plv_problem &q = probs[p];
             if (!q.x || q.batch == 0 || q.N == 0) continue;
-            st = check_cuda(launch_zero_pad_rows(0, q.P, q.batch, q.N, q.T),
+            st = PLV_CHECK_LAUNCH(launch_zero_pad_rows(0, q.P, q.batch, q.N, q.T),
                             "plv_group_create: padding rows");
         }
         if (st == PLV_OK)
@@ -590,10 +671,10 @@ plv_status plv_group_create(plv_handle *hp, const plv_problem *probs, int nprob,
     g->nitems = (int)items.size();
     if (h.prec != PLV_PREC_FP32 && g->nprob > 0) {
         DeviceGuard guard(h.device);
-        plv_status st = check_cuda(cudaMalloc(&g->probs, sizeof(TcProblem) * dp.size()),
+        plv_status st = check_alloc(dev_malloc(&g->probs, sizeof(TcProblem) * dp.size()),
                                    "plv_group_create: descriptors");
         if (st == PLV_OK)
-            st = check_cuda(cudaMalloc(&g->items, sizeof(int4) * items.size()),
+            st = check_alloc(dev_malloc(&g->items, sizeof(int4) * items.size()),
                             "plv_group_create: tile list");
         if (st == PLV_OK)
             st = check_cuda(cudaMemcpy(g->probs, dp.data(), sizeof(TcProblem) * dp.size(),
@@ -628,11 +709,11 @@ plv_status plv_gram_grouped(plv_handle *hp, void *stream, const plv_group *g) {
     }
     if (g->nitems == 0) return PLV_OK;
     if (g->any_diag) {
-        plv_status st = check_cuda(launch_zero_group_diag(s, g->probs, g->nprob),
+        plv_status st = PLV_CHECK_LAUNCH(launch_zero_group_diag(s, g->probs, g->nprob),
                                    "plv_gram_grouped: clear diag");
         if (st != PLV_OK) return st;
     }
-    return check_cuda(launch_gram_tc_group(&hp->h, s, g->probs, g->items, g->nitems),
+    return PLV_CHECK_LAUNCH(launch_gram_tc_group(&hp->h, s, g->probs, g->items, g->nitems),
                       "plv_gram_grouped launch");
 }
 
@@ -643,7 +724,7 @@ plv_status plv_analytic_grouped(plv_handle *hp, void *stream, const plv_group *g
                     "plv_analytic_grouped: plan made for another device or precision");
     if (!g->has_k1) return fail(PLV_ERR_INVALID, "plv_analytic_grouped: the plan has no input");
     PLV_GUARD(&hp->h);
-    return check_cuda(launch_analytic_group(&hp->h, (cudaStream_t)stream, g->k1_dtype, g->k1),
+    return PLV_CHECK_LAUNCH(launch_analytic_group(&hp->h, (cudaStream_t)stream, g->k1_dtype, g->k1),
                       "plv_analytic_grouped launch");
 }
 
@@ -678,7 +759,7 @@ plv_status plv_trial_operands(plv_handle *hp, void *stream, const float *V, int 
     if (((uintptr_t)V % 4) != 0 || ((uintptr_t)P % 16) != 0)
         return fail(PLV_ERR_INVALID, "plv_trial_operands: misaligned pointer");
     PLV_GUARD(&hp->h);
-    return check_cuda(launch_trial_operands(&hp->h, (cudaStream_t)stream, V, E, N, ldv, l0, L,
+    return PLV_CHECK_LAUNCH(launch_trial_operands(&hp->h, (cudaStream_t)stream, V, E, N, ldv, l0, L,
                                             mode == PLV_TRIAL_RMS, P),
                       "plv_trial_operands launch");
 }
@@ -697,7 +778,7 @@ plv_status plv_dft_bins(plv_handle *hp, void *stream, const void *x, plv_dtype d
     if (((uintptr_t)x % (dtype == PLV_F32 ? 4 : 8)) != 0 || ((uintptr_t)X % 4) != 0)
         return fail(PLV_ERR_INVALID, "plv_dft_bins: misaligned pointer");
     PLV_GUARD(&hp->h);
-    return check_cuda(launch_dft_bins((cudaStream_t)stream, x, dtype, rows, T, ldx, f0, F, X, ldX),
+    return PLV_CHECK_LAUNCH(launch_dft_bins((cudaStream_t)stream, x, dtype, rows, T, ldx, f0, F, X, ldX),
                       "plv_dft_bins launch");
 }
 
@@ -709,7 +790,7 @@ plv_status plv_metrics(plv_handle *hp, void *stream, const void *C, int batch,
     if (!C) return fail(PLV_ERR_INVALID, "plv_metrics: C is NULL");
     if (((uintptr_t)C % 8) != 0) return fail(PLV_ERR_INVALID, "plv_metrics: C misaligned");
     PLV_GUARD(&hp->h);
-    return check_cuda(launch_metrics((cudaStream_t)stream, (const float2 *)C, batch, N,
+    return PLV_CHECK_LAUNCH(launch_metrics((cudaStream_t)stream, (const float2 *)C, batch, N,
                                      plv, iplv, ciplv),
                       "plv_metrics launch");
 }
@@ -768,10 +849,10 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
     char *w = (char *)h.ws;
     float *P = (float *)w, *rinv = (float *)(w + bP), *Gm = (float *)(w + bP + bR),
           *S = (float *)(w + bP + bR + bG);
-    st = check_cuda(launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv, T, plan),
+    st = PLV_CHECK_LAUNCH(launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv, T, plan),
                     "plv_backward: recompute");
     if (st != PLV_OK) return st;
-    return check_cuda(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,
+    return PLV_CHECK_LAUNCH(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,
                                       g_ciplv, P, rinv, tc ? nullptr : S, Gm, grad_x, plan,
                                       tc ? (void *)S : nullptr),
                       "plv_backward launch");

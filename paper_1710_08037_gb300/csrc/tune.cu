@@ -141,7 +141,7 @@ plv_status time_median(cudaStream_t s, int reps, F fn, float *ms) {
 template <class T>
 plv_status upload(const std::vector<T> &v, T **out, cudaStream_t s) {
     T *d = nullptr;
-    plv_status st = check_cuda(cudaMalloc(&d, sizeof(T) * std::max<size_t>(v.size(), 1)),
+    plv_status st = check_alloc(dev_malloc(&d, sizeof(T) * std::max<size_t>(v.size(), 1)),
                                "plv_group_tune: work list");
     if (st != PLV_OK) return st;
     st = check_cuda(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s),

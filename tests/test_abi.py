@@ -117,9 +117,10 @@ def test_every_entry_point_validates_before_touching_a_device(lib):
     without one, an invalid size) and zero arguments, fails with
     PLV_ERR_INVALID from its host-side checks; the destroy calls accept
     NULL.  No CUDA call is made, so this runs without a GPU."""
-    ok_on_null = {"plv_destroy", "plv_group_destroy"}
+    # plv_debug_fault(PLV_FAULT_NONE, 0) disarms: valid with all zeros
+    ok_on_null = {"plv_destroy", "plv_group_destroy", "plv_debug_fault"}
     not_status = {"plv_last_error", "plv_get_precision", "plv_phasor_ld",
-                  "plv_phasor_bytes"}
+                  "plv_phasor_bytes", "plv_debug_fault_armed"}
     for name, (res, args) in _lib.SIGNATURES.items():
         if name in not_status:
             continue
@@ -171,3 +172,41 @@ def test_no_cpu_path_without_a_gpu():
                           "import sys, paper_1710_08037_gb300; print('oracle' in sys.modules)"],
                          cwd=ROOT, capture_output=True, text=True, check=True)
     assert out.stdout.strip() == "False"
+
+
+def test_fault_injection_arms_and_validates_on_the_host(lib):
+    """plv_debug_fault arms one host-side fault (allocation, launch, or the
+    tensor-core Gram's withheld copy) with a countdown, rejects unknown kinds
+    and countdowns below 1, and disarms with PLV_FAULT_NONE; no CUDA call."""
+    f = lib.plv_debug_fault
+    f.restype, f.argtypes = ctypes.c_int, [ctypes.c_int, ctypes.c_int]
+    g = lib.plv_debug_fault_armed
+    g.restype, g.argtypes = ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]
+    n = ctypes.c_int(-1)
+    assert f(_lib.PLV_FAULT_ALLOC, 3) == _lib.PLV_OK
+    assert g(ctypes.byref(n)) == _lib.PLV_FAULT_ALLOC and n.value == 3
+    assert f(_lib.PLV_FAULT_LAUNCH, 0) == _lib.PLV_ERR_INVALID
+    assert f(99, 1) == _lib.PLV_ERR_INVALID
+    assert g(None) == _lib.PLV_FAULT_ALLOC  # a rejected call leaves it armed
+    assert f(_lib.PLV_FAULT_STALL, 1) == _lib.PLV_OK
+    assert g(ctypes.byref(n)) == _lib.PLV_FAULT_STALL and n.value == 1
+    assert f(_lib.PLV_FAULT_NONE, 0) == _lib.PLV_OK
+    assert g(ctypes.byref(n)) == _lib.PLV_FAULT_NONE and n.value == 0
+
+
+@pytest.mark.parametrize("env,kind,count", [("alloc", 1, 1), ("alloc:4", 1, 4),
+                                            ("launch:2", 2, 2), ("timeout", 3, 1),
+                                            ("launch:0", 0, 0), ("bogus", 0, 0),
+                                            ("alloc:x", 0, 0)])
+def test_fault_injection_from_the_environment(env, kind, count):
+    """PLV_FAULT, read when the library loads, arms the same faults; a
+    malformed value arms nothing (checked in a fresh process)."""
+    import subprocess
+    import sys
+    code = ("import ctypes, sys; from paper_1710_08037_gb300 import build; "
+            "lib = ctypes.CDLL(build.build()); n = ctypes.c_int(-1); "
+            "lib.plv_debug_fault_armed.argtypes = [ctypes.POINTER(ctypes.c_int)]; "
+            "k = lib.plv_debug_fault_armed(ctypes.byref(n)); print(k, n.value)")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                         env=dict(os.environ, PLV_FAULT=env), check=True)
+    assert out.stdout.split() == [str(kind), str(count)]
