@@ -388,6 +388,14 @@ def run_ours(args):
           "unit": "GB/s", "bytes_per_launch": k1b}
     k1["frac"] = k1["achieved"] / k1["peak"]
 
+    # device memory high-water mark of the run (the analogue of the paper's
+    # RAM column): caller-owned tensors (torch) plus the handle's own
+    hcur, hpeak = h.memory_usage()
+    mem = {"torch_peak_bytes": int(torch.cuda.max_memory_allocated(dev)),
+           "library_peak_bytes": hpeak,
+           "note": "torch peak covers inputs, phasors, outputs and the end-to-end and FP32 "
+                   "legs' buffers; library peak is the handle's tables and plans"}
+
     cpu = None
     accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -417,6 +425,7 @@ def run_ours(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
             "device_status": device_status,
+            "device_memory": mem,
         }
         print(json.dumps(line), flush=True)
     h.close()

@@ -117,6 +117,13 @@ plv_status plv_set_gram_raster(plv_handle *h, int width);
  * PLV_ERR_INVALID for a NULL handle. */
 plv_status plv_set_wait_limit(plv_handle *h, uint64_t ns);
 
+/* Device memory the handle holds (twiddle tables, any-length and band
+ * plans, backward scratch including scratch kept for captured graphs): the
+ * bytes now and the most held so far, the high-water mark of the library's
+ * own allocations (caller-owned tensors are not included).  NULL outputs are
+ * skipped.  PLV_ERR_INVALID for a NULL handle. */
+plv_status plv_memory_usage(const plv_handle *h, size_t *current, size_t *peak);
+
 /* Host-side fault injection for tests of the error paths (no counterpart in
  * the paper).  Process-wide; one fault is armed at a time, and it disarms
  * itself when it fires.  Nothing here makes a GPU fault, trap or hang.

@@ -388,6 +388,14 @@ class Handle:
         columns of ``width`` 128-row blocks; 0 restores the default."""
         _lib.check(self.lib.plv_set_gram_raster(self.h, int(width)), self.h)
 
+    def memory_usage(self):
+        """(current, peak) device bytes held by the handle itself
+        (plv_memory_usage)."""
+        cur, peak = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _lib.check(self.lib.plv_memory_usage(self.h, ctypes.byref(cur), ctypes.byref(peak)),
+                   self.h)
+        return int(cur.value), int(peak.value)
+
     def set_wait_limit(self, ns: int = 0):
         """Bound of the tensor-core Gram's pipeline waits in nanoseconds
         (plv_set_wait_limit); 0 restores the default of 4 s."""

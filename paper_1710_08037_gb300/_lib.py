@@ -53,6 +53,7 @@ SIGNATURES = {
     "plv_get_precision": (_i, [_vp]),
     "plv_set_gram_raster": (_i, [_vp, _i]),
     "plv_set_wait_limit": (_i, [_vp, ctypes.c_uint64]),
+    "plv_memory_usage": (_i, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "plv_debug_fault": (_i, [_i, _i]),
     "plv_debug_fault_armed": (_i, [ctypes.POINTER(_i)]),
     "plv_phasor_ld": (_i64, [_i]),

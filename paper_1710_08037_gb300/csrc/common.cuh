@@ -13,9 +13,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "plv.h"
 
 namespace plv {
+
+// NVTX range around one entry point (header-only NVTX 3: a no-op unless a
+// profiler attaches).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define PLV_RANGE(name) ::plv::NvtxRange plv_nvtx_range_(name)
 
 // Phasor operand rows are padded to a multiple of this many samples (the
 // Gram's K tile); the padding holds zeros.
@@ -133,7 +145,8 @@ struct Handle {
     uint64_t wait_ns = kDefaultWaitNs;  // pipeline wait bound of the tensor-core Gram
     plv_precision prec = PLV_PREC_FP32;
     size_t workspace_limit = 0;
-    size_t workspace_used = 0;
+    size_t workspace_used = 0;  // device bytes the handle holds now
+    size_t workspace_peak = 0;  // and at most so far (plv_memory_usage)
     int num_sms = 0;
     // twiddles exp(-2 pi i m / 2^L), m < 2^L, for L = kMinLog2T..kMaxLog2T,
     // table L starting at element (2^L - 2^kMinLog2T)
@@ -155,6 +168,11 @@ struct Handle {
     std::map<std::string, GroupConfig> tuned;
     std::mutex mu;
 };
+
+// Record a new value of h.workspace_used in the high-water mark.
+inline void note_usage(Handle &h) {
+    if (h.workspace_used > h.workspace_peak) h.workspace_peak = h.workspace_used;
+}
 
 // Per-kernel launch set-up done once per device (the shared-memory opt-in
 // and the occupancy query are not stream operations, and doing them once

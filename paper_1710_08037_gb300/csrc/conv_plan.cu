@@ -138,6 +138,7 @@ plv_status get_conv_plan(Handle &h, int T, const ConvPlan **out) {
         }
         h.conv_tw[M] = d;
         h.workspace_used += sizeof(float2) * M;
+        note_usage(h);
     }
     float *dS = nullptr;
     cudaError_t e = dev_malloc(&dS, sizeof(float) * M);
@@ -149,6 +150,7 @@ plv_status get_conv_plan(Handle &h, int T, const ConvPlan **out) {
     }
     h.conv_S[T] = dS;
     h.workspace_used += sizeof(float) * M;
+    note_usage(h);
     ConvPlan p;
     p.M = M;
     p.nstages = (int)radix.size();
@@ -278,6 +280,7 @@ plv_status get_band_plan(Handle &h, cudaStream_t s, int T, const float *masks, i
     }
     h.band_K[key] = d;
     h.workspace_used += sizeof(float2) * Kf.size();
+    note_usage(h);
     *K = d;
     return PLV_OK;
 }

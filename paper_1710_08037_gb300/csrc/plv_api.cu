@@ -148,6 +148,7 @@ static plv_status ensure_workspace(Handle &h, cudaStream_t s, size_t bytes) {
     }
     h.ws_bytes = bytes;
     h.workspace_used = others + bytes;
+    note_usage(h);
     return PLV_OK;
 }
 
@@ -164,6 +165,7 @@ extern "C" {
 
 plv_status plv_create(plv_handle **out, int device, plv_precision prec,
                       size_t workspace_limit) {
+    PLV_RANGE("plv_create");
     if (!out) return fail(PLV_ERR_INVALID, "plv_create: handle pointer is NULL");
     *out = nullptr;
     if (prec != PLV_PREC_FP32 && prec != PLV_PREC_BF16X3 && prec != PLV_PREC_FP16X3)
@@ -213,11 +215,13 @@ plv_status plv_create(plv_handle **out, int device, plv_precision prec,
         return st;
     }
     h.workspace_used = need;
+    note_usage(h);
     *out = hp;
     return PLV_OK;
 }
 
 plv_status plv_destroy(plv_handle *hp) {
+    PLV_RANGE("plv_destroy");
     if (!hp) return PLV_OK;
     Handle &h = hp->h;
     {
@@ -249,6 +253,13 @@ plv_status plv_set_gram_raster(plv_handle *hp, int width) {
 plv_status plv_set_wait_limit(plv_handle *hp, uint64_t ns) {
     if (!hp) return fail(PLV_ERR_INVALID, "plv_set_wait_limit: NULL handle");
     hp->h.wait_ns = ns == 0 ? kDefaultWaitNs : ns;
+    return PLV_OK;
+}
+
+plv_status plv_memory_usage(const plv_handle *hp, size_t *current, size_t *peak) {
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_memory_usage: NULL handle");
+    if (current) *current = hp->h.workspace_used;
+    if (peak) *peak = hp->h.workspace_peak;
     return PLV_OK;
 }
 
@@ -284,6 +295,7 @@ size_t plv_phasor_bytes(const plv_handle *hp, int batch, int N, int T) {
 }
 
 plv_status plv_prepare(plv_handle *hp, int T) {
+    PLV_RANGE("plv_prepare");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_prepare: handle is NULL");
     if (T <= 0) return fail(PLV_ERR_INVALID, "plv_prepare: T = %d", T);
     const int L = log2_exact(T);
@@ -297,6 +309,7 @@ plv_status plv_prepare(plv_handle *hp, int T) {
 plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
                         plv_dtype dtype, int batch, int N, int T, int64_t ldx,
                         void *P) {
+    PLV_RANGE("plv_analytic");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_analytic: handle is NULL");
     if (batch < 0 || N < 0 || T <= 0)
         return fail(PLV_ERR_INVALID, "plv_analytic: bad sizes batch=%d N=%d T=%d", batch, N, T);
@@ -347,6 +360,7 @@ plv_status plv_analytic(plv_handle *hp, void *stream, const void *x,
 plv_status plv_analytic_bands(plv_handle *hp, void *stream, const void *x, plv_dtype dtype,
                               int batch, int N, int T, int64_t ldx, const float *masks,
                               int nbands, void *P) {
+    PLV_RANGE("plv_analytic_bands");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_analytic_bands: handle is NULL");
     if (batch < 0 || N < 0 || T <= 0 || nbands < 0)
         return fail(PLV_ERR_INVALID, "plv_analytic_bands: bad sizes batch=%d N=%d T=%d bands=%d",
@@ -407,6 +421,7 @@ plv_status plv_analytic_bands(plv_handle *hp, void *stream, const void *x, plv_d
 plv_status plv_normalize(plv_handle *hp, void *stream, const void *z,
                          plv_dtype dtype, int batch, int N, int T, int64_t ldz,
                          void *P) {
+    PLV_RANGE("plv_normalize");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_normalize: handle is NULL");
     if (batch < 0 || N < 0 || T <= 0)
         return fail(PLV_ERR_INVALID, "plv_normalize: bad sizes batch=%d N=%d T=%d", batch, N, T);
@@ -431,6 +446,7 @@ plv_status plv_normalize(plv_handle *hp, void *stream, const void *z,
 plv_status plv_gram(plv_handle *hp, void *stream, const void *P, int batch,
                     int N, int T, unsigned out_mask, float *plv, float *iplv,
                     float *ciplv, void *C, double *diag_dev) {
+    PLV_RANGE("plv_gram");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_gram: handle is NULL");
     if (batch < 0 || N < 0 || T <= 0)
         return fail(PLV_ERR_INVALID, "plv_gram: bad sizes batch=%d N=%d T=%d", batch, N, T);
@@ -469,6 +485,7 @@ plv_status plv_gram(plv_handle *hp, void *stream, const void *P, int batch,
 plv_status plv_gram_windows(plv_handle *hp, void *stream, const void *P, int batch, int N,
                             int T, int t0, int W, int hop, int nw, unsigned out_mask,
                             float *plv, float *iplv, float *ciplv, void *C, double *diag_dev) {
+    PLV_RANGE("plv_gram_windows");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_gram_windows: handle is NULL");
     if (batch < 0 || N < 0 || T <= 0 || nw < 0 || t0 < 0 || W < kTileK || hop < 0 ||
         t0 % kTileK || W % kTileK || hop % kTileK ||
@@ -599,6 +616,7 @@ extern "C" {
 
 plv_status plv_group_create(plv_handle *hp, const plv_problem *probs, int nprob,
                             unsigned out_mask, plv_group **out) {
+    PLV_RANGE("plv_group_create");
     if (!hp || !out) return fail(PLV_ERR_INVALID, "plv_group_create: NULL argument");
     *out = nullptr;
     if (nprob < 0 || (nprob > 0 && !probs))
@@ -694,6 +712,7 @@ plv_status plv_group_create(plv_handle *hp, const plv_problem *probs, int nprob,
 }
 
 plv_status plv_gram_grouped(plv_handle *hp, void *stream, const plv_group *g) {
+    PLV_RANGE("plv_gram_grouped");
     if (!hp || !g) return fail(PLV_ERR_INVALID, "plv_gram_grouped: NULL argument");
     if (g->device != hp->h.device || g->prec != hp->h.prec)
         return fail(PLV_ERR_INVALID, "plv_gram_grouped: plan made for another device or precision");
@@ -718,6 +737,7 @@ plv_status plv_gram_grouped(plv_handle *hp, void *stream, const plv_group *g) {
 }
 
 plv_status plv_analytic_grouped(plv_handle *hp, void *stream, const plv_group *g) {
+    PLV_RANGE("plv_analytic_grouped");
     if (!hp || !g) return fail(PLV_ERR_INVALID, "plv_analytic_grouped: NULL argument");
     if (g->device != hp->h.device || g->prec != hp->h.prec)
         return fail(PLV_ERR_INVALID,
@@ -729,6 +749,7 @@ plv_status plv_analytic_grouped(plv_handle *hp, void *stream, const plv_group *g
 }
 
 plv_status plv_group_destroy(plv_group *g) {
+    PLV_RANGE("plv_group_destroy");
     if (!g) return PLV_OK;
     {
         DeviceGuard guard(g->device);
@@ -747,6 +768,7 @@ plv_status plv_group_destroy(plv_group *g) {
 
 plv_status plv_trial_operands(plv_handle *hp, void *stream, const float *V, int E, int N,
                               int64_t ldv, int l0, int L, int mode, void *P) {
+    PLV_RANGE("plv_trial_operands");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_trial_operands: handle is NULL");
     if (E < 1 || N < 0 || L < 0 || l0 < 0 || ldv < 0 || (int64_t)l0 + L > ldv)
         return fail(PLV_ERR_INVALID, "plv_trial_operands: bad sizes E=%d N=%d ldv=%lld l0=%d L=%d",
@@ -766,6 +788,7 @@ plv_status plv_trial_operands(plv_handle *hp, void *stream, const float *V, int 
 
 plv_status plv_dft_bins(plv_handle *hp, void *stream, const void *x, plv_dtype dtype, int rows,
                         int T, int64_t ldx, int f0, int F, float *X, int64_t ldX) {
+    PLV_RANGE("plv_dft_bins");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_dft_bins: handle is NULL");
     if (dtype != PLV_F32 && dtype != PLV_F64)
         return fail(PLV_ERR_INVALID, "plv_dft_bins: unknown dtype %d", (int)dtype);
@@ -784,6 +807,7 @@ plv_status plv_dft_bins(plv_handle *hp, void *stream, const void *x, plv_dtype d
 
 plv_status plv_metrics(plv_handle *hp, void *stream, const void *C, int batch,
                        int N, float *plv, float *iplv, float *ciplv) {
+    PLV_RANGE("plv_metrics");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_metrics: handle is NULL");
     if (batch < 0 || N < 0) return fail(PLV_ERR_INVALID, "plv_metrics: bad sizes");
     if (batch == 0 || N == 0) return PLV_OK;
@@ -799,6 +823,7 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
                         int batch, int N, int T, int64_t ldx, const void *C,
                         const float *g_plv, const float *g_iplv, const float *g_ciplv,
                         float *grad_x) {
+    PLV_RANGE("plv_backward");
     if (!hp) return fail(PLV_ERR_INVALID, "plv_backward: handle is NULL");
     if (batch < 0 || N < 0 || T <= 0)
         return fail(PLV_ERR_INVALID, "plv_backward: bad sizes batch=%d N=%d T=%d", batch, N, T);
@@ -859,6 +884,7 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
 }
 
 plv_status plv_sync_status(plv_handle *hp, void *stream, int *device_status) {
+    PLV_RANGE("plv_sync_status");
     if (!hp || !device_status) return fail(PLV_ERR_INVALID, "plv_sync_status: NULL argument");
     PLV_GUARD(&hp->h);
     cudaStream_t s = (cudaStream_t)stream;

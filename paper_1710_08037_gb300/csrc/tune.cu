@@ -214,6 +214,7 @@ using namespace plv;
 
 extern "C" plv_status plv_group_tune(plv_handle *hp, void *stream, plv_group *g, int reps,
                                      plv_tune_result *res) {
+    PLV_RANGE("plv_group_tune");
     if (!hp || !g) return fail(PLV_ERR_INVALID, "plv_group_tune: NULL argument");
     Handle &h = hp->h;
     if (g->device != h.device || g->prec != h.prec)
@@ -412,6 +413,7 @@ extern "C" plv_status plv_group_tune(plv_handle *hp, void *stream, plv_group *g,
 extern "C" plv_status plv_group_configure(plv_handle *hp, void *stream, plv_group *g,
                                           int k1_widen, const int *k1_per_sm,
                                           int gram_schedule, int gram_tile_cost) {
+    PLV_RANGE("plv_group_configure");
     if (!hp || !g) return fail(PLV_ERR_INVALID, "plv_group_configure: NULL argument");
     Handle &h = hp->h;
     if (g->device != h.device || g->prec != h.prec)

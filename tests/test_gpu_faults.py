@@ -171,3 +171,24 @@ def test_short_bound_without_a_stall_changes_nothing(disarm):
     assert h.plv_sync_status() == 0
     h.close()
     assert np.isfinite(float(a["plv"].max()))
+
+
+def test_memory_high_water_mark(disarm):
+    """plv_memory_usage: the handle's own device bytes (tables, plans,
+    scratch) now and at most; a new plan and the backward scratch raise
+    both."""
+    import paper_1710_08037_gb300 as plv
+    h = plv.Handle(precision="fp32")
+    cur0, peak0 = h.memory_usage()
+    assert cur0 > 0 and peak0 == cur0
+    h.prepare(1000)
+    cur1, peak1 = h.memory_usage()
+    assert cur1 > cur0 and peak1 == cur1
+    x = synth.bandlimited(1, 40, 1000, seed=8, device="cuda")
+    C = h.plv_gram(h.plv_analytic(x), 1, 40, 1000, C=True)["C"]
+    g = torch.randn(1, 40, 40, device="cuda")
+    h.plv_backward(x, C, g)
+    cur2, peak2 = h.memory_usage()
+    ld = 1024
+    assert cur2 >= cur1 + 40 * ld * 20 and peak2 == cur2
+    h.close()
