@@ -124,6 +124,20 @@ plv_status plv_set_wait_limit(plv_handle *h, uint64_t ns);
  * skipped.  PLV_ERR_INVALID for a NULL handle. */
 plv_status plv_memory_usage(const plv_handle *h, size_t *current, size_t *peak);
 
+/* Bounds-checked builds (no counterpart in the paper).  The library built
+ * with PLV_CHECKED (libplv_checked.so) tests the bounds conditions of the
+ * index computations of the analytic-signal kernels (shared-memory
+ * positions, sample ranges of the stores) and of the tensor-core Gram
+ * (operand blocks copied, output rows and columns written): an access that
+ * fails its condition is skipped and the source line of the first failure
+ * is recorded on the device, never trapped.  plv_check_status synchronises
+ * `stream`, reads the first recorded line of the handle's device into
+ * *line (0: none) and clears it.  On the unchecked build it sets *line = 0.
+ * PLV_ERR_INVALID for a NULL argument. */
+plv_status plv_check_status(plv_handle *h, void *stream, int *line);
+/* 1 for the bounds-checked build, 0 otherwise. */
+int plv_build_checked(void);
+
 /* Host-side fault injection for tests of the error paths (no counterpart in
  * the paper).  Process-wide; one fault is armed at a time, and it disarms
  * itself when it fires.  Nothing here makes a GPU fault, trap or hang.
@@ -472,8 +486,12 @@ plv_status plv_dft_bins(plv_handle *h, void *stream, const void *x, plv_dtype dt
  * PLV_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits (plus the FFT twiddle tables, also static).
  *
- * Same arguments and results as plv_backward (minus the handle); it runs on
- * the CURRENT device.  A problem whose scratch (batch*N*ld*20 + batch*N*N*8
+ * Arguments as plv_backward (minus the handle); it runs on the CURRENT
+ * device, with the arithmetic of an FP32 handle's plv_backward (FP32, the
+ * contraction on the CUDA cores), whose result it equals bit for bit.  T
+ * must be a power of two from 32 to 8192 (other lengths, which plv_backward
+ * takes through its any-length plans, give PLV_ERR_UNSUPPORTED).  A problem
+ * whose scratch (batch*N*ld*20 + batch*N*N*8
  * bytes, each of the four parts rounded up to 256 bytes; ld = plv_phasor_ld(T))
  * exceeds the array is rejected with PLV_ERR_INVALID and a message naming
  * the sizes; nothing is launched.  For example batch = 4, N = 128, T = 4096
@@ -481,7 +499,10 @@ plv_status plv_dft_bins(plv_handle *h, void *stream, const void *x, plv_dtype dt
  *
  * The first call on each device sets that device up: it looks up the
  * array's device address and uploads the twiddle tables (synchronous
- * copies).  Make that first call outside any stream capture.
+ * copies).  Make that first call outside any stream capture.  The set-up
+ * is kept for the life of the process: after a reset of a device's context
+ * (cudaDeviceReset) the addresses it holds are stale, so do not call this
+ * entry point on that device again.
  *
  * All calls share the one array.  Each call writes every scratch element it
  * reads, so no clearing is needed between calls.  Calls whose work overlaps

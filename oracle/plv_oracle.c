@@ -24,7 +24,7 @@
  *   5. separately, for the equivalence check only, the reformulated
  *      definition (Eq. 5-7): c_ij = (1/T) sum_t z_i conj(z_j) / (|z_i||z_j|).
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent:
  *   - a sample with |z| = 0 has no phase; its unit phasor is taken as 0, so
  *     the sample contributes nothing to any pair (Eq. 4 divides by |z|).
  *   - where (1 - Re c)(1 + Re c) <= 0 (the diagonal, exact zero-lag copies),

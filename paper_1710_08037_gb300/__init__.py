@@ -53,24 +53,30 @@ def phasor_ld(T: int) -> int:
 class Handle:
     """Owns a ``plv_handle`` (device, Gram precision, workspace)."""
 
-    def __init__(self, precision="fp32", device=None, workspace_limit=0):
+    def __init__(self, precision="fp32", device=None, workspace_limit=0, checked=False):
+        """checked=True runs on the bounds-checked build of the library
+        (libplv_checked.so, PLV_CHECKED): see check_status()."""
         if not torch.cuda.is_available():
             raise PlvError(_lib.PLV_ERR_UNSUPPORTED,
                            "no CUDA device: this library has no CPU path")
-        self.lib = _lib.load()
+        self.lib = _lib.load(checked=checked)
+        self.checked = bool(checked)
         self.device = torch.device("cuda", torch.cuda.current_device()
                                    if device is None else int(device))
         self.precision = _PREC[precision]
         h = ctypes.c_void_p()
         _lib.check(self.lib.plv_create(ctypes.byref(h), self.device.index,
-                                       self.precision, int(workspace_limit)))
+                                       self.precision, int(workspace_limit)), None, self.lib)
         self.h = h
+        if checked:
+            _lib._checked_handles.add(h.value)
 
     def close(self):
         if getattr(self, "_h32", None) is not None:
             self._h32.close()
             self._h32 = None
         if getattr(self, "h", None):
+            _lib._checked_handles.discard(self.h.value)
             self.lib.plv_destroy(self.h)
             self.h = None
 
@@ -328,7 +334,7 @@ class Handle:
         if self.precision == PLV_PREC_FP32:
             return self
         if getattr(self, "_h32", None) is None:
-            self._h32 = Handle("fp32", device=self.device.index)
+            self._h32 = Handle("fp32", device=self.device.index, checked=self.checked)
         return self._h32
 
     def time_resolved(self, x, l0=0, L=None, C=False, out=None):
@@ -387,6 +393,16 @@ class Handle:
         """Tile order of the tensor-core Gram (plv_set_gram_raster): super-
         columns of ``width`` 128-row blocks; 0 restores the default."""
         _lib.check(self.lib.plv_set_gram_raster(self.h, int(width)), self.h)
+
+    def check_status(self) -> int:
+        """Checked builds: the source line of the first out-of-range access
+        the kernels caught (and skipped) on this handle's device since the
+        last call, 0 for none; always 0 on the unchecked build
+        (plv_check_status)."""
+        v = ctypes.c_int(0)
+        _lib.check(self.lib.plv_check_status(self.h, _stream(self.device), ctypes.byref(v)),
+                   self.h)
+        return int(v.value)
 
     def memory_usage(self):
         """(current, peak) device bytes held by the handle itself

@@ -54,6 +54,8 @@ SIGNATURES = {
     "plv_set_gram_raster": (_i, [_vp, _i]),
     "plv_set_wait_limit": (_i, [_vp, ctypes.c_uint64]),
     "plv_memory_usage": (_i, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "plv_check_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
+    "plv_build_checked": (_i, []),
     "plv_debug_fault": (_i, [_i, _i]),
     "plv_debug_fault_armed": (_i, [ctypes.POINTER(_i)]),
     "plv_phasor_ld": (_i64, [_i]),
@@ -83,7 +85,7 @@ SIGNATURES = {
 }
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
 class PlvError(RuntimeError):
@@ -92,18 +94,18 @@ class PlvError(RuntimeError):
         self.status = status
 
 
-def lib_path() -> str:
-    return _build.LIB
+def lib_path(checked: bool = False) -> str:
+    return _build.LIB_CHECKED if checked else _build.LIB
 
 
-def load(build_if_missing: bool = True):
-    """Load (building first if needed) libplv.so and declare signatures."""
-    global _lib
+def load(build_if_missing: bool = True, checked: bool = False):
+    """Load (building first if needed) libplv.so -- or, with checked=True,
+    the bounds-checked libplv_checked.so -- and declare signatures."""
     with _lock:
-        if _lib is None:
-            path = _build.LIB
-            if build_if_missing and not _build.up_to_date():
-                _build.build()
+        if checked not in _libs:
+            path = lib_path(checked)
+            if build_if_missing and not _build.up_to_date(checked):
+                _build.build(checked=checked)
             if not os.path.exists(path):
                 raise PlvError(PLV_ERR_UNSUPPORTED,
                                f"CUDA library not built: {path}")
@@ -112,13 +114,20 @@ def load(build_if_missing: bool = True):
                 f = getattr(lib, name)
                 f.restype = res
                 f.argtypes = args
-            _lib = lib
-    return _lib
+            _libs[checked] = lib
+    return _libs[checked]
 
 
-def check(status: int, handle=None):
+# handles created by the checked library (their error text lives there)
+_checked_handles = set()
+
+
+def check(status: int, handle=None, lib=None):
     if status != PLV_OK:
-        msg = load().plv_last_error(handle)
+        if lib is None:
+            hv = getattr(handle, "value", handle)
+            lib = load(checked=True) if hv in _checked_handles else load()
+        msg = lib.plv_last_error(handle)
         raise PlvError(status, msg.decode() if msg else "")
 
 

@@ -19,6 +19,14 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libplv.so")
+# the checked variant (-DPLV_CHECKED=1: bounds conditions of the kernels'
+# index computations tested at run time, failures recorded, not trapped)
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libplv_checked.so")
+
+
+def _paths(checked: bool):
+    return (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -45,13 +53,15 @@ VARIANTS = {
 }
 
 
-def _units():
+def _units(checked: bool = False):
     """(source, object, extra flags) of every compiler run."""
     out = []
+    bdir = _paths(checked)[0]
+    extra = ["-DPLV_CHECKED=1"] if checked else []
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         name = os.path.basename(src)[:-3]
         for suffix, flags in VARIANTS.get(os.path.basename(src), [("", [])]):
-            out.append((src, os.path.join(BUILD, name + suffix + ".o"), flags))
+            out.append((src, os.path.join(bdir, name + suffix + ".o"), flags + extra))
     return out
 
 
@@ -61,20 +71,23 @@ def _deps():
         os.path.join(ROOT, "include", "plv.h"), __file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = _paths(checked)[1]
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every .cu for sm_103a and link libplv.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile every .cu for sm_103a and link libplv.so (libplv_checked.so
+    with checked=True); returns its path."""
+    bdir, lib = _paths(checked)
+    if not force and up_to_date(checked):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
-    units = _units()
+    units = _units(checked)
 
     def compile_one(unit):
         src, obj, flags = unit
@@ -93,15 +106,16 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     order = sorted(units, key=lambda u: 0 if u[2] else 1)
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(compile_one, order))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [],
+                checked="--checked" in sys.argv))

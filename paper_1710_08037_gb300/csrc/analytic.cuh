@@ -133,6 +133,7 @@ __device__ __forceinline__ RowAddr<PREC> row_addr(int64_t r, int N, int64_t ld) 
 template <int PREC>
 __device__ __forceinline__ void store_phasor(void *P, const RowAddr<PREC> &ra, int64_t ld,
                                              int m, float2 p) {
+    if (!PLV_IN_BOUNDS(m >= 0 && m < ld)) return;
     if constexpr (PREC == PLV_PREC_FP32) {
         float *o = (float *)P + ra.base + m;
         o[0] = p.x;
@@ -212,6 +213,7 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
 template <int PREC>
 __device__ __forceinline__ void store_phasor8(void *P, const RowAddr<PREC> &ra, int64_t ld,
                                               int m0, const float2 (&p)[8]) {
+    if (!PLV_IN_BOUNDS(m0 >= 0 && (m0 & 7) == 0 && m0 + 8 <= ld)) return;
     if constexpr (PREC == PLV_PREC_FP32) {
         float4 *o = (float4 *)((float *)P + ra.base + m0);
         o[0] = make_float4(p[0].x, p[1].x, p[2].x, p[3].x);

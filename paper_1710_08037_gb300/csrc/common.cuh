@@ -29,6 +29,36 @@ struct NvtxRange {
 };
 #define PLV_RANGE(name) ::plv::NvtxRange plv_nvtx_range_(name)
 
+// Checked builds (-DPLV_CHECKED=1).  PLV_IN_BOUNDS(c) guards an access by the
+// bounds condition c of its index computation: true when c holds; when it
+// fails, the access is skipped (the macro is false) and the source line is
+// recorded in this translation unit's device word (the first failure wins),
+// which plv_check_status reads.  Unchecked builds compile the condition away.
+#ifndef PLV_CHECKED
+#define PLV_CHECKED 0
+#endif
+typedef int (*CheckReader)();  // reads and clears one unit's word (current device)
+int register_check_unit(CheckReader r);
+#if PLV_CHECKED
+// one word per translation unit: the library is linked without relocatable
+// device code, so every unit records into its own
+static __device__ int plv_check_line_;
+#define PLV_IN_BOUNDS(c) \
+    ((c) ? true : (atomicCAS(&plv_check_line_, 0, (int)__LINE__), false))
+static int plv_check_read_() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, plv_check_line_, sizeof(int)) != cudaSuccess) return 0;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(plv_check_line_, &z, sizeof(int));
+    }
+    return v;
+}
+static const int plv_check_registered_ = register_check_unit(&plv_check_read_);
+#else
+#define PLV_IN_BOUNDS(c) true
+#endif
+
 // Phasor operand rows are padded to a multiple of this many samples (the
 // Gram's K tile); the padding holds zeros.
 constexpr int kPadT = 32;

@@ -20,6 +20,7 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
 // iPLV = ciPLV = 0 there.
 __device__ __forceinline__ void emit(const GramOut &o, int64_t eNN, int N,
                                      int i, int j, float re, float im) {
+    if (!PLV_IN_BOUNDS(i >= 0 && j >= 0 && i < N && j < N)) return;
     const int64_t ij = eNN + (int64_t)i * N + j;
     const int64_t ji = eNN + (int64_t)j * N + i;
     float p, ip, cp;
@@ -136,6 +137,8 @@ __device__ __forceinline__ void store_block8(const GramOut &o, int m, int64_t eN
                                              const float *im, float invT, float *S, bool vec) {
     float *out = m == 0 ? o.plv : (m == 1 ? o.iplv : o.ciplv);
     if (!out) return;
+    // checked builds: the whole 32 x 8 block lies inside the N x N matrix
+    if (!PLV_IN_BOUNDS(i0 >= 0 && j0 >= 0 && i0 + 32 <= N && j0 + 8 <= N)) return;
     const float sgn = m == 2 ? -1.0f : 1.0f;  // ciPLV is antisymmetric
     float v[8];
 #pragma unroll

@@ -323,12 +323,16 @@ __device__ __forceinline__ void pass_load(const float2 *src, const float4 *tab, 
     for (int q = 0; q < B; ++q) {
         const int j = lt + q * Q;
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[q][r] = src[padi(j + r * (T / R))];
+        for (int r = 0; r < R; ++r) {
+            const int m = j + r * (T / R);
+            a[q][r] = PLV_IN_BOUNDS(m < T) ? src[padi(m)] : make_float2(0.f, 0.f);
+        }
         if constexpr (NS > 1) {
             const float4 *t = tab + tab_off(L, P) + (j & (NS - 1));
 #pragma unroll
             for (int s2 = 0; s2 < R / 2; ++s2) {
-                const float4 v = t[s2 * NS];
+                const float4 v = PLV_IN_BOUNDS((j & (NS - 1)) + s2 * NS < tab_len(L, P))
+                                     ? t[s2 * NS] : make_float4(0.f, 0.f, 0.f, 0.f);
                 if (s2 > 0) a[q][2 * s2] = cmul(a[q][2 * s2], make_float2(v.x, v.y));
                 a[q][2 * s2 + 1] = cmul(a[q][2 * s2 + 1], make_float2(v.z, v.w));
             }
@@ -348,7 +352,8 @@ __device__ __forceinline__ void pass_store(float2 *dst, int lt,
         const int k = j & (NS - 1);
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[padi(base + r * NS)] = a[q][r];
+        for (int r = 0; r < R; ++r)
+            if (PLV_IN_BOUNDS(base + r * NS < T)) dst[padi(base + r * NS)] = a[q][r];
     }
 }
 
@@ -446,7 +451,10 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
 #pragma unroll
         for (int q = 0; q < B0; ++q)
 #pragma unroll
-            for (int k = 0; k < R0; ++k) xin[q][k] = task.load(r, lt + q * C::Q + k * (T / R0));
+            for (int k = 0; k < R0; ++k) {
+                const int m = lt + q * C::Q + k * (T / R0);
+                xin[q][k] = PLV_IN_BOUNDS(m < T) ? task.load(r, m) : make_float2(0.f, 0.f);
+            }
     };
     if (blockIdx.x < nbatch) load_inputs(blockIdx.x);
 
@@ -529,14 +537,14 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
                     h0[k] = w.x;
                     h1[k] = -w.y;
                 }
-                task.finish8(rs, m0, h0, h1, floor2);
+                if (PLV_IN_BOUNDS(m0 + 8 <= T)) task.finish8(rs, m0, h0, h1, floor2);
             }
         } else {
 #pragma unroll 4
             for (int u = 0; u < kPow2EPT; ++u) {
                 const int m = lt + u * C::Q;
                 const float2 w = w_out[padi(m)];
-                task.finish(rs, m, w.x, -w.y, floor2);
+                if (PLV_IN_BOUNDS(m < T)) task.finish(rs, m, w.x, -w.y, floor2);
             }
         }
     }
@@ -685,6 +693,8 @@ __device__ __forceinline__ void conv_butterfly(float2 *s, int base, int sub, int
                                                const Task &task,
                                                const typename Task::Rows &rs, int T,
                                                int64_t ld, float *pw, float floor2) {
+    // every value of the butterfly lies inside the transform
+    if (!PLV_IN_BOUNDS(base >= 0 && base + (R - 1) * sub < plan.M)) return;
     float2 a[R];
     if constexpr (KIND == kDifFirst) {
 #pragma unroll
@@ -743,7 +753,7 @@ __device__ __forceinline__ void conv_butterfly(float2 *s, int base, int sub, int
         for (int q = 0; q < R; ++q) {
             float2 v = a[q];
             if (KIND == kDitSmem || KIND == kMidFused) v.y = -v.y;
-            s[padi(base + q * sub)] = v;
+            if (PLV_IN_BOUNDS(base + q * sub < plan.M)) s[padi(base + q * sub)] = v;
         }
     }
 }

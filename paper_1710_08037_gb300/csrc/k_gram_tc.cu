@@ -358,6 +358,12 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     nkb = g.nkb;
                     pa = g.A + (size_t)((int64_t)e * g.nrb_a + I) * nkb * SIDE_BYTES;
                     pj = g.B + (size_t)((int64_t)e * g.nrb_b + J) * nkb * SIDE_BYTES;
+                    // checked builds: operand blocks inside both operands
+                    if (!PLV_IN_BOUNDS(I >= 0 && I < g.nrb_a && J >= 0 && J < g.nrb_b &&
+                                       e >= 0 && (int64_t)e * g.tpe < args.total_items)) {
+                        pa = g.A;
+                        pj = g.B;
+                    }
                 } else {
                     const TcProblem &pb = item_of(args, t, e, I, J);
                     diag = I == J;
@@ -367,6 +373,12 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     const int64_t k0 = pb.kb0 + (int64_t)w * pb.hop_kb;
                     pa = pb.P + (size_t)(((int64_t)b * pb.nrb + I) * pb.kb_stride + k0) * SIDE_BYTES;
                     pj = pb.P + (size_t)(((int64_t)b * pb.nrb + J) * pb.kb_stride + k0) * SIDE_BYTES;
+                    // checked builds: the tile's blocks inside its epoch's operand
+                    if (!PLV_IN_BOUNDS(I >= 0 && I <= J && J < pb.nrb && e >= 0 && e < pb.batch &&
+                                       k0 >= 0 && k0 + nkb <= pb.kb_stride)) {
+                        pa = pb.P;
+                        pj = pb.P;
+                    }
                 }
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status, args.wait_ns)) break;
@@ -607,6 +619,10 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                 const TcProblem &pb = *pbp;
                 const int N = pb.N;
                 const int j0 = J * TN + cq * 32;
+                // checked builds: the output matrix and the tile exist
+                if (!PLV_IN_BOUNDS(e >= 0 && e < pb.batch && I >= 0 && I <= J &&
+                                   J * TN < N + TN - 1 && J < pb.nrb))
+                    continue;
                 // warp-uniform, per 32 x 32 block of the warp: blocks strictly
                 // above the diagonal (every block of an off-diagonal tile; those
                 // with q < cq of a diagonal tile) whose rows and columns are all

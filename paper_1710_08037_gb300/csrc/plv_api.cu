@@ -44,6 +44,16 @@ plv_status check_cuda(cudaError_t e, const char *what) {
     return fail(PLV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// ---- checked builds: the registry of per-unit recording words -------------
+static std::vector<CheckReader> &check_units() {
+    static std::vector<CheckReader> v;
+    return v;
+}
+int register_check_unit(CheckReader r) {
+    check_units().push_back(r);
+    return 0;
+}
+
 // ---- host-side fault injection ---------------------------------------------
 static std::atomic<int> g_fault_kind{PLV_FAULT_NONE};
 static std::atomic<int> g_fault_left{0};
@@ -255,6 +265,26 @@ plv_status plv_set_wait_limit(plv_handle *hp, uint64_t ns) {
     hp->h.wait_ns = ns == 0 ? kDefaultWaitNs : ns;
     return PLV_OK;
 }
+
+plv_status plv_check_status(plv_handle *hp, void *stream, int *line) {
+    if (!hp || !line) return fail(PLV_ERR_INVALID, "plv_check_status: NULL argument");
+    *line = 0;
+#if PLV_CHECKED
+    PLV_GUARD(&hp->h);
+    plv_status st = check_cuda(cudaStreamSynchronize((cudaStream_t)stream),
+                               "plv_check_status: sync");
+    if (st != PLV_OK) return st;
+    for (CheckReader r : check_units()) {
+        const int v = r();
+        if (v && !*line) *line = v;
+    }
+#else
+    (void)stream;
+#endif
+    return PLV_OK;
+}
+
+int plv_build_checked(void) { return PLV_CHECKED ? 1 : 0; }
 
 plv_status plv_memory_usage(const plv_handle *hp, size_t *current, size_t *peak) {
     if (!hp) return fail(PLV_ERR_INVALID, "plv_memory_usage: NULL handle");

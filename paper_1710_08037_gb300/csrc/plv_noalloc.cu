@@ -6,8 +6,8 @@
 // library holds until the process exits:
 //   g_scratch   PLV_NOALLOC_SCRATCH_BYTES of scratch (recomputed phasors,
 //               reciprocal amplitudes, S = G + G^H, Gamma);
-//   g_twiddles  the FFT twiddle tables for every supported length;
-//   g_status    the device status word of the bounded waits.
+//   g_twiddles  the FFT twiddle tables for every supported length.
+// (The FP32 backward has no bounded waits, so no status word is needed.)
 // Host code cannot use these names as device addresses: on each device the
 // first call (with that device current) looks the addresses up with
 // cudaGetSymbolAddress, checks the result, and uploads the twiddles.  Later
@@ -28,13 +28,11 @@ constexpr size_t kTwiddleCount = ((size_t)1 << (kMaxLog2T + 1)) - ((size_t)1 << 
 
 static __device__ __align__(256) unsigned char g_scratch[PLV_NOALLOC_SCRATCH_BYTES];
 static __device__ __align__(256) float2 g_twiddles[kTwiddleCount];
-static __device__ __align__(256) int g_status[64];
 
 struct DeviceState {
     bool ready = false;
     unsigned char *scratch = nullptr;
     float2 *twiddles = nullptr;
-    int *status = nullptr;
     int num_sms = 0;
 };
 
@@ -52,9 +50,6 @@ plv_status setup_current_device(int dev, DeviceState &st) {
     e = cudaGetSymbolAddress(&p, g_twiddles);
     if (e != cudaSuccess) return check_cuda(e, "plv_backward_noalloc: twiddle address");
     st.twiddles = (float2 *)p;
-    e = cudaGetSymbolAddress(&p, g_status);
-    if (e != cudaSuccess) return check_cuda(e, "plv_backward_noalloc: status address");
-    st.status = (int *)p;
     e = cudaDeviceGetAttribute(&st.num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return check_cuda(e, "plv_backward_noalloc: SM count");
     std::vector<float2> tw(kTwiddleCount);
@@ -143,7 +138,7 @@ extern "C" plv_status plv_backward_noalloc(void *stream, const void *x, plv_dtyp
     h.prec = PLV_PREC_FP32;
     h.num_sms = st->num_sms;
     h.twiddles = st->twiddles;
-    h.status = st->status;
+    h.status = nullptr;  // no kernel of the FP32 backward writes a status
 
     const int64_t ld = padded_len(T);
     const size_t rows = (size_t)batch * N;

@@ -120,7 +120,7 @@ def test_every_entry_point_validates_before_touching_a_device(lib):
     # plv_debug_fault(PLV_FAULT_NONE, 0) disarms: valid with all zeros
     ok_on_null = {"plv_destroy", "plv_group_destroy", "plv_debug_fault"}
     not_status = {"plv_last_error", "plv_get_precision", "plv_phasor_ld",
-                  "plv_phasor_bytes", "plv_debug_fault_armed"}
+                  "plv_phasor_bytes", "plv_debug_fault_armed", "plv_build_checked"}
     for name, (res, args) in _lib.SIGNATURES.items():
         if name in not_status:
             continue
@@ -210,3 +210,15 @@ def test_fault_injection_from_the_environment(env, kind, count):
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
                          env=dict(os.environ, PLV_FAULT=env), check=True)
     assert out.stdout.split() == [str(kind), str(count)]
+
+
+def test_checked_build_flag(lib):
+    """The regular library reports itself as unchecked; its check query
+    rejects a NULL handle before touching a device."""
+    lib.plv_build_checked.restype = ctypes.c_int
+    assert lib.plv_build_checked() == 0
+    f = lib.plv_check_status
+    f.restype, f.argtypes = ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_int)]
+    v = ctypes.c_int(-1)
+    assert f(None, None, ctypes.byref(v)) == _lib.PLV_ERR_INVALID

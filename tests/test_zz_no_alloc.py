@@ -12,7 +12,6 @@ import numpy as np
 import pytest
 import torch
 
-from tests.helpers import TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -42,10 +41,18 @@ def test_noalloc_backward_matches_allocating_backward():
                                       ctypes.c_void_p(out.data_ptr()))
         assert rc == _lib.PLV_OK, lib.plv_last_error(None)
         torch.cuda.synchronize()
-        scale = float(ref.abs().max())
-        err = float((out - ref).abs().max())
-        assert torch.isfinite(out).all()
-        assert err <= TOL["fp32"] * scale, (call, err, scale)
+        # the FP32 handle's backward runs the same kernels on the same values
+        assert torch.equal(out, ref), call
+        if call == 0:
+            # and it is the gradient: FP64 autograd through plain torch ops
+            from oracle import backward as obw
+            e = 1
+            want = obw.torch_grad(x[e].double().cpu().numpy(), g1[e].double().cpu().numpy(),
+                                  None, g3[e].double().cpu().numpy())
+            got = out[e].double().cpu().numpy()
+            rel2 = np.linalg.norm(got - want) / np.linalg.norm(want)
+            err = np.abs(got - want).max() / np.abs(want).max()
+            assert rel2 < 5e-4 and err < 2e-3, (rel2, err)
     h.close()
 
 
