@@ -214,9 +214,16 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16 (fmt 1) or FP16
 // (fmt 0), both K-major, M = 128, N = 128, optional negate-A.
-__host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, bool negA) {
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, bool negA, int n = TN) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((negA ? 1u : 0u) << 13) |
-           ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+// MMA width of a tile: its valid columns rounded up to 16 (the N step of an
+// M = 128 MMA), so a ragged last column block costs only the columns it has.
+// TMEM columns past it keep stale values, which no store reads.
+__device__ __forceinline__ int mma_width(int valid) {
+    return valid >= TN ? TN : ((valid + 15) & ~15);
 }
 
 __device__ __forceinline__ void tile_of(int t, int &I, int &J) {
@@ -411,8 +418,6 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t ID_POS = idesc_f16(FMT, false);
-            constexpr uint32_t ID_NEG = idesc_f16(FMT, true);
             int stage = 0;
             uint32_t phase = 0;
             int buf = 0;
@@ -422,17 +427,22 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             bool ok = true;
             for (int t = blockIdx.x; ok && t < args.total_items && !*abort_flag;
                  t += gridDim.x) {
-                int e, I, J, nkb;
+                int e, I, J, nkb, ncols;
                 bool diag;
                 if constexpr (GEMM) {
                     gemm_item(args.gemm, t, e, I, J);
                     diag = false;
                     nkb = args.gemm.nkb;
+                    ncols = (int)args.gemm.ld - J * TN;
                 } else {
                     const TcProblem &pb = item_of(args, t, e, I, J);
                     diag = I == J;
                     nkb = pb.nkb;
+                    ncols = pb.N - J * TN;
                 }
+                const int nw = mma_width(ncols);
+                const uint32_t ID_POS = idesc_f16(FMT, false, nw);
+                const uint32_t ID_NEG = idesc_f16(FMT, true, nw);
                 for (int kb0 = 0; ok && kb0 < nkb; kb0 += Chunk<FMT>::CH) {
                     if (!wait_bar(TEMPTY(buf), buf_phase ^ 1u, abort_flag, args.status, args.wait_ns)) {
                         ok = false;
