@@ -345,6 +345,41 @@ struct PrepTask {
         if (rs.x0) one(rs.x0, rs.p0, rs.q0, m, h0, floor2);
         if (rs.x1) one(rs.x1, rs.p1, rs.q1, m, h1, floor2);
     }
+    // eight consecutive samples m0 .. m0+7 (m0 % 8 == 0, m0 + 8 <= ld):
+    // vector loads of x and 16-byte stores of both planes and of 1/|z|
+    static constexpr bool kFinish8 = true;
+    __device__ void row8(const Tin *xr, float *pr, float *qr, int m0, const float (&h)[8],
+                         float floor2) const {
+        if (!PLV_IN_BOUNDS(m0 >= 0 && (m0 & 7) == 0 && m0 + 8 <= ld)) return;
+        float xv[8];
+        load_x8(xr + m0, xv);
+        float re[8], im[8], ri[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float2 p = unit_phasor_inv(xv[k], h[k], floor2, ri[k]);
+            re[k] = p.x;
+            im[k] = p.y;
+        }
+        float4 *o = (float4 *)(pr + m0), *oi = (float4 *)(pr + ld + m0), *oq = (float4 *)(qr + m0);
+        o[0] = make_float4(re[0], re[1], re[2], re[3]);
+        o[1] = make_float4(re[4], re[5], re[6], re[7]);
+        oi[0] = make_float4(im[0], im[1], im[2], im[3]);
+        oi[1] = make_float4(im[4], im[5], im[6], im[7]);
+        oq[0] = make_float4(ri[0], ri[1], ri[2], ri[3]);
+        oq[1] = make_float4(ri[4], ri[5], ri[6], ri[7]);
+    }
+    __device__ void finish8(const Rows &rs, int m0, const float (&h0)[8], const float (&h1)[8],
+                            float floor2) const {
+        if (rs.x0) row8(rs.x0, rs.p0, rs.q0, m0, h0, floor2);
+        if (rs.x1) row8(rs.x1, rs.p1, rs.q1, m0, h1, floor2);
+    }
+    static constexpr bool kPrefetch = true;
+    __device__ void prefetch(int64_t r0, bool v0, int64_t r1, bool v1) const {
+        const uint32_t bytes = (uint32_t)(ld * sizeof(Tin)) <= (uint32_t)(ldx * sizeof(Tin))
+                                   ? (uint32_t)(ld * sizeof(Tin)) : (uint32_t)(ldx * sizeof(Tin));
+        if (v0) prefetch_l2(x + r0 * ldx, bytes);
+        if (v1) prefetch_l2(x + r1 * ldx, bytes);
+    }
     __device__ void pad(const Rows &rs, int m) const {
         if (rs.x0) { rs.p0[m] = 0.f; rs.p0[ld + m] = 0.f; rs.q0[m] = 0.f; }
         if (rs.x1) { rs.p1[m] = 0.f; rs.p1[ld + m] = 0.f; rs.q1[m] = 0.f; }

@@ -397,6 +397,18 @@ __device__ __forceinline__ void passes(float2 *const (&buf)[2], const float4 *ta
     }
 }
 
+// Optional task trait: the task's load() computes on the values it reads
+// (kLoadComputes), so loading a pair early would stall the thread on those
+// loads in the middle of the previous pair's passes; such tasks load at pass 0.
+template <class Task, class = void>
+struct LoadsEarly {
+    static constexpr bool value = true;
+};
+template <class Task>
+struct LoadsEarly<Task, decltype((void)Task::kLoadComputes)> {
+    static constexpr bool value = !Task::kLoadComputes;
+};
+
 // Optional task hook: issue an L2 prefetch of the inputs of rows (r0, r1).
 template <class Task, class = void>
 struct HasPrefetch {
@@ -442,7 +454,9 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
 
     // Pass 0's inputs come from registers loaded one pair ahead: the loads of
     // the next pair are issued after the fused middle pass, so their latency
-    // hides behind the inverse passes and the finish.
+    // hides behind the inverse passes and the finish (tasks whose load()
+    // computes on what it reads load at pass 0 instead).
+    constexpr bool EARLY = LoadsEarly<Task>::value;
     constexpr int R0 = radix_of(L, 0), B0 = kPow2EPT / R0;
     float2 xin[B0][R0];
     auto load_inputs = [&](int64_t bb) {
@@ -456,7 +470,7 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
                 xin[q][k] = PLV_IN_BOUNDS(m < T) ? task.load(r, m) : make_float2(0.f, 0.f);
             }
     };
-    if (blockIdx.x < nbatch) load_inputs(blockIdx.x);
+    if (EARLY && blockIdx.x < nbatch) load_inputs(blockIdx.x);
 
     for (int64_t b = blockIdx.x; b < nbatch; b += gridDim.x) {
         const int64_t pair = b * C::SEQ + sq;
@@ -474,6 +488,7 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
         __syncthreads();
         if (lt == 0) s_pow[sq] = 0.f;  // ordered before the adds by pass 0's barrier
         const auto rs = task.rows(r0, v0, r1, v1);
+        if (!EARLY) load_inputs(b);
         // forward pass 0 from the rows, summing |c|^2
         {
             float pw = 0.f;
@@ -516,7 +531,7 @@ k_hilbert_pairs(const Task task, const float2 *__restrict__ tw, int64_t rows,
             pass_smem<L, 0>(buf[FB], buf[FB ^ 1], tab, lt);
         }
         // the next pair's inputs, in flight during the inverse passes
-        if (b + gridDim.x < nbatch) load_inputs(b + gridDim.x);
+        if (EARLY && b + gridDim.x < nbatch) load_inputs(b + gridDim.x);
         // inverse passes 1 .. NP-1: inverse pass 0 left its output in buf[O],
         // and pass p reads pbuf[p & 1]
         constexpr int O = C::FUSED ? FB : FB ^ 1;

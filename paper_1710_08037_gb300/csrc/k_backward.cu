@@ -105,30 +105,49 @@ __device__ __forceinline__ void store_split_bf16(__nv_bfloat16 *base, int64_t of
 }
 
 // S = G + G^H as the A operand of the tensor-core contraction: row i, K = k,
-// tiled split layout with NRB row blocks and NKB blocks of 32 along k.  The
-// grid covers the padded extents, which are written as zeros.
+// tiled split layout with NRB row blocks and NKB blocks of 32 along k.  S is
+// Hermitian, so one block takes the pair of 32 x 32 tiles (p, q) and (q, p),
+// p <= q: it forms G once on both, S(p, q) = G(p, q) + G(q, p)^H, and writes
+// S(p, q) and its conjugate transpose S(q, p).  Rows and columns from N up
+// to the 32-tile edge are zeros (G is 0 there), so the zero columns k >= N
+// meet the B operand's zero rows.  The 128-row padding past the last 32-row
+// tile is not written: it only feeds output rows i >= N, which are never
+// stored.
 __global__ void __launch_bounds__(256)
 k_bwd_s_split(const float2 *__restrict__ C, const float *__restrict__ g1,
               const float *__restrict__ g2, const float *__restrict__ g3, int N, int64_t NRB,
               int64_t NKB, __nv_bfloat16 *__restrict__ A) {
-    __shared__ float2 Gt[32][33];
-    const int b = blockIdx.z;
-    const int bi = blockIdx.y * 32, bk = blockIdx.x * 32;
+    __shared__ float2 Gt[32][33];  // G(q-tile rows, p-tile columns), transposed on read
+    __shared__ float2 Sm[32][33];  // S(p, q)
+    const int b = blockIdx.y;
+    // pair index -> (p, q), p <= q, column-major over the upper triangle
+    const int t = blockIdx.x;
+    int q = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((q + 1) * (q + 2) / 2 <= t) ++q;
+    while (q * (q + 1) / 2 > t) --q;
+    const int p = t - q * (q + 1) / 2;
+    const int bi = p * 32, bk = q * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t eb = (int64_t)b * N * N;
     auto G = [&](int r, int c) -> float2 {
         if (r >= N || c >= N || r == c) return make_float2(0.f, 0.f);
-        const int64_t q = eb + (int64_t)r * N + c;
-        return gfun(C[q], g1 ? g1[q] : 0.f, g2 ? g2[q] : 0.f, g3 ? g3[q] : 0.f);
+        const int64_t qq = eb + (int64_t)r * N + c;
+        return gfun(C[qq], g1 ? g1[qq] : 0.f, g2 ? g2[qq] : 0.f, g3 ? g3[qq] : 0.f);
     };
-    for (int yy = ty; yy < 32; yy += 8) Gt[yy][tx] = G(bk + yy, bi + tx);
+    for (int yy = ty; yy < 32; yy += 8) Gt[yy][tx] = G(bk + yy, bi + tx);  // G(k, i)
     __syncthreads();
     for (int yy = ty; yy < 32; yy += 8) {
-        const int i = bi + yy, k = bk + tx;
-        const float2 gik = G(i, k);
-        const float2 gki = Gt[tx][yy];  // G(k, i)
-        store_split_bf16(A, split_offset(b, i, k, NRB, NKB),
-                         make_float2(gik.x + gki.x, gik.y - gki.y));
+        const float2 gik = G(bi + yy, bk + tx);
+        const float2 gki = Gt[tx][yy];
+        const float2 v = make_float2(gik.x + gki.x, gik.y - gki.y);  // G_ik + conj(G_ki)
+        Sm[yy][tx] = v;
+        store_split_bf16(A, split_offset(b, bi + yy, bk + tx, NRB, NKB), v);
+    }
+    if (p == q) return;  // the diagonal pair is its own mirror
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += 8) {
+        const float2 v = Sm[tx][yy];  // S(bi + tx, bk + yy)
+        store_split_bf16(A, split_offset(b, bk + yy, bi + tx, NRB, NKB), make_float2(v.x, -v.y));
     }
 }
 
@@ -269,6 +288,8 @@ k_bwd_gemm(const float *__restrict__ S, const float *__restrict__ P, int N, int6
 // Stage 4 on the FFT engine: rows of v = Re(P) s in, grad = -Im(P) s - H{v}
 // out, s = Im(conj(P) Gamma) / |z|.
 struct BwdTask {
+    // load() forms u, v from P, Gamma and 1/|z| (see below)
+    static constexpr bool kLoadComputes = true;
     const float *P;     // [rows][2][ld]
     const float *Gm;    // [rows][2][ld]
     const float *rinv;  // [rows][ld]
@@ -301,6 +322,37 @@ struct BwdTask {
         return make_float2(a, b);
     }
     __device__ void pad(const Rows &, int) const {}  // grad has no padding
+    // eight consecutive samples m0 .. m0+7 (m0 % 8 == 0): 16-byte loads of P,
+    // Gamma and 1/|z| and 16-byte stores of grad (rows are 32-float aligned)
+    static constexpr bool kFinish8 = true;
+    __device__ void row8(const Row &w, int m0, const float (&h)[8]) const {
+        if (!PLV_IN_BOUNDS(m0 >= 0 && (m0 & 7) == 0 && m0 + 8 <= T)) return;
+        float pr[8], pi[8], gr[8], gi[8], q[8];
+        auto ld8 = [](const float *p, float (&v)[8]) {
+            const float4 a = __ldg((const float4 *)p), b = __ldg((const float4 *)p + 1);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        };
+        ld8(w.p + m0, pr);
+        ld8(w.p + ld + m0, pi);
+        ld8(w.g + m0, gr);
+        ld8(w.g + ld + m0, gi);
+        ld8(w.q + m0, q);
+        float o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float sk = fmaf(pr[k], gi[k], -pi[k] * gr[k]) * q[k];
+            o[k] = -pi[k] * sk - h[k];
+        }
+        float4 *d = (float4 *)(w.o + m0);
+        d[0] = make_float4(o[0], o[1], o[2], o[3]);
+        d[1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
+    __device__ void finish8(const Rows &rs, int m0, const float (&h0)[8], const float (&h1)[8],
+                            float) const {
+        if (rs.v0) row8(rs.a, m0, h0);
+        if (rs.v1) row8(rs.b, m0, h1);
+    }
     __device__ void finish(const Rows &rs, int m, float h0, float h1, float) const {
         float pr, pi;
         if (rs.v0) {
@@ -338,7 +390,8 @@ cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, 
         __nv_bfloat16 *B = (__nv_bfloat16 *)((uint8_t *)tc_ops + a_bytes);
         const int64_t NRB = row_blocks(N), NKB = ((int64_t)N + kTileK - 1) / kTileK;
         const int64_t NRBT = row_blocks((int)ld);
-        dim3 sg((unsigned)NKB, (unsigned)(NRB * 4), batch);
+        const unsigned nt = (unsigned)NKB;  // 32-tiles along i and along k
+        dim3 sg(nt * (nt + 1) / 2, batch);
         k_bwd_s_split<<<sg, 256, 0, st>>>(C, g1, g2, g3, N, NRB, NKB, A);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
