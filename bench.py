@@ -426,10 +426,19 @@ def run_ours(args):
     # under CUDA graphs), measured after the main workload's buffers are freed
     in_bytes = x.element_size()
     grouped = None
-    if not args.no_grouped:
+    configs = None
+    if not args.no_grouped or not args.no_configs:
         del x, P, out, e2e_buffers
         torch.cuda.empty_cache()
+    if not args.no_grouped:
         grouped = grouped_measure(args, dev, dist, rank, world)
+    if not args.no_configs:
+        # the other configurations of the same job, each in its own launch
+        # configuration, so one line carries every workload the metric names
+        configs = {"fp32-N4096-T4096-E30": fp32_workload_measure(args, dev, dist, rank, world),
+                   BACKWARD: backward_measure(args, dev, dist, rank, world)}
+        if rank == 0:
+            configs["tones-N64-T2048"] = parity_measure(args, dev)
 
     if rank == 0:
         line = {
@@ -454,6 +463,7 @@ def run_ours(args):
             "device_status": device_status,
             "device_memory": mem,
             "grouped": grouped,
+            "configs": configs,
         }
         print(json.dumps(line), flush=True)
     h.close()
@@ -598,6 +608,133 @@ def grouped_measure(args, dev, dist, rank, world):
     return out
 
 
+def parity_measure(args, dev):
+    """The parity workload (64 channels, T = 2048, fs = 512 Hz tones, FP64
+    input, one epoch): the whole path on the GPU in FP32 and BF16x3 (CUDA
+    events), and the full FP64 oracle (every row's direct-DFT analytic
+    signal, the pairwise loop over all 64^2 pairs, no sampling) on the host
+    cores, with each GPU path's largest error per metric against it."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    x, _ = synth.tones(seed=1001)
+    E, N, T = x.shape
+    t0 = time.perf_counter()
+    ref = oracle.connectivity(x[0])
+    t_oracle = time.perf_counter() - t0
+    units = float(N) * N * T
+    rec = {"workload": f"tones-N{N}-T{T}-E{E} (FP64 input, 16 lagged pairs, 8 zero-lag "
+                       f"mixtures, noise 0.5)",
+           "oracle": {"seconds": t_oracle, "value": units / t_oracle, "unit": UNIT,
+                      "cores": oracle.threads(),
+                      "what": "full oracle: direct-DFT analytic signal of every row, pairwise "
+                              "loop over all ordered pairs"}}
+    xd = torch.tensor(x, device=dev)
+    c = ref["c"]
+    d = np.maximum((1 - c.real) * (1 + c.real), 1e-12)
+    for prec, tol in (("fp32", 1e-5), ("bf16x3", 2e-5)):
+        h = plv.Handle(precision=prec, device=dev.index)
+        P = h.empty_phasors(E, N, T)
+        out = {k: torch.empty((E, N, N), dtype=torch.float32, device=dev)
+               for k in ("plv", "iplv", "ciplv")}
+        s = torch.cuda.current_stream(dev)
+
+        def step():
+            h.plv_analytic(xd, P)
+            h.plv_gram(P, E, N, T, out=out)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(args.steps):
+            step()
+        b.record(s)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / args.steps
+        got = {k: v[0].double().cpu().numpy() for k, v in out.items()}
+        bound = tol / np.sqrt(d) + np.abs(c.imag * c.real) * tol / d ** 1.5 + 1e-6
+        ce = np.abs(got["ciplv"] - ref["ciplv"])
+        rec[prec] = {"ms_per_step": ms, "value": units / (ms / 1e3),
+                     "speedup_vs_oracle": t_oracle / (ms / 1e3),
+                     "max_abs_err": {k: float(np.abs(got[k] - ref[k]).max())
+                                     for k in ("plv", "iplv", "ciplv")},
+                     "ciplv_within_conditioned_bound": bool(np.all(ce <= bound)),
+                     "bound_plv_iplv": tol}
+        h.close()
+    return rec
+
+
+def fp32_workload_measure(args, dev, dist, rank, world):
+    """The plain FP32 workload: N = T = 4096, 30 epochs, analytic signal and
+    the CUDA-core Gram with fused read-outs (the same generator as the
+    headline); per-metric error against the FP64 oracle on a 128-channel
+    sample of epoch 0 (rank 0)."""
+    import torch
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    wl = "bandlimited-N4096-T4096-E30"
+    E, N, T, seed = WORKLOADS[wl]
+    h = plv.Handle(precision="fp32", device=dev.index)
+    x = synth.bandlimited(E, N, T, seed=rank_seed(seed, rank), device=dev)
+    P = h.empty_phasors(E, N, T)
+    out = {k: torch.empty((E, N, N), dtype=torch.float32, device=dev)
+           for k in ("plv", "iplv", "ciplv")}
+    s = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(e=None):
+        if e:
+            e[0].record(s)
+        h.plv_analytic(x, P)
+        if e:
+            e[1].record(s)
+        h.plv_gram(P, E, N, T, out=out)
+        if e:
+            e[2].record(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    per = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    for p_ in per:
+        step(p_)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(sum(p_[0].elapsed_time(p_[2]) for p_ in per), dist, dev)
+    k1_ms = statistics.mean(p_[0].elapsed_time(p_[1]) for p_ in per)
+    k2_ms = statistics.mean(p_[1].elapsed_time(p_[2]) for p_ in per)
+    ms_step = ms / args.steps
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    flops = gram_flops(N, T, E, "fp32")
+    rec = {"workload": wl, "value": job_value(float(N) * N * T * E, world, ms_step),
+           "unit": UNIT, "ms_per_step": ms_step,
+           "roofline": {"bound": "alu", "kernel": "k_gram_fp32", "launch_ms": k2_ms,
+                        "achieved": flops / (k2_ms / 1e3) / 1e12, "peak": alu_peak,
+                        "unit": "TFLOP/s", "frac": flops / (k2_ms / 1e3) / 1e12 / alu_peak,
+                        "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {sm_mhz:.0f} MHz"},
+           "k1_ms": k1_ms,
+           "k1_frac_of_hbm": k1_bytes(N, T, E) / (k1_ms / 1e3) / 1e9 / float(peaks["hbm_gbs"])}
+    if rank == 0 and not args.no_cpu_baseline:
+        sub = sample_channels(N, seed, 128)
+        ref, _, _, _ = oracle_step(x[0], sub)
+        sub_t = torch.as_tensor(sub, device=dev)
+        got = {k: out[k][0].index_select(0, sub_t).index_select(1, sub_t).double().cpu().numpy()
+               for k in ("plv", "iplv", "ciplv")}
+        rec["accuracy_vs_oracle"] = oracle_errors({"fp32": got}, ref, len(sub), N)
+    h.close()
+    del x, P, out
+    torch.cuda.empty_cache()
+    return rec
+
+
 def run_grouped(args):
     """The uneven batch alone, as its own bench line."""
     import torch
@@ -625,22 +762,15 @@ def run_grouped(args):
         dist.destroy_process_group()
 
 
-def run_backward(args):
+def backward_measure(args, dev, dist, rank, world):
     """Forward (analytic signal, Gram with C) and backward (recompute,
-    S = G + G^H, Gamma = S P / T, adjoint Hilbert) of the masked ciPLV loss."""
+    S = G + G^H, Gamma = S P / T, adjoint Hilbert) of the masked ciPLV loss;
+    returns the measurement as a dict (a bench line without the run keys)."""
     import torch
     import paper_1710_08037_gb300 as plv
     from paper_1710_08037_gb300 import synth
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
+    local = dev.index
     B, N, T = 16, 1024, 4096
     hf = plv.Handle(precision=args.precision, device=local)
     hb = hf  # split handles take the backward contraction to the tensor cores
@@ -710,36 +840,52 @@ def run_backward(args):
         fp32_bwd = {"backward_ms": a.elapsed_time(b) / 2,
                     "rel_l2_diff_vs_split": rel}
         h32.close()
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"{args.precision} (backward contraction "
-                     f"{'bf16x3' if args.precision != 'fp32' else 'f32'}, "
-                     f"rest f32)",
-            "data": "synthetic",
-            "config": {"workload": BACKWARD, "B": B, "N": N, "T": T,
-                       "loss": "sum of ciPLV over a seeded 10% mask of ordered "
-                               "pairs", "recompute": "analytic signal "
-                       "recomputed in the backward pass"},
-            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
-            "backward_contraction": {
-                "flops_per_step": gemm_flops * (3 if split else 1),
-                "note": ("Gamma = S P / T on the tensor cores, BF16 hi+lo "
-                         "splits (3 products per term); bound: tensor, "
-                         "peak %s BF16 burst" % peak_kind) if split else
-                        ("Gamma = S P / T, FP32 on the CUDA cores; bound: "
-                         "alu, peak derived from 152 SMs x 128 FMA x 2 x "
-                         "max SM clock"),
-                "peak_tflops": peak,
-                "lower_bound_tflops_over_whole_backward":
-                    gemm_flops * (3 if split else 1) / (bwd_ms / 1e3) / 1e12},
-            "fp32_backward": fp32_bwd,
-            "gpu_launches": (2 + (6 if split else 4)) * args.steps,
-            "clocks": clk, "device_status": hb.plv_sync_status()}
-        print(json.dumps(line), flush=True)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{args.precision} (backward contraction "
+                 f"{'bf16x3' if args.precision != 'fp32' else 'f32'}, "
+                 f"rest f32)",
+        "data": "synthetic",
+        "config": {"workload": BACKWARD, "B": B, "N": N, "T": T,
+                   "loss": "sum of ciPLV over a seeded 10% mask of ordered "
+                           "pairs", "recompute": "analytic signal "
+                   "recomputed in the backward pass"},
+        "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+        "backward_contraction": {
+            "flops_per_step": gemm_flops * (3 if split else 1),
+            "note": ("Gamma = S P / T on the tensor cores, BF16 hi+lo "
+                     "splits (3 products per term); bound: tensor, "
+                     "peak %s BF16 burst" % peak_kind) if split else
+                    ("Gamma = S P / T, FP32 on the CUDA cores; bound: "
+                     "alu, peak derived from 152 SMs x 128 FMA x 2 x "
+                     "max SM clock"),
+            "peak_tflops": peak,
+            "lower_bound_tflops_over_whole_backward":
+                gemm_flops * (3 if split else 1) / (bwd_ms / 1e3) / 1e12},
+        "fp32_backward": fp32_bwd,
+        "gpu_launches": (2 + (6 if split else 4)) * args.steps,
+        "clocks": clk, "device_status": hb.plv_sync_status()}
     hf.close()
+    return line
+
+
+def run_backward(args):
+    """The differentiable-loss workload alone, as its own bench line."""
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    line = backward_measure(args, torch.device("cuda", local), dist, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -1332,6 +1478,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-grouped", action="store_true",
                     help="main workload: skip the uneven-batch sub-record")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="main workload: skip the FP32, backward and parity sub-records")
     ap.add_argument("--no-tune", action="store_true",
                     help="grouped workload: keep the plan's default launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
