@@ -257,9 +257,11 @@ plv_status plv_normalize(plv_handle *h, void *stream, const void *z,
  *   C        : complex64 interleaved [batch][N][N] (8 bytes per entry).
  *   diag_dev : double [batch] or NULL: max_i |C_ii - 1| per epoch, the unit-
  *              modulus check of Eq. 4 (1/T applied in FP64).
- * FP64 is used only for the diagonal check and for the ciPLV denominator
- * (1 - Re C)(1 + Re C) where |Re C| > 1 - 2^-6, the range where 1 - Re^2
- * cancels; elsewhere the factored FP32 form is within one ulp of it. */
+ * FP64 is used only for the diagonal check.  The ciPLV denominator
+ * (1 - Re C)(1 + Re C) is formed with an error-free transformation in FP32
+ * (exact product via FMA, exact 1 + |Re C| via Fast2Sum): within one ulp of
+ * its correctly rounded exact value, as an FP64 evaluation would give, with
+ * no cancellation as |Re C| -> 1. */
 plv_status plv_gram(plv_handle *h, void *stream, const void *P, int batch,
                     int N, int T, unsigned out_mask, float *plv, float *iplv,
                     float *ciplv, void *C, double *diag_dev);

@@ -7,22 +7,27 @@
 
 namespace plv {
 
-// Denominator of Eq. 14, d = 1 - (Re C)^2, formed as (1 - r)(1 + r).  Where
-// the plain 1 - r^2 would cancel, |r| > 1 - 2^-6 (d < 2^-5), the factors and
-// their product are taken in FP64, so d is the exactly rounded FP32 value of
-// the FP32 input's true denominator.  Below that threshold the FP32 factored
-// form already carries about one ulp: for |r| >= 1/2 the factor 1 - |r| is
-// exact (Sterbenz's lemma) and the other lies in [3/2, 2) with at most half
-// an ulp of rounding; below 1/2 both factors lie in (1/2, 3/2).  Either way
-// the rounding of d is far below the effect of the Gram's own error in r
-// (2 |r| dr).
-constexpr float kCiplvFp64Above = 1.0f - 0x1p-6f;
+// Denominator of Eq. 14, d = 1 - (Re C)^2 = (1 - a)(1 + a), a = |Re C|,
+// formed without cancellation and to the accuracy of an FP64 evaluation,
+// with an error-free transformation in FP32 (no FP64 instruction, no branch):
+//   u = 1 - a              exact for a >= 1/2 (Sterbenz's lemma);
+//   v = RN(1 + a), e = (1 - v) + a, so v + e = 1 + a exactly (Fast2Sum);
+//   p = RN(u v), pe = fma(u, v, -p), so u v = p + pe exactly;
+//   d = RN(p + fma(u, e, pe))  =  u (1 + a) with two final roundings,
+// within one ulp of the correctly rounded exact value -- the value that the
+// factors and product taken in FP64 and rounded to FP32 give -- in the range
+// where 1 - Re^2 cancels (a -> 1).  Below a = 1/2, where nothing cancels, u
+// carries half an ulp.  An FP64 branch for |Re| > 1 - 2^-6 gave the same
+// values but, taken or not, cost 30-53 % of the epilogue-bound Grams (K = 64
+// trials, short windows) on GB300's slow FP64 pipe.
 __device__ __forceinline__ float ciplv_den(float r) {
-    if (fabsf(r) > kCiplvFp64Above) {
-        const double rd = (double)r;
-        return (float)((1.0 - rd) * (1.0 + rd));
-    }
-    return (1.0f - r) * (1.0f + r);
+    const float a = fabsf(r);
+    const float u = 1.0f - a;
+    const float v = 1.0f + a;
+    const float e = (1.0f - v) + a;
+    const float p = u * v;
+    const float pe = fmaf(u, v, -p);
+    return p + fmaf(u, e, pe);
 }
 
 // The square root and the division of the read-outs go through the

@@ -206,9 +206,10 @@ def test_ciplv_near_zero_lag_tones(handles, prec):
 @pytest.mark.parametrize("prec", PRECISIONS)
 def test_ciplv_denominator_near_unit_real_part(handles, prec):
     """Eq. 14's denominator (1 - Re)(1 + Re) on given FP32 values of C with
-    |Re C| from 0.3 to 1 - 2^-24 (both sides of the FP64 threshold 1 - 2^-6):
-    ciPLV against the FP64 value of the same FP32 inputs to a few ulp
-    (the reciprocal square root's error), and 0 where Re^2 >= 1."""
+    |Re C| from 0.3 to 1 - 2^-24 (where 1 - Re^2 cancels): ciPLV against the
+    FP64 value of the same FP32 inputs to a few ulp (the reciprocal square
+    root's error; the denominator itself is the error-free FP32 form), and
+    0 where Re^2 >= 1."""
     h = handles[prec]
     n = 64
     rng = np.random.default_rng(11)
