@@ -314,8 +314,9 @@ plv_status plv_group_create(plv_handle *h, const plv_problem *probs, int nprob,
 
 /* Run a plan: Eq. 7, 13, 14 for every problem.  BF16X3 / FP16X3 handles run
  * ONE persistent tensor-core launch over the whole tile list (CTAs take
- * tiles round-robin, longest first); an FP32 handle runs one Gram launch per
- * problem.  Allocates nothing: can be captured in a CUDA graph. */
+ * tiles round-robin, longest first), preceded by a memset of the split-K
+ * counters when the plan splits tiles; an FP32 handle runs one Gram launch
+ * per problem.  Allocates nothing: can be captured in a CUDA graph. */
 plv_status plv_gram_grouped(plv_handle *h, void *stream, const plv_group *group);
 
 /* Eq. 3 and 4 for every problem of a plan that has an input x: the
@@ -340,6 +341,8 @@ typedef struct {
     int k1_launches;    /* non-empty thread class launches of plv_analytic_grouped */
     int gram_schedule;  /* 0: longest first, round-robin; 1: balanced rounds */
     int gram_tile_cost; /* per-tile cost (in 32-sample K blocks) the balanced rounds assumed */
+    int gram_split;     /* split-K factor f kept (0: no tile split; plv_group_configure) */
+    int gram_split_tiles; /* tiles that run as several parts under it */
     int timed_configs;  /* configurations launched and timed */
     int cached;         /* 1: the configuration came from the handle's cache; nothing was timed */
 } plv_tune_result;
@@ -356,7 +359,9 @@ typedef struct {
  *   - Gram (BF16X3 / FP16X3): the tile schedule, i.e. the order of the
  *     tile list that the persistent CTAs take round-robin: longest first
  *     (default) or balanced rounds (each round of G tiles dealt to the
- *     least-loaded CTAs under a per-tile cost of 0, 8 or 32 K blocks).
+ *     least-loaded CTAs under a per-tile cost of 0, 8 or 32 K blocks); then,
+ *     in that schedule, split K with factor f = 1, 2 or 4 (see
+ *     plv_gram_split_plan and plv_group_configure), kept if 3 % faster.
  * The candidates run on the plan's own buffers and write the plan's outputs
  * (with the values any run writes), so the phasors P must be valid for the
  * Gram part: with an input x the tuner's own analytic-signal launches write
@@ -380,12 +385,38 @@ plv_status plv_group_tune(plv_handle *h, void *stream, plv_group *group, int rep
  *   k1_per_sm      [4] CTAs per SM of each class launch (0: the occupancy
  *                  limit; values above it act as 0), or NULL for all 0;
  *   gram_schedule  0: longest first; 1: balanced rounds with per-tile cost
- *                  gram_tile_cost (0 .. 2^20 K blocks).
- * Results do not depend on these.  Same synchronisation, allocation and
- * graph rules as plv_group_tune.  Errors: PLV_ERR_INVALID for values out of
- * range. */
+ *                  gram_tile_cost (0 .. 2^20 K blocks);
+ *   gram_split     split-K factor f (0 .. 64; 0: no tile split): tiles longer
+ *                  than the grid's fair share / f (and than 2048 samples) run
+ *                  as several parts on different CTAs (plv_gram_split_plan).
+ *                  A part sums its K range as a whole tile does and stores
+ *                  the sums in a 128 KB slot of the plan; for each 32 x 32
+ *                  block, the last part to finish adds the tile's slots in
+ *                  part order and stores the block.  The plan allocates the
+ *                  slots (at most 8192, 1 GiB) and 16 counters per split
+ *                  tile.
+ * Results do not depend on the K1 shapes and the schedule: they give the
+ * same bits.  Split K regroups a split tile's FP32 additions (part sums,
+ * then their sum in part order), so its results differ from the unsplit
+ * plan's by FP32 rounding; a given configuration gives the same bits on
+ * every run.  Same synchronisation, allocation and graph rules as
+ * plv_group_tune.  Errors: PLV_ERR_INVALID for values out of range. */
 plv_status plv_group_configure(plv_handle *h, void *stream, plv_group *group, int k1_widen,
-                               const int *k1_per_sm, int gram_schedule, int gram_tile_cost);
+                               const int *k1_per_sm, int gram_schedule, int gram_tile_cost,
+                               int gram_split);
+
+/* The split-K plan of plv_group_configure and plv_group_tune (host only;
+ * needs no device).  For ntiles tiles of nkb[i] 32-sample K blocks, `chunk`
+ * K blocks per summation chunk (16 for BF16X3, 4 for FP16X3), a persistent
+ * grid of `grid` CTAs and factor `split` (0 .. 64), writes parts[i], the
+ * number of parts tile i runs as (1: whole).  With W the total K blocks and
+ * L = max(chunk, 64, ceil(W / (grid split))), a tile of nkb > L K blocks
+ * takes S = min(ceil(nkb / L), ceil(nkb / chunk)) parts, longest tiles
+ * first while the slots (8192, one per part) last; part s of S covers the
+ * chunks [floor(s nch / S), floor((s + 1) nch / S)) of the tile's nch.
+ * split = 0 gives 1 everywhere.  Errors: PLV_ERR_INVALID. */
+plv_status plv_gram_split_plan(const int *nkb, int ntiles, int chunk, int grid, int split,
+                               int *parts);
 
 /* Free a plan (synchronises the device).  NULL is ignored. */
 plv_status plv_group_destroy(plv_group *group);

@@ -293,8 +293,9 @@ class Handle:
 
     def plv_group_tune(self, group, reps=3):
         """Autotune the plan's launch shapes (thread class per transform
-        length, CTAs per SM, Gram tile schedule) by timing candidates on its
-        own buffers; returns what was chosen and measured as a dict."""
+        length, CTAs per SM, Gram tile schedule and split K) by timing
+        candidates on its own buffers; returns what was chosen and measured
+        as a dict."""
         r = _lib.PlvTuneResult()
         _lib.check(self.lib.plv_group_tune(self.h, _stream(self.device),
                                            group.g, int(reps),
@@ -306,13 +307,14 @@ class Handle:
         return out
 
     def plv_group_configure(self, group, k1_widen=False, k1_per_sm=None,
-                            gram_schedule="longest_first", gram_tile_cost=0):
+                            gram_schedule="longest_first", gram_tile_cost=0,
+                            gram_split=0):
         """Pin one of the tuner's candidate launch shapes without timing."""
         ps = (ctypes.c_int * 4)(*(k1_per_sm or (0, 0, 0, 0)))
         sched = {"longest_first": 0, "balanced_rounds": 1}[gram_schedule]
         _lib.check(self.lib.plv_group_configure(
             self.h, _stream(self.device), group.g, int(bool(k1_widen)), ps,
-            sched, int(gram_tile_cost)), self.h)
+            sched, int(gram_tile_cost), int(gram_split)), self.h)
 
     def plv_trial_operands(self, V, E, N, ldv, l0, L, mode="asis", P=None):
         """Operands of the Gram over trials (Eq. 1 / 8 with mode "asis",
@@ -481,6 +483,20 @@ def connectivity(x, handle=None):
     if handle is None:
         handle = _default_handle(x.device)
     return _Connectivity.apply(x, handle)
+
+
+def gram_split_plan(nkb, chunk, grid, split):
+    """The split-K plan of grouped Grams (host only, no device): for tiles
+    of nkb[i] 32-sample K blocks, `chunk` K blocks per summation chunk, a
+    grid of `grid` CTAs and factor `split`, the number of parts each tile
+    runs as (plv_gram_split_plan)."""
+    lib = _lib.load()
+    n = len(nkb)
+    a = (ctypes.c_int * max(n, 1))(*[int(v) for v in nkb])
+    out = (ctypes.c_int * max(n, 1))()
+    _lib.check(lib.plv_gram_split_plan(a, n, int(chunk), int(grid), int(split), out),
+               None, lib)
+    return list(out[:n])
 
 
 _handles = {}

@@ -79,7 +79,8 @@ SIGNATURES = {
     "plv_gram_windows": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _u, _vp, _vp, _vp,
                               _vp, _vp]),
     "plv_group_tune": (_i, [_vp, _vp, _vp, _i, _vp]),
-    "plv_group_configure": (_i, [_vp, _vp, _vp, _i, _vp, _i, _i]),
+    "plv_group_configure": (_i, [_vp, _vp, _vp, _i, _vp, _i, _i, _i]),
+    "plv_gram_split_plan": (_i, [_vp, _i, _i, _i, _i, _vp]),
     "plv_group_destroy": (_i, [_vp]),
     "plv_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
 }
@@ -142,6 +143,8 @@ class PlvTuneResult(ctypes.Structure):
                 ("k1_launches", ctypes.c_int),
                 ("gram_schedule", ctypes.c_int),
                 ("gram_tile_cost", ctypes.c_int),
+                ("gram_split", ctypes.c_int),
+                ("gram_split_tiles", ctypes.c_int),
                 ("timed_configs", ctypes.c_int), ("cached", ctypes.c_int)]
 
 

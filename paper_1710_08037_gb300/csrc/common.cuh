@@ -155,11 +155,12 @@ struct GroupConfig {
     int k1_per_sm[kConvClasses] = {0, 0, 0, 0};  // 0: occupancy limit
     int gram_schedule = kSchedLongestFirst;
     int gram_tile_cost = 0;             // per-tile fixed cost, in K blocks
+    int gram_split = 0;                 // split-K factor f (0: no tile split)
     bool operator==(const GroupConfig &o) const {
         for (int c = 0; c < kConvClasses; ++c)
             if (k1_per_sm[c] != o.k1_per_sm[c]) return false;
         return k1_class == o.k1_class && gram_schedule == o.gram_schedule &&
-               gram_tile_cost == o.gram_tile_cost;
+               gram_tile_cost == o.gram_tile_cost && gram_split == o.gram_split;
     }
 };
 
@@ -386,9 +387,34 @@ struct TcGemm {
     float *G;
 };
 cudaError_t launch_gemm_tc(const Handle *h, cudaStream_t s, const TcGemm &g, int batch);
-// One persistent launch over a list of (problem, epoch, I, J) tiles.
+// Split K of a grouped Gram.  A long tile may run as S parts, each over a
+// range of whole K chunks (the chunks of the two-level summation), on
+// different CTAs.  A part adds its chunks' sums as an unsplit tile does and
+// stores the result in its slot of `partials`; per 32 x 32 block of the
+// tile, the warp that completes the block's count of S arrivals adds the S
+// slots in part order (a fixed order: every run gives the same bits) and
+// stores the block.
+struct SplitPart {
+    int kb_lo, kb_hi;  // K blocks of the part
+    int tile;          // the tile's counter index
+    int slot;          // this part's slot; the tile's parts use slot - s .. + S - 1
+    int s, S;          // part s of S
+    int pad[2];
+};
+struct TcSplit {
+    const SplitPart *parts = nullptr;
+    float *partials = nullptr;  // [slot][Re, Im][128][128] FP32
+    int *counters = nullptr;    // [split tile][16 blocks], zero before each launch
+    int nslots = 0, ntiles = 0; // sizes of partials (slots) and counters (tiles)
+};
+constexpr int kTileFloats = 2 * 128 * 128;  // one slot
+// K blocks of 32 samples per chunk of the two-level summation (BF16x3: 512
+// samples, FP16x3: 128).
+inline int gram_chunk_kb(plv_precision p) { return p == PLV_PREC_FP16X3 ? 4 : 16; }
+// One persistent launch over a list of tiles: items[t] = (problem, epoch,
+// I | J << 16, 1 + split part, or 0 for a whole tile).
 cudaError_t launch_gram_tc_group(const Handle *h, cudaStream_t s, const TcProblem *probs,
-                                 const int4 *items, int nitems);
+                                 const int4 *items, int nitems, const TcSplit &split);
 // Zero the diagonal-check outputs of every problem of a group.
 cudaError_t launch_zero_group_diag(cudaStream_t s, const TcProblem *probs, int nprob);
 // Operands of a Gram over trials (k_trials.cu): one problem per column.

@@ -45,7 +45,11 @@
 // Work list.  A launch covers one problem (every epoch's upper-triangle
 // tiles, enumerated in the kernel) or a group of problems of different N
 // and T (an explicit list of (problem, epoch, I, J) items, longest first).
-// CTAs take items round-robin; all three roles walk the same sequence.
+// CTAs take items round-robin; all three roles walk the same sequence.  In
+// a group, a long tile may run as several split-K parts (whole chunks each)
+// on different CTAs: each part stores its running sums in a slot, and per
+// 32 x 32 block the last part to arrive (an atomic count, no waiting) adds
+// the slots in part order and does the block's epilogue.
 //
 // Every wait on an mbarrier is bounded in time; on expiry the CTA records
 // PLV_ERR_TIMEOUT in the device status word, stops issuing work, lets the
@@ -75,6 +79,8 @@ template <uint32_t FMT>
 struct Chunk {
     static constexpr int CH = FMT == 1u ? 16 : 4;
 };
+static_assert(Chunk<1u>::CH == 16 && Chunk<0u>::CH == 4, "gram_chunk_kb (common.cuh)");
+static_assert(kTileFloats == 2 * TM * TN, "split-K chunk slot");
 // per epilogue warp, a 32-row x 8-column FP32 staging tile for the row-wise
 // stores (after the operand ring and the barriers)
 constexpr int STAGE_TILE_FLOATS = 32 * 8;
@@ -307,7 +313,8 @@ __device__ __forceinline__ void tile_raster(int t, int nrb, int W, int &I, int &
 struct TcArgs {
     TcProblem single;         // the problem when items == nullptr
     const TcProblem *probs;   // group: problem descriptors
-    const int4 *items;        // group: (problem, epoch, I, J), longest first
+    const int4 *items;        // group: (problem, epoch, I | J << 16, 1 + part or 0)
+    TcSplit split;            // group: split-K parts of long tiles
     TcGemm gemm;              // GEMM mode: the contraction
     int total_items;
     int *status;
@@ -324,21 +331,89 @@ __device__ __forceinline__ void gemm_item(const TcGemm &g, int t, int &e, int &I
     J = r - I * g.nrb_b;
 }
 
+// Item t: its problem, output matrix e, tile (I, J), K blocks [kb_lo,
+// kb_hi) and split part (-1: the whole tile; always, unless SPLIT).
+template <bool SPLIT>
 __device__ __forceinline__ const TcProblem &item_of(const TcArgs &a, int t, int &e, int &I,
-                                                    int &J) {
+                                                    int &J, int &kb_lo, int &kb_hi, int &part) {
     if (a.items) {
         const int4 it = a.items[t];
         e = it.y;
-        I = it.z;
-        J = it.w;
-        return a.probs[it.x];
+        I = it.z & 0xffff;
+        J = (int)((unsigned)it.z >> 16);
+        const TcProblem &pb = a.probs[it.x];
+        part = SPLIT ? it.w - 1 : -1;
+        kb_lo = 0;
+        kb_hi = pb.nkb;
+        if (SPLIT && part >= 0) {
+            const SplitPart &pr = a.split.parts[part];
+            // checked builds: a part inside its tile's K range
+            if (PLV_IN_BOUNDS(pr.kb_lo >= 0 && pr.kb_lo < pr.kb_hi && pr.kb_hi <= pb.nkb)) {
+                kb_lo = pr.kb_lo;
+                kb_hi = pr.kb_hi;
+            }
+        }
+        return pb;
     }
     e = t / a.single.tpe;
     tile_raster(t - e * a.single.tpe, a.single.nrb, a.single.raster, I, J);
+    kb_lo = 0;
+    kb_hi = a.single.nkb;
+    part = -1;
     return a.single;
 }
 
-template <uint32_t FMT, bool GEMM>
+// Split K, per 32 x 32 block of a tile: the warp stores its block of the
+// part's sums in the part's slot and counts the arrival on the block's
+// counter; the warp that completes the count (all S parts stored) adds the
+// S slots in part order and returns true to store the block.  Writers fence
+// before counting and the last one fences after, so it reads every part's
+// slot (through L2, bypassing L1).
+__device__ __forceinline__ bool split_last(const TcSplit &sp, const SplitPart &pr, int blk,
+                                           int row, int cq, int lane, float (&sre)[32],
+                                           float (&sim)[32]) {
+    float *d = sp.partials + (size_t)pr.slot * kTileFloats + (size_t)row * TN + cq * 32;
+#pragma unroll
+    for (int k = 0; k < 32; k += 4) {
+        __stcg((float4 *)(d + k), make_float4(sre[k], sre[k + 1], sre[k + 2], sre[k + 3]));
+        __stcg((float4 *)(d + TM * TN + k),
+               make_float4(sim[k], sim[k + 1], sim[k + 2], sim[k + 3]));
+    }
+    __threadfence();
+    __syncwarp();
+    int old = 0;
+    if (lane == 0) old = atomicAdd(sp.counters + (size_t)pr.tile * 16 + blk, 1);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != pr.S - 1) return false;
+    __threadfence();
+    const float *b = sp.partials + (size_t)(pr.slot - pr.s) * kTileFloats + (size_t)row * TN +
+                     cq * 32;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        sre[k] = 0.f;
+        sim[k] = 0.f;
+    }
+    for (int r = 0; r < pr.S; ++r, b += kTileFloats) {
+#pragma unroll
+        for (int k = 0; k < 32; k += 4) {
+            const float4 vr = __ldcg((const float4 *)(b + k));
+            const float4 vi = __ldcg((const float4 *)(b + TM * TN + k));
+            sre[k] += vr.x;
+            sre[k + 1] += vr.y;
+            sre[k + 2] += vr.z;
+            sre[k + 3] += vr.w;
+            sim[k] += vi.x;
+            sim[k + 1] += vi.y;
+            sim[k + 2] += vi.z;
+            sim[k + 3] += vi.w;
+        }
+    }
+    return true;
+}
+
+// SPLIT: the launch list holds split parts (grouped plans with split K);
+// the other instantiations carry none of the split code.
+template <uint32_t FMT, bool GEMM, bool SPLIT = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_gram_tc(const __grid_constant__ TcArgs args) {
     extern __shared__ uint8_t smem_raw[];
@@ -391,7 +466,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             // never issued, so the MMA issuer's wait for it runs into the bound
             bool withhold = args.stall != 0;
             for (int t = blockIdx.x; t < args.total_items && !*abort_flag; t += gridDim.x) {
-                int e, I, J, nkb;
+                int e, I, J, nkb, kb_lo = 0, kb_hi;
                 bool diag;
                 const uint8_t *pa, *pj;
                 if constexpr (GEMM) {
@@ -399,6 +474,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     gemm_item(g, t, e, I, J);
                     diag = false;
                     nkb = g.nkb;
+                    kb_hi = nkb;
                     pa = g.A + (size_t)((int64_t)e * g.nrb_a + I) * nkb * SIDE_BYTES;
                     pj = g.B + (size_t)((int64_t)e * g.nrb_b + J) * nkb * SIDE_BYTES;
                     // checked builds: operand blocks inside both operands
@@ -408,7 +484,8 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                         pj = g.B;
                     }
                 } else {
-                    const TcProblem &pb = item_of(args, t, e, I, J);
+                    int part;
+                    const TcProblem &pb = item_of<SPLIT>(args, t, e, I, J, kb_lo, kb_hi, part);
                     diag = I == J;
                     nkb = pb.nkb;
                     // output matrix e: window w of epoch b
@@ -423,7 +500,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                         pj = pb.P;
                     }
                 }
-                for (int kb = 0; kb < nkb; ++kb) {
+                for (int kb = kb_lo; kb < kb_hi; ++kb) {
                     if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status, args.wait_ns)) break;
                     const uint32_t sa = base + stage * STAGE_BYTES;
                     mbar_expect_tx(FULL(stage), diag ? SIDE_BYTES : 2 * SIDE_BYTES);
@@ -463,23 +540,23 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             bool ok = true;
             for (int t = blockIdx.x; ok && t < args.total_items && !*abort_flag;
                  t += gridDim.x) {
-                int e, I, J, nkb, ncols;
+                int e, I, J, kb_lo = 0, kb_hi, ncols;
                 bool diag;
                 if constexpr (GEMM) {
                     gemm_item(args.gemm, t, e, I, J);
                     diag = false;
-                    nkb = args.gemm.nkb;
+                    kb_hi = args.gemm.nkb;
                     ncols = (int)args.gemm.ld - J * TN;
                 } else {
-                    const TcProblem &pb = item_of(args, t, e, I, J);
+                    int part;
+                    const TcProblem &pb = item_of<SPLIT>(args, t, e, I, J, kb_lo, kb_hi, part);
                     diag = I == J;
-                    nkb = pb.nkb;
                     ncols = pb.N - J * TN;
                 }
                 const int nw = mma_width(ncols);
                 const uint32_t ID_POS = idesc_f16(FMT, false, nw);
                 const uint32_t ID_NEG = idesc_f16(FMT, true, nw);
-                for (int kb0 = 0; ok && kb0 < nkb; kb0 += Chunk<FMT>::CH) {
+                for (int kb0 = kb_lo; ok && kb0 < kb_hi; kb0 += Chunk<FMT>::CH) {
                     if (!wait_bar(TEMPTY(buf), buf_phase ^ 1u, abort_flag, args.status, args.wait_ns)) {
                         ok = false;
                         break;
@@ -487,7 +564,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     tc_fence_after();
                     const uint32_t d_re = tmem + buf * ACC_COLS;
                     const uint32_t d_im = d_re + TN;
-                    const int kb1 = kb0 + Chunk<FMT>::CH < nkb ? kb0 + Chunk<FMT>::CH : nkb;
+                    const int kb1 = kb0 + Chunk<FMT>::CH < kb_hi ? kb0 + Chunk<FMT>::CH : kb_hi;
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!wait_bar(FULL(stage), phase, abort_flag, args.status, args.wait_ns)) {
                             ok = false;
@@ -553,17 +630,18 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
         uint32_t buf_phase = 0;
         bool ok = true;
         for (int t = blockIdx.x; ok && t < args.total_items; t += gridDim.x) {
-            int e, I, J, nkb;
+            int e, I, J, nkb, kb_lo = 0, kb_hi, part = -1;
             const TcProblem *pbp = nullptr;
             if constexpr (GEMM) {
                 gemm_item(args.gemm, t, e, I, J);
                 nkb = args.gemm.nkb;
+                kb_hi = nkb;
             } else {
-                pbp = &item_of(args, t, e, I, J);
+                pbp = &item_of<SPLIT>(args, t, e, I, J, kb_lo, kb_hi, part);
                 nkb = pbp->nkb;
             }
             if constexpr (!GEMM) {
-                if (nkb <= Chunk<FMT>::CH) {
+                if (part < 0 && nkb <= Chunk<FMT>::CH) {
                     // The whole K range is one chunk (short windows, Grams over
                     // trials): stream the accumulators from TMEM eight columns
                     // at a time straight into the stores, instead of holding
@@ -621,7 +699,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
             float sre[32], sim[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) { sre[c] = 0.f; sim[c] = 0.f; }
-            for (int kb0 = 0; kb0 < nkb; kb0 += Chunk<FMT>::CH) {
+            for (int kb0 = kb_lo; kb0 < kb_hi; kb0 += Chunk<FMT>::CH) {
                 if (!wait_bar(TFULL(buf), buf_phase, abort_flag, args.status, args.wait_ns)) {
                     ok = false;
                     break;
@@ -646,6 +724,21 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                 if (++buf == 2) { buf = 0; buf_phase ^= 1u; }
             }
             if (!ok) break;
+            if constexpr (SPLIT) {
+                // a split part: blocks below a diagonal tile's diagonal store
+                // nothing; the others go through the tile's slots
+                if (part >= 0) {
+                    if (I == J && q > cq) continue;
+                    const SplitPart &pr = args.split.parts[part];
+                    // checked builds: the part's slots and counter exist
+                    if (!PLV_IN_BOUNDS(pr.s >= 0 && pr.s < pr.S && pr.slot - pr.s >= 0 &&
+                                       pr.slot - pr.s + pr.S <= args.split.nslots &&
+                                       pr.tile >= 0 && pr.tile < args.split.ntiles))
+                        continue;
+                    if (!split_last(args.split, pr, q * 4 + cq, row, cq, lane, sre, sim))
+                        continue;
+                }
+            }
             const int i = I * TM + row;
             if constexpr (GEMM) {
                 // the complex tile, scaled, as planar FP32 rows [e N + i][2][ld]
@@ -747,10 +840,13 @@ static cudaError_t launch_tc(const Handle *h, cudaStream_t s, TcArgs a) {
     a.stall = take_fault(PLV_FAULT_STALL) ? 1 : 0;
     const int grid = a.total_items < h->num_sms ? a.total_items : h->num_sms;
     const bool fp16 = h->prec == PLV_PREC_FP16X3;
-    auto kern = fp16 ? k_gram_tc<0u, false> : k_gram_tc<1u, false>;
-    static LaunchSetup ls16, ls_bf;
+    const bool split = a.items && a.split.ntiles > 0;
+    auto kern = split ? (fp16 ? k_gram_tc<0u, false, true> : k_gram_tc<1u, false, true>)
+                      : (fp16 ? k_gram_tc<0u, false> : k_gram_tc<1u, false>);
+    static LaunchSetup ls16, ls_bf, ls16s, ls_bfs;
     int per_sm = 0;
-    cudaError_t e = setup_once(fp16 ? ls16 : ls_bf, kern, NTHREADS, SMEM_BYTES, per_sm);
+    cudaError_t e = setup_once(split ? (fp16 ? ls16s : ls_bfs) : (fp16 ? ls16 : ls_bf), kern,
+                               NTHREADS, SMEM_BYTES, per_sm);
     if (e != cudaSuccess) return e;
     kern<<<grid, NTHREADS, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
@@ -759,6 +855,7 @@ static cudaError_t launch_tc(const Handle *h, cudaStream_t s, TcArgs a) {
 cudaError_t launch_gram_tc_windows(const Handle *h, cudaStream_t s, const void *P, int batch,
                                    int N, int T, int t0, int W, int hop, int nw, GramOut out) {
     TcArgs a;
+    a.split = TcSplit{};
     a.single = make_tc_window_problem(P, batch, N, T, t0, W, hop, nw, out);
     a.single.raster = h->gram_raster;
     a.probs = nullptr;
@@ -774,6 +871,7 @@ cudaError_t launch_gram_tc_windows(const Handle *h, cudaStream_t s, const void *
 
 cudaError_t launch_gemm_tc(const Handle *h, cudaStream_t s, const TcGemm &g, int batch) {
     TcArgs a;
+    a.split = TcSplit{};
     a.single = TcProblem{};
     a.probs = nullptr;
     a.items = nullptr;
@@ -800,6 +898,7 @@ cudaError_t launch_gemm_tc(const Handle *h, cudaStream_t s, const TcGemm &g, int
 cudaError_t launch_gram_tc(const Handle *h, cudaStream_t s, const void *P, int batch,
                            int N, int T, GramOut out) {
     TcArgs a;
+    a.split = TcSplit{};
     a.single = make_tc_problem(P, batch, N, T, out);
     a.single.raster = h->gram_raster;
     a.probs = nullptr;
@@ -828,11 +927,12 @@ cudaError_t launch_zero_group_diag(cudaStream_t s, const TcProblem *probs, int n
 }
 
 cudaError_t launch_gram_tc_group(const Handle *h, cudaStream_t s, const TcProblem *probs,
-                                 const int4 *items, int nitems) {
+                                 const int4 *items, int nitems, const TcSplit &split) {
     TcArgs a;
     a.single = TcProblem{};
     a.probs = probs;
     a.items = items;
+    a.split = split;
     a.total_items = nitems;
     a.status = h->status;
     a.wait_ns = h->wait_ns;

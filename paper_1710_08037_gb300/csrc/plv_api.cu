@@ -691,6 +691,11 @@ plv_status plv_group_create(plv_handle *hp, const plv_problem *probs, int nprob,
         o.vec_ok = (q.N % 4 == 0) && !((uintptr_t)o.plv % 16) && !((uintptr_t)o.iplv % 16) &&
                    !((uintptr_t)o.ciplv % 16) && !((uintptr_t)o.C % 16);
         const TcProblem tp = make_tc_problem(q.P, q.batch, q.N, q.T, o);
+        if (tp.nrb > 0xffff) {  // tile coordinates are 16-bit in the launch list
+            delete g;
+            return fail(PLV_ERR_UNSUPPORTED, "plv_group_create: problem %d N = %d too large", p,
+                        q.N);
+        }
         const int pid = (int)dp.size();
         dp.push_back(tp);
         for (int e = 0; e < q.batch; ++e)
@@ -716,22 +721,22 @@ plv_status plv_group_create(plv_handle *hp, const plv_problem *probs, int nprob,
     g->dp_host = dp;
     g->items_host = items;
     g->nprob = (int)dp.size();
-    g->nitems = (int)items.size();
+    g->ntiles = (int)items.size();
+    g->nitems = g->ntiles;
     if (h.prec != PLV_PREC_FP32 && g->nprob > 0) {
         DeviceGuard guard(h.device);
         plv_status st = check_alloc(dev_malloc(&g->probs, sizeof(TcProblem) * dp.size()),
                                    "plv_group_create: descriptors");
         if (st == PLV_OK)
-            st = check_alloc(dev_malloc(&g->items, sizeof(int4) * items.size()),
-                            "plv_group_create: tile list");
-        if (st == PLV_OK)
             st = check_cuda(cudaMemcpy(g->probs, dp.data(), sizeof(TcProblem) * dp.size(),
                                        cudaMemcpyHostToDevice),
                             "plv_group_create: upload descriptors");
-        if (st == PLV_OK)
-            st = check_cuda(cudaMemcpy(g->items, items.data(), sizeof(int4) * items.size(),
-                                       cudaMemcpyHostToDevice),
-                            "plv_group_create: upload tiles");
+        if (st == PLV_OK && g->ntiles > 0) {
+            // the default launch list: longest first, no tile split
+            const GramList list = gram_list(dp, items, gram_chunk_kb(h.prec), h.num_sms, g->cfg);
+            st = upload_list(list, nullptr, &g->items, &g->split);
+            if (st == PLV_OK) g->nitems = (int)list.items.size();
+        }
         if (st != PLV_OK) {
             plv_group_destroy(g);
             return st;
@@ -762,8 +767,16 @@ plv_status plv_gram_grouped(plv_handle *hp, void *stream, const plv_group *g) {
                                    "plv_gram_grouped: clear diag");
         if (st != PLV_OK) return st;
     }
-    return PLV_CHECK_LAUNCH(launch_gram_tc_group(&hp->h, s, g->probs, g->items, g->nitems),
-                      "plv_gram_grouped launch");
+    if (g->split.ntiles > 0) {
+        // split tiles count their chunks from zero in every launch
+        plv_status st = check_cuda(cudaMemsetAsync(g->split.counters, 0,
+                                                   sizeof(int) * 16 * (size_t)g->split.ntiles, s),
+                                   "plv_gram_grouped: split counters");
+        if (st != PLV_OK) return st;
+    }
+    return PLV_CHECK_LAUNCH(
+        launch_gram_tc_group(&hp->h, s, g->probs, g->items, g->nitems, g->split),
+        "plv_gram_grouped launch");
 }
 
 plv_status plv_analytic_grouped(plv_handle *hp, void *stream, const plv_group *g) {
@@ -786,7 +799,7 @@ plv_status plv_group_destroy(plv_group *g) {
         if (g->probs || g->items || g->k1_descs || g->k1_items || !g->retired.empty())
             cudaDeviceSynchronize();
         if (g->probs) cudaFree(g->probs);
-        if (g->items) cudaFree(g->items);
+        free_list(g->items, g->split);
         if (g->k1_descs) cudaFree(g->k1_descs);
         if (g->k1_items) cudaFree(g->k1_items);
         for (void *p : g->retired)

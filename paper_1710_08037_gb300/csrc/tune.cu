@@ -53,19 +53,22 @@ void k1_layout(const std::vector<K1Desc> &descs, const std::map<int, int> &cls,
     }
 }
 
-std::vector<int4> gram_order(const std::vector<TcProblem> &dp, const std::vector<int4> &sorted,
-                             int schedule, int G, int tile_cost) {
-    if (schedule == kSchedLongestFirst || G <= 1 || (int64_t)sorted.size() <= G) return sorted;
+std::vector<int64_t> gram_order(const std::vector<int> &cost, int schedule, int G,
+                                int tile_cost) {
+    const int64_t n = (int64_t)cost.size();
+    std::vector<int64_t> out(n);
+    for (int64_t i = 0; i < n; ++i) out[i] = i;
+    if (schedule == kSchedLongestFirst || G <= 1 || n <= G) return out;
     // Balanced rounds: deal the longest-first list in rounds of G items, each
     // round's items (longest first) to the CTAs with the least accumulated
-    // cost (nkb + tile_cost per tile).  A CTA gets exactly one item per full
-    // round, so the deal is a permutation within each round.  The partial
-    // last round goes to the least-loaded CTAs, which are then numbered
-    // 0 .. rem - 1 so that the round-robin launch gives them those slots.
-    const int64_t n = (int64_t)sorted.size();
+    // cost (K blocks + tile_cost per item).  A CTA gets exactly one item per
+    // full round, so the deal is a permutation within each round.  The
+    // partial last round goes to the least-loaded CTAs, which are then
+    // numbered 0 .. rem - 1 so that the round-robin launch gives them those
+    // slots.
     const int64_t rounds = n / G, rem = n % G;
     std::vector<int64_t> load(G, 0);
-    std::vector<std::vector<int64_t>> mine(G);  // per virtual CTA: indices into sorted
+    std::vector<std::vector<int64_t>> mine(G);  // per virtual CTA: indices into the list
     std::vector<int> ctas(G);
     for (int b = 0; b < G; ++b) ctas[b] = b;
     for (int64_t r = 0; r <= rounds; ++r) {
@@ -77,7 +80,7 @@ std::vector<int4> gram_order(const std::vector<TcProblem> &dp, const std::vector
             const int b = ctas[k];
             const int64_t idx = base + k;
             mine[b].push_back(idx);
-            load[b] += dp[sorted[idx].x].nkb + tile_cost;
+            load[b] += cost[idx] + tile_cost;
         }
     }
     // number the CTAs: those holding a last-round item first
@@ -88,11 +91,177 @@ std::vector<int4> gram_order(const std::vector<TcProblem> &dp, const std::vector
         return mine[a].size() > mine[b].size();
     });
     for (int k = 0; k < G; ++k) label[by_len[k]] = k;
-    std::vector<int4> out(n);
     for (int b = 0; b < G; ++b)
-        for (size_t k = 0; k < mine[b].size(); ++k)
-            out[(int64_t)k * G + label[b]] = sorted[mine[b][k]];
+        for (size_t k = 0; k < mine[b].size(); ++k) out[(int64_t)k * G + label[b]] = mine[b][k];
     return out;
+}
+
+void split_plan(const std::vector<int> &nkb, int chunk, int G, int f, std::vector<int> &parts) {
+    parts.assign(nkb.size(), 1);
+    if (f <= 0 || G <= 0 || chunk <= 0) return;
+    int64_t W = 0;
+    for (int k : nkb) W += k;
+    // a tile longer than L runs as parts of about L: the grid's fair share
+    // / f, but at least kMinPartKb (a part's partial sums cost a 128 KB
+    // round trip through L2) and a chunk
+    const int64_t share = (W + (int64_t)G * f - 1) / ((int64_t)G * f);
+    const int64_t L = std::max<int64_t>(std::max<int64_t>(chunk, kMinPartKb), share);
+    std::vector<int> order(nkb.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nkb[a] > nkb[b]; });
+    int64_t slots = 0;
+    for (int i : order) {
+        const int64_t n = nkb[i];
+        if (n <= L) break;
+        const int64_t nch = (n + chunk - 1) / chunk;
+        const int S = (int)std::min<int64_t>((n + L - 1) / L, nch);
+        if (S < 2) continue;
+        if (slots + S > kMaxSplitSlots) break;  // longest tiles first while slots last
+        slots += S;
+        parts[i] = S;
+    }
+}
+
+void part_range(int nkb, int chunk, int S, int s, int &lo, int &hi) {
+    const int64_t nch = (nkb + chunk - 1) / chunk;
+    lo = (int)(chunk * ((int64_t)s * nch / S));
+    hi = (int)std::min<int64_t>(nkb, chunk * ((int64_t)(s + 1) * nch / S));
+}
+
+GramList gram_list(const std::vector<TcProblem> &dp, const std::vector<int4> &tiles, int chunk,
+                   int num_sms, const GroupConfig &cfg) {
+    GramList L;
+    std::vector<int> nkb(tiles.size());
+    for (size_t i = 0; i < tiles.size(); ++i) nkb[i] = dp[tiles[i].x].nkb;
+    std::vector<int> S;
+    split_plan(nkb, chunk, num_sms, cfg.gram_split, S);
+    // (tile, part) units; the parts of a tile get consecutive part numbers
+    struct Unit {
+        int tile, part, len;
+    };
+    std::vector<Unit> units;
+    units.reserve(tiles.size());
+    for (size_t i = 0; i < tiles.size(); ++i) {
+        if (S[i] == 1) {
+            units.push_back({(int)i, -1, nkb[i]});
+            continue;
+        }
+        for (int s = 0; s < S[i]; ++s) {
+            SplitPart p{};
+            part_range(nkb[i], chunk, S[i], s, p.kb_lo, p.kb_hi);
+            p.tile = L.ntiles;
+            p.slot = L.nslots + s;
+            p.s = s;
+            p.S = S[i];
+            units.push_back({(int)i, (int)L.parts.size(), p.kb_hi - p.kb_lo});
+            L.parts.push_back(p);
+        }
+        L.nslots += S[i];
+        ++L.ntiles;
+    }
+    // longest first, then the schedule
+    std::stable_sort(units.begin(), units.end(),
+                     [](const Unit &a, const Unit &b) { return a.len > b.len; });
+    std::vector<int> cost(units.size());
+    for (size_t k = 0; k < units.size(); ++k) cost[k] = units[k].len;
+    const int G = (int64_t)units.size() < num_sms ? (int)units.size() : num_sms;
+    const std::vector<int64_t> order = gram_order(cost, cfg.gram_schedule, G, cfg.gram_tile_cost);
+    L.items.resize(units.size());
+    for (size_t k = 0; k < units.size(); ++k) {
+        const Unit &u = units[order[k]];
+        const int4 &t = tiles[u.tile];
+        L.items[k] = make_int4(t.x, t.y, t.z | (t.w << 16), u.part + 1);
+    }
+    return L;
+}
+
+bool covers(const std::vector<TcProblem> &dp, const std::vector<int4> &tiles,
+            const GramList &list) {
+    // every tile's K range, as the union of its entries' ranges, exactly once
+    std::map<std::tuple<int, int, int, int>, std::vector<std::pair<int, int>>> got;
+    for (const int4 &it : list.items) {
+        const int I = it.z & 0xffff, J = (int)((unsigned)it.z >> 16);
+        if (it.x < 0 || it.x >= (int)dp.size()) return false;
+        int lo = 0, hi = dp[it.x].nkb;
+        if (it.w > 0) {
+            if (it.w - 1 >= (int)list.parts.size()) return false;
+            const SplitPart &p = list.parts[it.w - 1];
+            if (p.s < 0 || p.s >= p.S || p.slot - p.s < 0 || p.slot - p.s + p.S > list.nslots ||
+                p.tile < 0 || p.tile >= list.ntiles)
+                return false;
+            lo = p.kb_lo;
+            hi = p.kb_hi;
+        }
+        got[std::make_tuple(it.x, it.y, I, J)].push_back({lo, hi});
+    }
+    if (got.size() != tiles.size()) return false;
+    for (const int4 &t : tiles) {
+        auto f = got.find(std::make_tuple(t.x, t.y, t.z, t.w));
+        if (f == got.end()) return false;
+        auto r = f->second;
+        std::sort(r.begin(), r.end());
+        int at = 0;
+        for (auto &pr : r) {
+            if (pr.first != at || pr.second <= pr.first) return false;
+            at = pr.second;
+        }
+        if (at != dp[t.x].nkb) return false;
+    }
+    return true;
+}
+
+plv_status upload_list(const GramList &list, cudaStream_t s, int4 **items, TcSplit *split) {
+    *items = nullptr;
+    *split = TcSplit{};
+    int4 *di = nullptr;
+    SplitPart *dparts = nullptr;
+    float *dslots = nullptr;
+    int *dcnt = nullptr;
+    plv_status st = check_alloc(dev_malloc(&di, sizeof(int4) * std::max<size_t>(list.items.size(), 1)),
+                                "gram work list");
+    if (st == PLV_OK && !list.parts.empty())
+        st = check_alloc(dev_malloc(&dparts, sizeof(SplitPart) * list.parts.size()),
+                         "split parts");
+    if (st == PLV_OK && list.nslots > 0)
+        st = check_alloc(dev_malloc(&dslots, sizeof(float) * (size_t)kTileFloats * list.nslots),
+                         "split slots");
+    if (st == PLV_OK && list.ntiles > 0)
+        st = check_alloc(dev_malloc(&dcnt, sizeof(int) * 16 * (size_t)list.ntiles),
+                         "split counters");
+    if (st == PLV_OK)
+        st = check_cuda(cudaMemcpyAsync(di, list.items.data(), sizeof(int4) * list.items.size(),
+                                        cudaMemcpyHostToDevice, s),
+                        "gram work list upload");
+    if (st == PLV_OK && dparts)
+        st = check_cuda(cudaMemcpyAsync(dparts, list.parts.data(),
+                                        sizeof(SplitPart) * list.parts.size(),
+                                        cudaMemcpyHostToDevice, s),
+                        "split parts upload");
+    if (st == PLV_OK && dcnt)
+        st = check_cuda(cudaMemsetAsync(dcnt, 0, sizeof(int) * 16 * (size_t)list.ntiles, s),
+                        "split counters");
+    if (st == PLV_OK) st = check_cuda(cudaStreamSynchronize(s), "gram work list upload");
+    if (st != PLV_OK) {
+        if (di) cudaFree(di);
+        if (dparts) cudaFree(dparts);
+        if (dslots) cudaFree(dslots);
+        if (dcnt) cudaFree(dcnt);
+        return st;
+    }
+    *items = di;
+    split->parts = dparts;
+    split->partials = dslots;
+    split->counters = dcnt;
+    split->nslots = list.nslots;
+    split->ntiles = list.ntiles;
+    return PLV_OK;
+}
+
+void free_list(int4 *items, const TcSplit &split) {
+    if (items) cudaFree(items);
+    if (split.parts) cudaFree((void *)split.parts);
+    if (split.partials) cudaFree(split.partials);
+    if (split.counters) cudaFree(split.counters);
 }
 
 namespace {
@@ -155,18 +324,6 @@ plv_status upload(const std::vector<T> &v, T **out, cudaStream_t s) {
     return PLV_OK;
 }
 
-// Whether a schedule holds every tile of the plan exactly once.
-bool same_tiles(std::vector<int4> a, std::vector<int4> b) {
-    if (a.size() != b.size()) return false;
-    auto key = [](const int4 &v) { return std::make_tuple(v.x, v.y, v.z, v.w); };
-    auto less = [&](const int4 &u, const int4 &v) { return key(u) < key(v); };
-    std::sort(a.begin(), a.end(), less);
-    std::sort(b.begin(), b.end(), less);
-    for (size_t i = 0; i < a.size(); ++i)
-        if (key(a[i]) != key(b[i])) return false;
-    return true;
-}
-
 // CTAs per SM a class launch gets from its register budget alone.
 int k1_default_per_sm(int c) {
     const int v = 65536 / (kConvRegs * conv_class_threads(c));
@@ -190,18 +347,23 @@ plv_status apply_config(const Handle &h, plv_group &g, const GroupConfig &cfg, c
         kg.items = d;
         g.k1 = kg;
     }
-    if (g.prec != PLV_PREC_FP32 && g.nitems > 0) {
-        const std::vector<int4> order =
-            gram_order(g.dp_host, g.items_host, cfg.gram_schedule,
-                       gram_group_grid(h, g.nitems), cfg.gram_tile_cost);
-        if (!same_tiles(order, g.items_host))
-            return fail(PLV_ERR_NUMERIC, "plv_group_tune: internal error: schedule is not a "
-                                         "permutation of the tile list");
+    if (g.prec != PLV_PREC_FP32 && g.ntiles > 0) {
+        const GramList list =
+            gram_list(g.dp_host, g.items_host, gram_chunk_kb(g.prec), h.num_sms, cfg);
+        if (!covers(g.dp_host, g.items_host, list))
+            return fail(PLV_ERR_NUMERIC, "plv_group_tune: internal error: the launch list does "
+                                         "not cover every tile once");
         int4 *d = nullptr;
-        plv_status st = upload(order, &d, s);
+        TcSplit sp;
+        plv_status st = upload_list(list, s, &d, &sp);
         if (st != PLV_OK) return st;
         g.retired.push_back(g.items);
+        g.retired.push_back((void *)g.split.parts);
+        g.retired.push_back(g.split.partials);
+        g.retired.push_back(g.split.counters);
         g.items = d;
+        g.split = sp;
+        g.nitems = (int)list.items.size();
     }
     g.cfg = cfg;
     return PLV_OK;
@@ -253,11 +415,29 @@ extern "C" plv_status plv_group_tune(plv_handle *hp, void *stream, plv_group *g,
     auto run_k1 = [&](const K1Group &kg) {
         return launch_analytic_group(&h, s, g->k1_dtype, kg);
     };
-    auto run_gram = [&](const int4 *items) {
+    auto run_gram = [&](const int4 *items, int n, const TcSplit &sp) {
         cudaError_t e = cudaSuccess;
         if (g->any_diag) e = launch_zero_group_diag(s, g->probs, g->nprob);
-        if (e == cudaSuccess) e = launch_gram_tc_group(&h, s, g->probs, items, g->nitems);
+        if (e == cudaSuccess && sp.ntiles > 0)
+            e = cudaMemsetAsync(sp.counters, 0, sizeof(int) * 16 * (size_t)sp.ntiles, s);
+        if (e == cudaSuccess) e = launch_gram_tc_group(&h, s, g->probs, items, n, sp);
         return e;
+    };
+    // the Gram's launch list under configuration c, timed
+    auto time_gram = [&](const GroupConfig &c, float *ms) {
+        const GramList list =
+            gram_list(g->dp_host, g->items_host, gram_chunk_kb(g->prec), h.num_sms, c);
+        if (!covers(g->dp_host, g->items_host, list))
+            return fail(PLV_ERR_NUMERIC, "plv_group_tune: internal error: the launch list does "
+                                         "not cover every tile once");
+        int4 *d = nullptr;
+        TcSplit sp;
+        plv_status st2 = upload_list(list, s, &d, &sp);
+        if (st2 != PLV_OK) return st2;
+        st2 = time_median(s, reps, [&] { return run_gram(d, (int)list.items.size(), sp); }, ms);
+        cudaStreamSynchronize(s);
+        free_list(d, sp);
+        return st2;
     };
 
     if (!cached && g->has_k1) {
@@ -358,36 +538,52 @@ extern "C" plv_status plv_group_tune(plv_handle *hp, void *stream, plv_group *g,
     }
 
     if (!cached && gram) {
-        // the schedule of the tile list; P holds valid phasors (step 1 wrote
-        // them, or the caller did)
-        const int4 *cur = g->items;
-        st = time_median(s, reps, [&] { return run_gram(cur); }, &r.gram_ms_default);
+        // P holds valid phasors (step 1 wrote them, or the caller did).
+        // 1. the default: longest first, no tile split
+        GroupConfig best = cfg;
+        best.gram_schedule = kSchedLongestFirst;
+        best.gram_tile_cost = 0;
+        best.gram_split = 0;
+        st = time_gram(best, &r.gram_ms_default);
         ++r.timed_configs;
         float best_ms = r.gram_ms_default;
-        const int G = gram_group_grid(h, g->nitems);
+        // 2. the schedule: balanced rounds under per-tile costs
+        const GroupConfig plain = best;
         for (int cost : {0, 8, 32}) {
             if (st != PLV_OK) break;
-            const std::vector<int4> order =
-                gram_order(g->dp_host, g->items_host, kSchedBalanced, G, cost);
-            if (!same_tiles(order, g->items_host)) {
-                st = fail(PLV_ERR_NUMERIC, "plv_group_tune: internal error: schedule is not "
-                                           "a permutation of the tile list");
-                break;
-            }
-            int4 *d = nullptr;
-            st = upload(order, &d, s);
-            if (st != PLV_OK) break;
+            GroupConfig c = plain;
+            c.gram_schedule = kSchedBalanced;
+            c.gram_tile_cost = cost;
             float ms = 0.f;
-            st = time_median(s, reps, [&] { return run_gram(d); }, &ms);
+            st = time_gram(c, &ms);
             ++r.timed_configs;
-            cudaStreamSynchronize(s);
-            cudaFree(d);
             if (st == PLV_OK && ms < 0.99f * best_ms) {
                 best_ms = ms;
-                cfg.gram_schedule = kSchedBalanced;
-                cfg.gram_tile_cost = cost;
+                best = c;
             }
         }
+        // 3. split K of the longest tiles, in the chosen schedule (factors
+        //    whose split plan splits no tile are the unsplit list: skipped)
+        const GroupConfig sched = best;
+        const float sched_ms = best_ms;
+        for (int f : {1, 2, 4}) {
+            if (st != PLV_OK) break;
+            GroupConfig c = sched;
+            c.gram_split = f;
+            if (gram_list(g->dp_host, g->items_host, gram_chunk_kb(g->prec), h.num_sms, c)
+                    .ntiles == 0)
+                continue;
+            float ms = 0.f;
+            st = time_gram(c, &ms);
+            ++r.timed_configs;
+            if (st == PLV_OK && ms < 0.97f * sched_ms && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        cfg.gram_schedule = best.gram_schedule;
+        cfg.gram_tile_cost = best.gram_tile_cost;
+        cfg.gram_split = best.gram_split;
         r.gram_ms_tuned = best_ms;
         if (st != PLV_OK) return st;
     }
@@ -405,6 +601,8 @@ extern "C" plv_status plv_group_tune(plv_handle *hp, void *stream, plv_group *g,
     }
     r.gram_schedule = cfg.gram_schedule;
     r.gram_tile_cost = cfg.gram_tile_cost;
+    r.gram_split = cfg.gram_split;
+    r.gram_split_tiles = g->split.ntiles;
     r.cached = cached ? 1 : 0;
     if (res) *res = r;
     return PLV_OK;
@@ -412,7 +610,8 @@ extern "C" plv_status plv_group_tune(plv_handle *hp, void *stream, plv_group *g,
 
 extern "C" plv_status plv_group_configure(plv_handle *hp, void *stream, plv_group *g,
                                           int k1_widen, const int *k1_per_sm,
-                                          int gram_schedule, int gram_tile_cost) {
+                                          int gram_schedule, int gram_tile_cost,
+                                          int gram_split) {
     PLV_RANGE("plv_group_configure");
     if (!hp || !g) return fail(PLV_ERR_INVALID, "plv_group_configure: NULL argument");
     Handle &h = hp->h;
@@ -426,6 +625,9 @@ extern "C" plv_status plv_group_configure(plv_handle *hp, void *stream, plv_grou
                     gram_schedule);
     if (gram_tile_cost < 0 || gram_tile_cost > (1 << 20))
         return fail(PLV_ERR_INVALID, "plv_group_configure: gram_tile_cost = %d", gram_tile_cost);
+    if (gram_split < 0 || gram_split > kMaxSplitFactor)
+        return fail(PLV_ERR_INVALID, "plv_group_configure: gram_split = %d (0..%d)", gram_split,
+                    kMaxSplitFactor);
     GroupConfig cfg;
     for (int c = 0; c < kConvClasses; ++c) {
         const int v = k1_per_sm ? k1_per_sm[c] : 0;
@@ -440,6 +642,7 @@ extern "C" plv_status plv_group_configure(plv_handle *hp, void *stream, plv_grou
         }
     cfg.gram_schedule = gram_schedule;
     cfg.gram_tile_cost = gram_tile_cost;
+    cfg.gram_split = gram_split;
     DeviceGuard guard(h.device);
     if (!guard.ok) return fail(PLV_ERR_CUDA, "cannot select device %d", h.device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -449,4 +652,19 @@ extern "C" plv_status plv_group_configure(plv_handle *hp, void *stream, plv_grou
     plv_status st = check_cuda(cudaDeviceSynchronize(), "plv_group_configure: synchronise");
     if (st != PLV_OK) return st;
     return apply_config(h, *g, cfg, s);
+}
+
+extern "C" plv_status plv_gram_split_plan(const int *nkb, int ntiles, int chunk, int grid,
+                                          int split, int *parts) {
+    if (ntiles < 0 || (ntiles > 0 && (!nkb || !parts)))
+        return fail(PLV_ERR_INVALID, "plv_gram_split_plan: bad tile list");
+    if (chunk < 1 || grid < 1 || split < 0 || split > kMaxSplitFactor)
+        return fail(PLV_ERR_INVALID, "plv_gram_split_plan: chunk %d, grid %d, split %d", chunk,
+                    grid, split);
+    std::vector<int> k(nkb, nkb + ntiles), S;
+    for (int v : k)
+        if (v < 1) return fail(PLV_ERR_INVALID, "plv_gram_split_plan: tile of %d K blocks", v);
+    split_plan(k, chunk, grid, split, S);
+    for (int i = 0; i < ntiles; ++i) parts[i] = S[i];
+    return PLV_OK;
 }

@@ -81,3 +81,27 @@ def test_checked_backward(hc):
     torch.cuda.synchronize()
     assert hc.check_status() == 0
     assert torch.isfinite(grad).all()
+
+
+def test_checked_split_k(hc):
+    """Split-K parts (long tiles of a grouped plan) under the bounds checks."""
+    if hc.precision == 0:
+        pytest.skip("split K is a tensor-core Gram schedule")
+    prec = {1: "bf16x3", 2: "fp16x3"}[hc.precision]
+    probs, xs = [], []
+    for N, T in ((68, 10000), (130, 4096), (3, 7000)):
+        x = synth.bandlimited(1, N, T, seed=N + 3 * T, device="cuda")
+        hc.prepare(T)
+        xs.append(x)
+        probs.append({"x": x, "P": hc.empty_phasors(1, N, T), "batch": 1, "N": N, "T": T})
+    grp = hc.plv_group_create(probs)
+    hc.plv_group_configure(grp, gram_split=4)
+    hc.plv_analytic_grouped(grp)
+    hc.plv_gram_grouped(grp)
+    torch.cuda.synchronize()
+    assert hc.check_status() == 0
+    for q, x in zip(grp.problems, xs):
+        ref = oracle.connectivity(x[0].double().cpu().numpy())
+        compare({k: q[k][0].double().cpu().numpy() for k in ("plv", "iplv", "ciplv")}, ref,
+                TOL[prec])
+    grp.close()
