@@ -439,6 +439,7 @@ def run_ours(args):
                    BACKWARD: backward_measure(args, dev, dist, rank, world)}
         if rank == 0:
             configs["tones-N64-T2048"] = parity_measure(args, dev)
+            configs["grouped-small-N-long-T"] = split_k_measure(args, dev)
 
     if rank == 0:
         line = {
@@ -601,6 +602,81 @@ def grouped_measure(args, dev, dist, rank, world):
                   "frac_of_hbm": k1b / (k1_ms / 1e3) / 1e9 / float(peaks["hbm_gbs"])},
            "gpu_launches": (k1_launches + 1) * args.steps,
            "clocks": clk, "device_status": device_status}
+    grp.close()
+    h.close()
+    del probs
+    torch.cuda.empty_cache()
+    return out
+
+
+def split_k_measure(args, dev, nsub=8):
+    """The corner of the uneven batch where few long tiles leave the grid
+    idle: nsub subjects with N in 68..300 and T in 5000..10000, five bands
+    each, on one grouped plan.  Times the grouped Gram (CUDA events, inputs
+    resident) unsplit and with each split-K factor, and what the autotuner
+    keeps; reports the largest output difference split vs unsplit."""
+    import numpy as np
+    import torch
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import synth
+
+    if args.precision == "fp32":
+        return None
+    h = plv.Handle(precision=args.precision, device=dev.index)
+    rng = np.random.default_rng(1014)
+    specs = []
+    for sj in range(nsub):
+        N, T = int(rng.integers(68, 301)), int(rng.integers(5000, 10001))
+        for b, band in enumerate(BANDS):
+            specs.append((N, T, band, 1014 * 1000 + sj * 5 + b))
+    probs = []
+    for (N, T, band, sd) in specs:
+        x = synth.bandlimited(1, N, T, seed=sd, band=band, device=dev)
+        h.prepare(T)
+        probs.append({"x": x, "P": h.empty_phasors(1, N, T), "batch": 1, "N": N, "T": T})
+    grp = h.plv_group_create(probs)
+    s = torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(reps=20):
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                h.plv_gram_grouped(grp)
+            a, b = ev(), ev()
+            a.record(s)
+            for _ in range(reps):
+                h.plv_gram_grouped(grp)
+            b.record(s)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    with torch.cuda.stream(s):
+        h.plv_analytic_grouped(grp)
+    times = {}
+    for f in (0, 1, 2, 4):
+        with torch.cuda.stream(s):
+            h.plv_group_configure(grp, gram_split=f)
+        times[f] = timed()
+        if f == 0:
+            ref = [q["plv"].clone() for q in probs]
+    diff = max(float((q["plv"] - r).abs().max()) for q, r in zip(probs, ref))
+    with torch.cuda.stream(s):
+        h.plv_group_configure(grp)
+        tune = h.plv_group_tune(grp, reps=3)
+    tuned = timed()
+    units = float(sum(N * N * T for (N, T, _, _) in specs))
+    out = {"metric": METRIC, "value": units / (tuned / 1e3), "unit": UNIT,
+           "ms_per_step": tuned,
+           "config": {"workload": "grouped-small-N-long-T", "problems": len(specs),
+                      "N": "68..300", "T": "5000..10000", "precision": args.precision,
+                      "what": "the grouped Gram alone (phasors resident)"},
+           "gram_ms_by_split_factor": {str(f): v for f, v in times.items()},
+           "speedup_of_tuned_over_unsplit": times[0] / tuned,
+           "autotune": {k: tune[k] for k in ("gram_schedule", "gram_tile_cost", "gram_split",
+                                             "gram_split_tiles", "gram_ms_default",
+                                             "gram_ms_tuned")},
+           "max_abs_plv_diff_split_vs_unsplit": diff,
+           "gpu_launches": 1, "device_status": h.plv_sync_status()}
     grp.close()
     h.close()
     del probs
@@ -865,7 +941,9 @@ def backward_measure(args, dev, dist, rank, world):
             "lower_bound_tflops_over_whole_backward":
                 gemm_flops * (3 if split else 1) / (bwd_ms / 1e3) / 1e12},
         "fp32_backward": fp32_bwd,
-        "gpu_launches": (2 + (6 if split else 4)) * args.steps,
+        # forward: K1, Gram; backward: recompute, S, contraction, adjoint (and
+        # the split P's padding rows when N % 128 != 0)
+        "gpu_launches": (2 + 4 + (1 if split and N % 128 else 0)) * args.steps,
         "clocks": clk, "device_status": hb.plv_sync_status()}
     hf.close()
     return line

@@ -27,6 +27,7 @@ struct K1Args {
     int N, T, log2T;
     int64_t ld;     // padded row length
     int64_t rows;
+    void *Ps = nullptr;  // kK1Prep only: P also in the BF16 split operand layout
 };
 
 // Launchers, defined in k_fwd.cu and instantiated there once per
@@ -308,17 +309,22 @@ struct FwdTask {
 
 // Backward preparation: the same analytic signal, stored as FP32 phasors
 // P[row][2][ld] and the reciprocal amplitude rinv[row][ld] = 1/|z| (0 where
-// |z| counts as 0), which the gradient of Eq. 4 needs.
-template <typename Tin>
+// |z| counts as 0), which the gradient of Eq. 4 needs; with SPLIT also as
+// BF16 hi + lo splits in the tiled operand layout at Ps (rows of N per
+// epoch), the B operand of the tensor-core contraction.
+template <typename Tin, bool SPLIT = false>
 struct PrepTask {
     const Tin *x;
     int64_t ldx;
     float *P;
     float *rinv;
     int64_t ld;
+    void *Ps;
+    int N;
     struct Rows {
         const Tin *x0, *x1;
         float *p0, *p1, *q0, *q1;  // phasor rows, reciprocal-amplitude rows
+        RowAddr<PLV_PREC_BF16X3> s0, s1;  // SPLIT: rows of the split layout
     };
     __device__ Rows rows(int64_t r0, bool v0, int64_t r1, bool v1) const {
         Rows rs;
@@ -328,50 +334,53 @@ struct PrepTask {
         rs.p1 = P + (v1 ? r1 : 0) * 2 * ld;
         rs.q0 = rinv + (v0 ? r0 : 0) * ld;
         rs.q1 = rinv + (v1 ? r1 : 0) * ld;
+        if constexpr (SPLIT) {
+            rs.s0 = row_addr<PLV_PREC_BF16X3>(v0 ? r0 : 0, N, ld);
+            rs.s1 = row_addr<PLV_PREC_BF16X3>(v1 ? r1 : 0, N, ld);
+        }
         return rs;
     }
-    __device__ void one(const Tin *xr, float *pr, float *qr, int m, float h,
-                        float floor2) const {
+    __device__ void one(const Tin *xr, float *pr, float *qr, const RowAddr<PLV_PREC_BF16X3> &sa,
+                        int m, float h, float floor2) const {
         float ri;
         const float2 p = unit_phasor_inv(ldx_f(xr + m), h, floor2, ri);
         pr[m] = p.x;
         pr[ld + m] = p.y;
         qr[m] = ri;
+        if constexpr (SPLIT) store_phasor<PLV_PREC_BF16X3>(Ps, sa, ld, m, p);
     }
     __device__ float2 load(const Rows &rs, int m) const {
         return make_float2(rs.x0 ? ldx_f(rs.x0 + m) : 0.f, rs.x1 ? ldx_f(rs.x1 + m) : 0.f);
     }
     __device__ void finish(const Rows &rs, int m, float h0, float h1, float floor2) const {
-        if (rs.x0) one(rs.x0, rs.p0, rs.q0, m, h0, floor2);
-        if (rs.x1) one(rs.x1, rs.p1, rs.q1, m, h1, floor2);
+        if (rs.x0) one(rs.x0, rs.p0, rs.q0, rs.s0, m, h0, floor2);
+        if (rs.x1) one(rs.x1, rs.p1, rs.q1, rs.s1, m, h1, floor2);
     }
     // eight consecutive samples m0 .. m0+7 (m0 % 8 == 0, m0 + 8 <= ld):
     // vector loads of x and 16-byte stores of both planes and of 1/|z|
     static constexpr bool kFinish8 = true;
-    __device__ void row8(const Tin *xr, float *pr, float *qr, int m0, const float (&h)[8],
-                         float floor2) const {
+    __device__ void row8(const Tin *xr, float *pr, float *qr, const RowAddr<PLV_PREC_BF16X3> &sa,
+                         int m0, const float (&h)[8], float floor2) const {
         if (!PLV_IN_BOUNDS(m0 >= 0 && (m0 & 7) == 0 && m0 + 8 <= ld)) return;
         float xv[8];
         load_x8(xr + m0, xv);
-        float re[8], im[8], ri[8];
+        float2 p[8];
+        float ri[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float2 p = unit_phasor_inv(xv[k], h[k], floor2, ri[k]);
-            re[k] = p.x;
-            im[k] = p.y;
-        }
+        for (int k = 0; k < 8; ++k) p[k] = unit_phasor_inv(xv[k], h[k], floor2, ri[k]);
         float4 *o = (float4 *)(pr + m0), *oi = (float4 *)(pr + ld + m0), *oq = (float4 *)(qr + m0);
-        o[0] = make_float4(re[0], re[1], re[2], re[3]);
-        o[1] = make_float4(re[4], re[5], re[6], re[7]);
-        oi[0] = make_float4(im[0], im[1], im[2], im[3]);
-        oi[1] = make_float4(im[4], im[5], im[6], im[7]);
+        o[0] = make_float4(p[0].x, p[1].x, p[2].x, p[3].x);
+        o[1] = make_float4(p[4].x, p[5].x, p[6].x, p[7].x);
+        oi[0] = make_float4(p[0].y, p[1].y, p[2].y, p[3].y);
+        oi[1] = make_float4(p[4].y, p[5].y, p[6].y, p[7].y);
         oq[0] = make_float4(ri[0], ri[1], ri[2], ri[3]);
         oq[1] = make_float4(ri[4], ri[5], ri[6], ri[7]);
+        if constexpr (SPLIT) store_phasor8<PLV_PREC_BF16X3>(Ps, sa, ld, m0, p);
     }
     __device__ void finish8(const Rows &rs, int m0, const float (&h0)[8], const float (&h1)[8],
                             float floor2) const {
-        if (rs.x0) row8(rs.x0, rs.p0, rs.q0, m0, h0, floor2);
-        if (rs.x1) row8(rs.x1, rs.p1, rs.q1, m0, h1, floor2);
+        if (rs.x0) row8(rs.x0, rs.p0, rs.q0, rs.s0, m0, h0, floor2);
+        if (rs.x1) row8(rs.x1, rs.p1, rs.q1, rs.s1, m0, h1, floor2);
     }
     static constexpr bool kPrefetch = true;
     __device__ void prefetch(int64_t r0, bool v0, int64_t r1, bool v1) const {
@@ -383,6 +392,10 @@ struct PrepTask {
     __device__ void pad(const Rows &rs, int m) const {
         if (rs.x0) { rs.p0[m] = 0.f; rs.p0[ld + m] = 0.f; rs.q0[m] = 0.f; }
         if (rs.x1) { rs.p1[m] = 0.f; rs.p1[ld + m] = 0.f; rs.q1[m] = 0.f; }
+        if constexpr (SPLIT) {
+            if (rs.x0) store_phasor<PLV_PREC_BF16X3>(Ps, rs.s0, ld, m, make_float2(0.f, 0.f));
+            if (rs.x1) store_phasor<PLV_PREC_BF16X3>(Ps, rs.s1, ld, m, make_float2(0.f, 0.f));
+        }
     }
 };
 

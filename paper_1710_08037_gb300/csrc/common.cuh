@@ -320,19 +320,21 @@ cudaError_t launch_analytic_pow2(const Handle *h, cudaStream_t s,
                                  int N, int log2T, int64_t ldx, void *P);
 // Zero the padding rows N .. NRB*128-1 of a split-precision phasor buffer.
 cudaError_t launch_zero_pad_rows(cudaStream_t s, void *P, int batch, int N, int T);
-// Backward preparation: FP32 phasors P[rows][2][ld] and rinv[rows][ld].
+// Backward preparation: FP32 phasors P[rows][2][ld] and rinv[rows][ld]; with
+// Ps, P also as BF16 splits in the tiled operand layout (rows of N per epoch).
 cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
                             int64_t rows, int log2T, int64_t ldx, float *P, float *rinv,
-                            int T, const ConvPlan *plan);
+                            int T, const ConvPlan *plan, void *Ps = nullptr, int N = 0);
 // K5: S = G + G^H, Gamma = S P / T, grad = Re Gamma_z - H{Im Gamma_z}.
 // tc_ops NULL: FP32 contraction on the CUDA cores with S FP32 planar
 // [batch][2][N][N]; else the tensor-core contraction with its split operands
-// (backward_tc_bytes bytes at tc_ops) and S unused.
+// (backward_tc_bytes bytes at tc_ops: S rows, then P in the split operand
+// layout, which the preparation wrote) and S unused.
 cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
                             int log2T, const float2 *C, const float *g1, const float *g2,
                             const float *g3, const float *P, const float *rinv, float *S,
                             float *Gm, float *grad, const ConvPlan *plan, void *tc_ops);
-// Bytes of the tensor-core backward's split operands (S rows, then conj(P)^T
+// Bytes of the tensor-core backward's split operands (S rows, then P's split
 // rows); *a_bytes receives the first part's size.
 size_t backward_tc_bytes(int batch, int N, int T, size_t *a_bytes);
 // Eq. 4 on a given analytic signal.
@@ -375,12 +377,15 @@ cudaError_t launch_gram_fp32_windows(const Handle *h, cudaStream_t s, const floa
                                      int N, int T, int t0, int W, int hop, int nw, GramOut out);
 // The backward pass's contraction on the tensor cores (BF16 split):
 // G[e][i][2][ld] = (1/T) sum_k S[e][i][k] P[e][k][t], from A = split rows of S
-// (row i, K = k; rows padded to nrb_a blocks of 128) and B = split rows of
-// conj(P)^T (row t, K = k; nrb_b blocks of 128 rows), both in the tiled split
-// layout with nkb blocks of 32 along k.  Every (I, J) tile of every epoch.
+// (row i, K = k; rows padded to nrb_a blocks of 128, nkb blocks of 32 along
+// k) and B = P's own split rows (row k, t contiguous: nrb_a blocks of 128
+// rows, nkb_t blocks of 32 along t), read by the MMA as an MN-major operand.
+// Tiles (I, J) of 128 rows i x 128 samples t, nrb_b = ceil(ld / 128) along t,
+// every tile of every epoch.
 struct TcGemm {
     const uint8_t *A, *B;
     int nrb_a, nrb_b, nkb, tpe;  // tpe = nrb_a * nrb_b tiles per epoch
+    int nkb_t;                   // 32-sample blocks along t of B's layout (ld / 32)
     int N;                       // valid rows i (and k)
     int64_t ld;                  // row length of G (valid t)
     float invT;

@@ -141,13 +141,13 @@ cudaError_t launch_analytic_group(const Handle *h, cudaStream_t s, plv_dtype dt,
 
 cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_dtype dt,
                             int64_t rows, int log2T, int64_t ldx, float *P, float *rinv,
-                            int T, const ConvPlan *plan) {
+                            int T, const ConvPlan *plan, void *Ps, int N) {
     if (plan) {
-        const K1Args a{x, ldx, P, rinv, 0, T, 0, padded_len(T), rows};
+        const K1Args a{x, ldx, P, rinv, N, T, 0, padded_len(T), rows, Ps};
         return dt == PLV_F32 ? k1_conv<float, kK1Prep>(h, s, a, *plan)
                              : k1_conv<double, kK1Prep>(h, s, a, *plan);
     }
-    const K1Args a{x, ldx, P, rinv, 0, T, log2T, (int64_t)1 << log2T, rows};
+    const K1Args a{x, ldx, P, rinv, N, T, log2T, (int64_t)1 << log2T, rows, Ps};
     return dt == PLV_F32 ? k1_pow2<float, kK1Prep>(h, s, a) : k1_pow2<double, kK1Prep>(h, s, a);
 }
 

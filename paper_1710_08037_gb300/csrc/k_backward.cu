@@ -17,7 +17,8 @@
 //     dL/dx = Re Gamma_z - H{Im Gamma_z}.
 //
 // Stages:
-//   1. recompute P and 1/|z| from x (the forward FFT task, fft.cuh), FP32;
+//   1. recompute P and 1/|z| from x (the forward FFT task, fft.cuh), FP32,
+//      and for split-precision handles P's BF16 splits in the operand layout;
 //   2. S = G + G^H from C and the upstream gradients, 32x32 tiles staged
 //      through shared memory for the transposed reads;
 //   3. Gamma = S P / T, the one dense contraction of the pass:
@@ -27,8 +28,9 @@
 //        blocks, double-buffered shared memory;
 //      - split-precision handles: the tensor-core kernel of the Gram in its
 //        GEMM mode (BF16 hi + lo splits, three products per term).  Stage 2
-//        then writes S as split rows (k_bwd_s_split) and k_bwd_pt_split
-//        writes conj(P)^T as split rows, so that both operands are K-major;
+//        then writes S as split rows (k_bwd_s_split, K-major A operand) and
+//        the MMA reads stage 1's split P rows (row k, t contiguous) as an
+//        MN-major B operand, so P is never transposed;
 //   4. BwdTask on the FFT engine: u = -Im(P) s, v = Re(P) s with
 //      s = Im(conj(P) Gamma) / |z|, then grad = u - H{v}.
 #include "fft.cuh"
@@ -148,35 +150,6 @@ k_bwd_s_split(const float2 *__restrict__ C, const float *__restrict__ g1,
     for (int yy = ty; yy < 32; yy += 8) {
         const float2 v = Sm[tx][yy];  // S(bi + tx, bk + yy)
         store_split_bf16(A, split_offset(b, bk + yy, bi + tx, NRB, NKB), make_float2(v.x, -v.y));
-    }
-}
-
-// conj(P)^T as the B operand: row t, K = k (rows k of P are channels), tiled
-// split layout with NRBT row blocks along t and NKB blocks of 32 along k.
-// P is FP32 planar [batch * N][2][ld]; t >= ld and k >= N are zeros.
-__global__ void __launch_bounds__(256)
-k_bwd_pt_split(const float *__restrict__ P, int N, int64_t ld, int64_t NRBT, int64_t NKB,
-               __nv_bfloat16 *__restrict__ B) {
-    __shared__ float2 tile[32][33];  // [k][t]
-    const int b = blockIdx.z;
-    const int64_t t0 = (int64_t)blockIdx.y * 32;
-    const int k0 = blockIdx.x * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int kk = ty; kk < 32; kk += 8) {
-        const int k = k0 + kk;
-        const int64_t t = t0 + tx;
-        float2 v = make_float2(0.f, 0.f);
-        if (k < N && t < ld) {
-            const float *row = P + ((int64_t)b * N + k) * 2 * ld;
-            v = make_float2(__ldg(row + t), __ldg(row + ld + t));
-        }
-        tile[kk][tx] = v;
-    }
-    __syncthreads();
-    for (int yy = ty; yy < 32; yy += 8) {
-        const float2 v = tile[tx][yy];  // P[k0 + tx][t0 + yy]
-        store_split_bf16(B, split_offset(b, t0 + yy, k0 + tx, NRBT, NKB),
-                         make_float2(v.x, -v.y));
     }
 }
 
@@ -371,7 +344,7 @@ struct BwdTask {
 size_t backward_tc_bytes(int batch, int N, int T, size_t *a_bytes) {
     const int64_t NKB = ((int64_t)N + kTileK - 1) / kTileK;
     const size_t a = (size_t)batch * row_blocks(N) * NKB * kBlockElems * 2;
-    const size_t b = (size_t)batch * row_blocks((int)padded_len(T)) * NKB * kBlockElems * 2;
+    const size_t b = (size_t)batch * row_blocks(N) * (padded_len(T) / kTileK) * kBlockElems * 2;
     if (a_bytes) *a_bytes = a;
     return a + b;
 }
@@ -387,24 +360,21 @@ cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, 
         size_t a_bytes = 0;
         backward_tc_bytes(batch, N, T, &a_bytes);
         __nv_bfloat16 *A = (__nv_bfloat16 *)tc_ops;
-        __nv_bfloat16 *B = (__nv_bfloat16 *)((uint8_t *)tc_ops + a_bytes);
+        const uint8_t *B = (const uint8_t *)tc_ops + a_bytes;  // stage 1 wrote it
         const int64_t NRB = row_blocks(N), NKB = ((int64_t)N + kTileK - 1) / kTileK;
-        const int64_t NRBT = row_blocks((int)ld);
+        const int64_t NRBT = (ld + 127) / 128;  // output tiles along t
         const unsigned nt = (unsigned)NKB;  // 32-tiles along i and along k
         dim3 sg(nt * (nt + 1) / 2, batch);
         k_bwd_s_split<<<sg, 256, 0, st>>>(C, g1, g2, g3, N, NRB, NKB, A);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        dim3 pg((unsigned)NKB, (unsigned)(NRBT * 4), batch);
-        k_bwd_pt_split<<<pg, 256, 0, st>>>(P, N, ld, NRBT, NKB, B);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
         TcGemm g;
         g.A = (const uint8_t *)A;
-        g.B = (const uint8_t *)B;
+        g.B = B;
         g.nrb_a = (int)NRB;
         g.nrb_b = (int)NRBT;
         g.nkb = (int)NKB;
+        g.nkb_t = (int)(ld / kTileK);
         g.tpe = (int)(NRB * NRBT);
         g.N = N;
         g.ld = ld;

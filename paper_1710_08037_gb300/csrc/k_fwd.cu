@@ -34,9 +34,9 @@ struct TaskOf {
 template <typename T_>
 struct TaskOf<T_, kK1Prep> {
     typedef PrepTask<T_> type;
-    static __host__ __device__ type make(const void *x, int64_t ldx, void *P, float *rinv, int,
+    static __host__ __device__ type make(const void *x, int64_t ldx, void *P, float *rinv, int N,
                                          int64_t ld) {
-        return type{(const T_ *)x, ldx, (float *)P, rinv, ld};
+        return type{(const T_ *)x, ldx, (float *)P, rinv, ld, nullptr, N};
     }
 };
 typedef TaskOf<Tin, KIND> Tk;
@@ -94,12 +94,27 @@ cudaError_t launch_group_class(const Handle *h, cudaStream_t s, const K1Group &g
 
 template <typename Tin_, int KIND_>
 cudaError_t k1_pow2(const Handle *h, cudaStream_t s, const K1Args &a) {
+    if constexpr (KIND_ == kK1Prep) {
+        if (a.Ps) {  // the backward recompute, with the split operand as well
+            const PrepTask<Tin_, true> task{(const Tin_ *)a.x, a.ldx, (float *)a.P, a.rinv, a.ld,
+                                            a.Ps, a.N};
+            return launch_hilbert_pow2(h->num_sms, s, a.log2T, task, twiddle_table(h, a.log2T),
+                                       a.rows);
+        }
+    }
     const auto task = TaskOf<Tin_, KIND_>::make(a.x, a.ldx, a.P, a.rinv, a.N, a.ld);
     return launch_hilbert_pow2(h->num_sms, s, a.log2T, task, twiddle_table(h, a.log2T), a.rows);
 }
 
 template <typename Tin_, int KIND_>
 cudaError_t k1_conv(const Handle *h, cudaStream_t s, const K1Args &a, const ConvPlan &plan) {
+    if constexpr (KIND_ == kK1Prep) {
+        if (a.Ps) {
+            const PrepTask<Tin_, true> task{(const Tin_ *)a.x, a.ldx, (float *)a.P, a.rinv, a.ld,
+                                            a.Ps, a.N};
+            return launch_hilbert_conv(h->num_sms, s, task, plan, a.T, a.ld, a.rows);
+        }
+    }
     const auto task = TaskOf<Tin_, KIND_>::make(a.x, a.ldx, a.P, a.rinv, a.N, a.ld);
     return launch_hilbert_conv(h->num_sms, s, task, plan, a.T, a.ld, a.rows);
 }

@@ -13,10 +13,11 @@
 // MMA's negate-A bit.
 //
 // The same machinery serves the backward pass's dense contraction
-// Gamma = S P / T (GEMM mode): with A the split rows of S (row i, K = k) and
-// B the split rows of conj(P)^T (row t, K = k), the products above give
-// sum_k S[i][k] P[k][t].  The tile grid is then full (every (I, J)) and the
-// epilogue stores the complex tile instead of read-outs.
+// Gamma = S P / T (GEMM mode): A is the split rows of S (row i, K = k) and B
+// P's own split rows (row k, t contiguous), which the MMA reads MN-major; with
+// a, b the parts of S and a', b' those of P, Re Gamma = a a' - b b' and
+// Im Gamma = b a' + a b' (12 MMAs again).  The tile grid is then full (every
+// (I, J)) and the epilogue stores the complex tile instead of read-outs.
 //
 // Accumulation.  The tensor core's FP32 accumulation into TMEM does not
 // round to nearest, and its error grows with the number of K blocks added
@@ -254,6 +255,15 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
            ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
+// Shared-memory matrix descriptor: MN-major operand, 64-byte swizzle: atoms
+// of 8 K-rows x 32 MN-elements (64 bytes each), the next 32 MN-elements
+// 2048 bytes on (LBO), the next 8 K-rows 512 bytes on (SBO).
+__device__ __forceinline__ uint64_t sdesc_mn64(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(2048 >> 4) << 16) |
+           ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+constexpr uint32_t kIdescBMn = 1u << 16;  // instruction descriptor: B is MN-major
+
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16 (fmt 1) or FP16
 // (fmt 0), both K-major, M = 128, N = 128, optional negate-A.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, bool negA, int n = TN) {
@@ -476,10 +486,13 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                     nkb = g.nkb;
                     kb_hi = nkb;
                     pa = g.A + (size_t)((int64_t)e * g.nrb_a + I) * nkb * SIDE_BYTES;
-                    pj = g.B + (size_t)((int64_t)e * g.nrb_b + J) * nkb * SIDE_BYTES;
+                    // B: P's split blocks of epoch e, t-blocks 4J .. 4J + 3 of
+                    // row block 0 (row block kb / 4 added per K block)
+                    pj = g.B + (size_t)((int64_t)e * g.nrb_a * g.nkb_t + 4 * J) * SIDE_BYTES;
                     // checked builds: operand blocks inside both operands
                     if (!PLV_IN_BOUNDS(I >= 0 && I < g.nrb_a && J >= 0 && J < g.nrb_b &&
-                                       e >= 0 && (int64_t)e * g.tpe < args.total_items)) {
+                                       4 * J < g.nkb_t && 4 * g.nrb_a >= nkb && e >= 0 &&
+                                       (int64_t)e * g.tpe < args.total_items)) {
                         pa = g.A;
                         pj = g.B;
                     }
@@ -503,12 +516,32 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                 for (int kb = kb_lo; kb < kb_hi; ++kb) {
                     if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, args.status, args.wait_ns)) break;
                     const uint32_t sa = base + stage * STAGE_BYTES;
-                    mbar_expect_tx(FULL(stage), diag ? SIDE_BYTES : 2 * SIDE_BYTES);
+                    // GEMM mode: B's t-blocks that exist (the last tile's
+                    // others hold stale data, which only feeds columns t >= ld)
+                    int nbv = 4;
+                    if constexpr (GEMM)
+                        nbv = args.gemm.nkb_t - 4 * J < 4 ? args.gemm.nkb_t - 4 * J : 4;
+                    mbar_expect_tx(FULL(stage), diag ? SIDE_BYTES
+                                                     : (GEMM ? SIDE_BYTES + nbv * SIDE_BYTES / 4
+                                                             : 2 * SIDE_BYTES));
                     if (withhold) {
                         withhold = false;
                     } else {
                         bulk_g2s(sa, pa + (size_t)kb * SIDE_BYTES, SIDE_BYTES, FULL(stage));
-                        if (!diag)
+                        if constexpr (GEMM) {
+                            // rows k = 32 kb .. 32 kb + 31 of each t-block and
+                            // plane (2 KB each) to [plane][t-block][32 rows]:
+                            // the MN-major layout of the B descriptor
+                            const uint8_t *src = pj +
+                                                 (size_t)(kb >> 2) * args.gemm.nkb_t * SIDE_BYTES +
+                                                 (size_t)(kb & 3) * (SIDE_BYTES / 16);
+                            for (int c = 0; c < nbv; ++c)
+                                for (int pl = 0; pl < 4; ++pl)
+                                    bulk_g2s(sa + SIDE_BYTES + pl * PLANE_BYTES +
+                                                 c * (PLANE_BYTES / 4),
+                                             src + (size_t)c * SIDE_BYTES + pl * PLANE_BYTES,
+                                             PLANE_BYTES / 4, FULL(stage));
+                        } else if (!diag)
                             bulk_g2s(sa + SIDE_BYTES, pj + (size_t)kb * SIDE_BYTES, SIDE_BYTES,
                                      FULL(stage));
                         pending |= 1u << stage;
@@ -573,6 +606,37 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                         tc_fence_after();
                         const uint32_t sa = base + stage * STAGE_BYTES;
                         const uint32_t sb = diag ? sa : sa + SIDE_BYTES;
+                        if constexpr (GEMM) {
+                            const uint32_t IP = ID_POS | kIdescBMn, IN = ID_NEG | kIdescBMn;
+#pragma unroll
+                            for (int ks = 0; ks < KB / 16; ++ks) {
+                                const uint32_t ko = ks * 32;    // A: 16 K-values x 2 bytes
+                                const uint32_t kr = ks * 1024;  // B: 16 K-rows x 64 bytes
+                                const uint64_t aRH = sdesc_sw64(sa + P_RH * PLANE_BYTES + ko);
+                                const uint64_t aRL = sdesc_sw64(sa + P_RL * PLANE_BYTES + ko);
+                                const uint64_t aIH = sdesc_sw64(sa + P_IH * PLANE_BYTES + ko);
+                                const uint64_t aIL = sdesc_sw64(sa + P_IL * PLANE_BYTES + ko);
+                                const uint64_t bRH = sdesc_mn64(sb + P_RH * PLANE_BYTES + kr);
+                                const uint64_t bRL = sdesc_mn64(sb + P_RL * PLANE_BYTES + kr);
+                                const uint64_t bIH = sdesc_mn64(sb + P_IH * PLANE_BYTES + kr);
+                                const uint64_t bIL = sdesc_mn64(sb + P_IL * PLANE_BYTES + kr);
+                                const uint32_t first = (kb == kb0 && ks == 0) ? 0u : 1u;
+                                // Re += a a' - b b', Im += b a' + a b' (hi*hi + hi*lo
+                                // + lo*hi each), grouped by A operand and sign
+                                mma_f16_ca<kFill>(d_re, aRH, bRH, IP, first);
+                                mma_f16_ca<kUse>(d_re, aRH, bRL, IP, 1u);
+                                mma_f16_ca<kUse>(d_im, aRH, bIH, IP, first);
+                                mma_f16_ca<kLast>(d_im, aRH, bIL, IP, 1u);
+                                mma_f16_ca<kFill>(d_re, aRL, bRH, IP, 1u);
+                                mma_f16_ca<kLast>(d_im, aRL, bIH, IP, 1u);
+                                mma_f16_ca<kFill>(d_re, aIH, bIH, IN, 1u);
+                                mma_f16_ca<kLast>(d_re, aIH, bIL, IN, 1u);
+                                mma_f16_ca<kFill>(d_im, aIH, bRH, IP, 1u);
+                                mma_f16_ca<kLast>(d_im, aIH, bRL, IP, 1u);
+                                mma_f16(d_re, aIL, bIH, IN, 1u);
+                                mma_f16(d_im, aIL, bRH, IP, 1u);
+                            }
+                        } else {
 #pragma unroll
                         for (int ks = 0; ks < KB / 16; ++ks) {
                             const uint32_t ko = ks * 32;  // 16 samples x 2 bytes
@@ -601,6 +665,7 @@ k_gram_tc(const __grid_constant__ TcArgs args) {
                             mma_f16_ca<kLast>(d_im, aIH, bRL, ID_POS, 1u);
                             mma_f16_ca<kFill>(d_re, aIL, bIH, ID_POS, 1u);
                             mma_f16_ca<kLast>(d_im, aIL, bRH, ID_POS, 1u);
+                        }
                         }
                         mma_commit(EMPTY(stage));  // frees the stage when done
                         issued = true;

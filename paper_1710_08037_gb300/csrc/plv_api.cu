@@ -917,7 +917,22 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
     char *w = (char *)h.ws;
     float *P = (float *)w, *rinv = (float *)(w + bP), *Gm = (float *)(w + bP + bR),
           *S = (float *)(w + bP + bR + bG);
-    st = PLV_CHECK_LAUNCH(launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv, T, plan),
+    // split-precision handles: the recompute also writes P's BF16 splits, the
+    // contraction's B operand, whose padding rows N .. 128 ceil(N/128) - 1
+    // must be zero (the scratch is shared with other calls)
+    void *Ps = nullptr;
+    if (tc) {
+        size_t a_bytes = 0;
+        backward_tc_bytes(batch, N, T, &a_bytes);
+        Ps = (char *)S + a_bytes;
+        if (N % 128 != 0) {
+            st = PLV_CHECK_LAUNCH(launch_zero_pad_rows(s, Ps, batch, N, T),
+                                  "plv_backward: padding rows");
+            if (st != PLV_OK) return st;
+        }
+    }
+    st = PLV_CHECK_LAUNCH(launch_bwd_prep(&h, s, x, dtype, (int64_t)rows, L, ldx, P, rinv, T, plan,
+                                          Ps, N),
                     "plv_backward: recompute");
     if (st != PLV_OK) return st;
     return PLV_CHECK_LAUNCH(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,

@@ -1,8 +1,9 @@
 """Host-side logic of the library on CPU, through small C++ programs linked
 against the built library (pure host functions: no GPU needed):
 - the autotuner's work lists: plv::gram_order (the grouped Gram's tile
-  schedules) and plv::k1_layout (the grouped analytic signal's items by
-  thread class);
+  schedules), plv::gram_list with split K (parts of whole chunks covering
+  every tile once, their slots and counters) and plv::k1_layout (the grouped
+  analytic signal's items by thread class);
 - the any-length plans: the transform length for T, its radix order, and
   the FP64 inverse DFT of any length that builds the band kernels, against
   a direct sum."""
@@ -29,10 +30,10 @@ using namespace plv;
 #define CHECK(c) do { if (!(c)) { std::printf("FAIL %s:%d %s\n", __FILE__, __LINE__, #c); \
     return 1; } } while (0)
 
-static std::vector<long> loads(const std::vector<TcProblem> &dp, const std::vector<int4> &v,
-                               int G, int cost) {
+static std::vector<long> loads(const std::vector<int> &cost, const std::vector<int64_t> &o,
+                               int G, int c0) {
     std::vector<long> l(G, 0);
-    for (size_t t = 0; t < v.size(); ++t) l[t % G] += dp[v[t].x].nkb + cost;
+    for (size_t t = 0; t < o.size(); ++t) l[t % G] += cost[o[t]] + c0;
     return l;
 }
 
@@ -41,47 +42,103 @@ int main() {
     const int nkb[5] = {313, 160, 40, 16, 3}, cnt[5] = {300, 200, 517, 100, 37};
     std::vector<TcProblem> dp(5);
     std::vector<int4> items;
+    std::vector<int> cost;
     for (int p = 0; p < 5; ++p) {
         dp[p] = TcProblem{};
         dp[p].nkb = nkb[p];
-        for (int c = 0; c < cnt[p]; ++c) items.push_back(make_int4(p, c, 0, 0));
+        for (int c = 0; c < cnt[p]; ++c) {
+            items.push_back(make_int4(p, c, 0, 0));
+            cost.push_back(nkb[p]);
+        }
     }
-    auto key = [](const int4 &a) { return std::make_tuple(a.x, a.y, a.z, a.w); };
-    auto sorted = [&](std::vector<int4> v) {
-        std::sort(v.begin(), v.end(), [&](const int4 &a, const int4 &b) { return key(a) < key(b); });
-        return v;
-    };
-    const std::vector<int4> ref = sorted(items);
+    const int64_t n = (int64_t)items.size();
     for (int G : {1, 7, 152, 2000}) {
-        CHECK(gram_order(dp, items, 0, G, 0).size() == items.size());
-        const std::vector<long> base = loads(dp, gram_order(dp, items, 0, G, 0), G, 0);
-        for (int cost : {0, 8, 32}) {
-            const std::vector<int4> o = gram_order(dp, items, 1, G, cost);
-            // a permutation of the tile list
-            const std::vector<int4> s = sorted(o);
-            CHECK(s.size() == ref.size());
-            for (size_t i = 0; i < s.size(); ++i) CHECK(key(s[i]) == key(ref[i]));
+        CHECK((int64_t)gram_order(cost, 0, G, 0).size() == n);
+        const std::vector<long> base = loads(cost, gram_order(cost, 0, G, 0), G, 0);
+        for (int c0 : {0, 8, 32}) {
+            const std::vector<int64_t> o = gram_order(cost, 1, G, c0);
+            // a permutation of the list
+            std::vector<int64_t> s = o;
+            std::sort(s.begin(), s.end());
+            for (int64_t i = 0; i < n; ++i) CHECK(s[i] == i);
             // no CTA's K-block load is further from the mean than under longest first
-            const std::vector<long> lb = loads(dp, o, G, 0);
+            const std::vector<long> lb = loads(cost, o, G, 0);
             const long spread = *std::max_element(lb.begin(), lb.end()) -
                                 *std::min_element(lb.begin(), lb.end());
             const long spread0 = *std::max_element(base.begin(), base.end()) -
                                  *std::min_element(base.begin(), base.end());
-            if (cost == 0) CHECK(spread <= spread0);
-            // each round of G slots holds the tiles of one longest-first round
+            if (c0 == 0) CHECK(spread <= spread0);
+            // each round of G slots holds the entries of one longest-first round
             for (size_t r = 0; r * G < o.size(); ++r) {
                 const size_t b = r * G, e = std::min(o.size(), b + (size_t)G);
-                std::vector<int4> a(o.begin() + b, o.begin() + e), c(items.begin() + b, items.begin() + e);
-                a = sorted(a);
-                c = sorted(c);
-                for (size_t i = 0; i < a.size(); ++i) CHECK(key(a[i]) == key(c[i]));
+                std::vector<int64_t> a(o.begin() + b, o.begin() + e);
+                std::sort(a.begin(), a.end());
+                for (size_t i = 0; i < a.size(); ++i) CHECK(a[i] == (int64_t)(b + i));
             }
         }
     }
     // longest first is the list as given
     {
-        const std::vector<int4> o = gram_order(dp, items, 0, 152, 0);
-        for (size_t i = 0; i < o.size(); ++i) CHECK(key(o[i]) == key(items[i]));
+        const std::vector<int64_t> o = gram_order(cost, 0, 152, 0);
+        for (int64_t i = 0; i < n; ++i) CHECK(o[i] == i);
+    }
+    // the launch list: tiles (problem, epoch, I, J) with I <= J, longest first
+    {
+        std::vector<int4> tiles;
+        const int nrb[5] = {3, 1, 2, 1, 4};
+        for (int p = 0; p < 5; ++p)
+            for (int e = 0; e < 2; ++e)
+                for (int J = 0; J < nrb[p]; ++J)
+                    for (int I = 0; I <= J; ++I) tiles.push_back(make_int4(p, e, I, J));
+        std::stable_sort(tiles.begin(), tiles.end(), [&](const int4 &a, const int4 &b) {
+            return dp[a.x].nkb > dp[b.x].nkb;
+        });
+        for (int chunk : {4, 16})
+            for (int f : {0, 1, 2, 4, 64})
+                for (int sched : {0, 1}) {
+                    GroupConfig cfg;
+                    cfg.gram_split = f;
+                    cfg.gram_schedule = sched;
+                    cfg.gram_tile_cost = 8;
+                    const GramList L = gram_list(dp, tiles, chunk, 152, cfg);
+                    CHECK(covers(dp, tiles, L));
+                    if (f == 0) CHECK(L.parts.empty() && L.items.size() == tiles.size());
+                    // parts: whole chunks, at least 64 K blocks unless the tile's end,
+                    // consecutive slots per tile, one counter per split tile
+                    std::map<int, std::vector<SplitPart>> by_tile;
+                    for (const SplitPart &q : L.parts) by_tile[q.tile].push_back(q);
+                    CHECK((int)by_tile.size() == L.ntiles);
+                    int slots = 0;
+                    for (auto &kv : by_tile) {
+                        const std::vector<SplitPart> &v = kv.second;
+                        CHECK((int)v.size() == v[0].S && v[0].S >= 2);
+                        for (int s2 = 0; s2 < (int)v.size(); ++s2) {
+                            CHECK(v[s2].s == s2 && v[s2].S == v[0].S);
+                            CHECK(v[s2].slot == v[0].slot + s2);
+                            CHECK(v[s2].kb_lo % chunk == 0);
+                            if (s2 + 1 < (int)v.size()) CHECK(v[s2].kb_hi == v[s2 + 1].kb_lo);
+                            CHECK(v[s2].kb_hi - v[s2].kb_lo >= std::min(64, chunk));
+                        }
+                        slots += v[0].S;
+                    }
+                    CHECK(slots == L.nslots);
+                    // the launch list is longest first under longest-first scheduling
+                    if (sched == 0)
+                        for (size_t i = 1; i < L.items.size(); ++i) {
+                            auto len = [&](const int4 &it) {
+                                return it.w ? L.parts[it.w - 1].kb_hi - L.parts[it.w - 1].kb_lo
+                                            : dp[it.x].nkb;
+                            };
+                            CHECK(len(L.items[i - 1]) >= len(L.items[i]));
+                        }
+                }
+        // a long tile split at f = 1 in a short plan: 313 K blocks, parts of >= 64
+        GroupConfig cfg;
+        cfg.gram_split = 1;
+        std::vector<int4> one(1, make_int4(0, 0, 0, 0));
+        const GramList L = gram_list(dp, one, 16, 152, cfg);
+        CHECK(L.parts.size() == 5 && L.ntiles == 1 && L.nslots == 5);
+        CHECK(L.parts[0].kb_lo == 0 && L.parts[4].kb_hi == 313);
     }
     // grouped analytic signal: problems with transform lengths in all classes
     const int Ms[6] = {1280, 20480, 4096, 1280, 10240, 768};
