@@ -131,15 +131,29 @@ k_bwd_s_split(const float2 *__restrict__ C, const float *__restrict__ g1,
     const int bi = p * 32, bk = q * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t eb = (int64_t)b * N * N;
-    auto G = [&](int r, int c) -> float2 {
-        if (r >= N || c >= N || r == c) return make_float2(0.f, 0.f);
-        const int64_t qq = eb + (int64_t)r * N + c;
-        return gfun(C[qq], g1 ? g1[qq] : 0.f, g2 ? g2[qq] : 0.f, g3 ? g3[qq] : 0.f);
-    };
-    for (int yy = ty; yy < 32; yy += 8) Gt[yy][tx] = G(bk + yy, bi + tx);  // G(k, i)
+    // the inputs of both tiles are loaded before any G is formed, so that
+    // each thread has its 8 loads of C (and of the gradients) in flight at once
+    float2 cv[8];
+    float a1[8], a2[8], a3[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        // u < 4: (k, i) of the transposed tile; u >= 4: (i, k)
+        const int yy = ty + 8 * (u & 3);
+        const int r = u < 4 ? bk + yy : bi + yy, c = u < 4 ? bi + tx : bk + tx;
+        const bool ok = r < N && c < N && r != c;
+        const int64_t qq = eb + (int64_t)(ok ? r : 0) * N + (ok ? c : 0);
+        cv[u] = ok ? __ldg(C + qq) : make_float2(0.f, 0.f);
+        a1[u] = ok && g1 ? __ldg(g1 + qq) : 0.f;
+        a2[u] = ok && g2 ? __ldg(g2 + qq) : 0.f;
+        a3[u] = ok && g3 ? __ldg(g3 + qq) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Gt[ty + 8 * u][tx] = gfun(cv[u], a1[u], a2[u], a3[u]);  // G(k, i)
     __syncthreads();
-    for (int yy = ty; yy < 32; yy += 8) {
-        const float2 gik = G(bi + yy, bk + tx);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int yy = ty + 8 * u;
+        const float2 gik = gfun(cv[4 + u], a1[4 + u], a2[4 + u], a3[4 + u]);
         const float2 gki = Gt[tx][yy];
         const float2 v = make_float2(gik.x + gki.x, gik.y - gki.y);  // G_ik + conj(G_ki)
         Sm[yy][tx] = v;
