@@ -316,7 +316,9 @@ plv_status plv_group_create(plv_handle *h, const plv_problem *probs, int nprob,
  * ONE persistent tensor-core launch over the whole tile list (CTAs take
  * tiles round-robin, longest first), preceded by a memset of the split-K
  * counters when the plan splits tiles; an FP32 handle runs one Gram launch
- * per problem.  Allocates nothing: can be captured in a CUDA graph. */
+ * per problem.  Allocates nothing: can be captured in a CUDA graph.  Two
+ * runs of one plan must not overlap (on two streams): they write the same
+ * outputs and share the split counters. */
 plv_status plv_gram_grouped(plv_handle *h, void *stream, const plv_group *group);
 
 /* Eq. 3 and 4 for every problem of a plan that has an input x: the
