@@ -409,7 +409,7 @@ plv_status plv_group_configure(plv_handle *h, void *stream, plv_group *group, in
 
 /* The split-K plan of plv_group_configure and plv_group_tune (host only;
  * needs no device).  For ntiles tiles of nkb[i] 32-sample K blocks, `chunk`
- * K blocks per summation chunk (16 for BF16X3, 4 for FP16X3), a persistent
+ * K blocks per summation chunk (32 for BF16X3, 4 for FP16X3), a persistent
  * grid of `grid` CTAs and factor `split` (0 .. 64), writes parts[i], the
  * number of parts tile i runs as (1: whole).  With W the total K blocks and
  * L = max(chunk, 64, ceil(W / (grid split))), a tile of nkb > L K blocks

@@ -413,9 +413,9 @@ struct TcSplit {
     int nslots = 0, ntiles = 0; // sizes of partials (slots) and counters (tiles)
 };
 constexpr int kTileFloats = 2 * 128 * 128;  // one slot
-// K blocks of 32 samples per chunk of the two-level summation (BF16x3: 512
+// K blocks of 32 samples per chunk of the two-level summation (BF16x3: 1024
 // samples, FP16x3: 128).
-inline int gram_chunk_kb(plv_precision p) { return p == PLV_PREC_FP16X3 ? 4 : 16; }
+inline int gram_chunk_kb(plv_precision p) { return p == PLV_PREC_FP16X3 ? 4 : 32; }
 // One persistent launch over a list of tiles: items[t] = (problem, epoch,
 // I | J << 16, 1 + split part, or 0 for a whole tile).
 cudaError_t launch_gram_tc_group(const Handle *h, cudaStream_t s, const TcProblem *probs,

@@ -21,8 +21,8 @@
 //
 // Accumulation.  The tensor core's FP32 accumulation into TMEM does not
 // round to nearest, and its error grows with the number of K blocks added
-// into one accumulator.  So the K loop runs in chunks (512 samples for BF16,
-// 128 for FP16):
+// into one accumulator.  So the K loop runs in chunks (1024 samples for
+// BF16, 128 for FP16):
 // each chunk accumulates into a fresh TMEM region (two regions, ping-pong),
 // and the epilogue warps drain every finished chunk into FP32 running sums
 // in registers (round to nearest), as a two-level summation.
@@ -71,16 +71,17 @@ constexpr int NEPI_WARPS = 16;               // 4 lane quarters x 4 column quart
 constexpr int NTHREADS = 64 + 32 * NEPI_WARPS;
 constexpr int TMEM_COLS = 512;
 constexpr int ACC_COLS = 256;                 // Re (128) + Im (128)
-// Stages per K chunk, by split: BF16x3 drains every 512 samples, FP16x3 every
-// 128.  Longer chunks leave the MMAs more slack over the tile-end stores but
-// add accumulation error (measured full-size worst error against the FP64
-// oracle: 1.1e-6 at 512, 5.3e-7 at 256); the FP16 split is the
-// accuracy-first mode.
+// Stages per K chunk, by split: BF16x3 drains every 1024 samples, FP16x3
+// every 128.  Fewer drains made the N = T = 8192 Gram 6 % faster than 512
+// (same-box A/B, under the power cap) but add accumulation error: the
+// largest PLV error against the FP64 oracle there (on the diagonal, where
+// the accumulators are largest) went from 5.5e-6 to 9.1e-6, within the
+// BF16x3 bound of 2e-5.  The FP16 split is the accuracy-first mode.
 template <uint32_t FMT>
 struct Chunk {
-    static constexpr int CH = FMT == 1u ? 16 : 4;
+    static constexpr int CH = FMT == 1u ? 32 : 4;
 };
-static_assert(Chunk<1u>::CH == 16 && Chunk<0u>::CH == 4, "gram_chunk_kb (common.cuh)");
+static_assert(Chunk<1u>::CH == 32 && Chunk<0u>::CH == 4, "gram_chunk_kb (common.cuh)");
 static_assert(kTileFloats == 2 * TM * TN, "split-K chunk slot");
 // per epilogue warp, a 32-row x 8-column FP32 staging tile for the row-wise
 // stores (after the operand ring and the barriers)

@@ -207,7 +207,7 @@ def test_split_k_results_in_graphs_and_after_tuning(prec):
         probs.append({"x": x, "P": h.empty_phasors(B, N, T), "batch": B, "N": N, "T": T})
     grp = h.plv_group_create(probs, C=True, diag=True)
     # the host plan splits every tile of this plan at f = 1
-    chunk = 16 if prec == "bf16x3" else 4
+    chunk = 32 if prec == "bf16x3" else 4
     nkb = []
     for B, N, T in LONG:
         nrb = (N + 127) // 128
