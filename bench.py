@@ -165,9 +165,9 @@ class ClockSampler:
 # precision; an entry is removed when the kernel changes after its capture.
 TRAFFIC = {
     # k_gram_tc on bandlimited-N8192-T8192-E2 (super-block raster of width 16,
-    # MMA width per tile, collector-buffer A reuse), read + write of its 4th
-    # launch, scaled by 20 / 2 epochs
-    ("k_gram_tc", "bandlimited-N8192-T8192-E20", "bf16x3"): (13.950117632e9 + 2.692750336e9) * 10,
+    # MMA width per tile, collector-buffer A reuse, 1024-sample summation
+    # chunks), read + write of its 4th launch, scaled by 20 / 2 epochs
+    ("k_gram_tc", "bandlimited-N8192-T8192-E20", "bf16x3"): (9.320439040e9 + 2.290635264e9) * 10,
 }
 
 
