@@ -916,6 +916,44 @@ def backward_measure(args, dev, dist, rank, world):
         fp32_bwd = {"backward_ms": a.elapsed_time(b) / 2,
                     "rel_l2_diff_vs_split": rel}
         h32.close()
+    # the same loss with the forward's phasors kept for the backward pass
+    # (plv_analytic_save / plv_backward_saved: no recompute), where the
+    # handle supports it
+    saved_mode = None
+    if args.precision in ("fp32", "bf16x3"):
+        grad_s = torch.empty_like(grad)
+
+        def step_saved(e=None):
+            if e:
+                e[0].record(s)
+            sv = hf.plv_analytic_save(x)
+            hf.plv_gram(sv["P"], B, N, T, plv=False, iplv=False, ciplv=True, C=True,
+                        out=out)
+            if e:
+                e[1].record(s)
+            hb.plv_backward_saved(sv, out["C"], None, None, g3, grad_x=grad_s)
+            if e:
+                e[2].record(s)
+
+        for _ in range(args.warmup):
+            step_saved()
+        torch.cuda.synchronize(dev)
+        per_s = [[ev(), ev(), ev()] for _ in range(args.steps)]
+        for p in per_s:
+            step_saved(p)
+        torch.cuda.synchronize(dev)
+        ms_s = max_over_ranks(sum(p[0].elapsed_time(p[2]) for p in per_s), dist, dev)
+        saved_mode = {
+            "ms_per_step": ms_s / args.steps,
+            "value": job_value(units, world, ms_s / args.steps),
+            "forward_ms": statistics.mean(p[0].elapsed_time(p[1]) for p in per_s),
+            "backward_ms": statistics.mean(p[1].elapsed_time(p[2]) for p in per_s),
+            "rel_l2_diff_vs_recompute": float(torch.linalg.norm(grad_s - grad)
+                                              / torch.linalg.norm(grad)),
+            "memory": "phasors and 1/|z| kept from the forward pass ("
+                      f"{20 if split else 12} bytes per sample)",
+            "gpu_launches": (2 + 3) * args.steps}
+        del grad_s
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -941,6 +979,7 @@ def backward_measure(args, dev, dist, rank, world):
             "lower_bound_tflops_over_whole_backward":
                 gemm_flops * (3 if split else 1) / (bwd_ms / 1e3) / 1e12},
         "fp32_backward": fp32_bwd,
+        "saved_analytic_signal": saved_mode,
         # forward: K1, Gram; backward: recompute, S, contraction, adjoint (and
         # the split P's padding rows when N % 128 != 0)
         "gpu_launches": (2 + 4 + (1 if split and N % 128 else 0)) * args.steps,

@@ -448,7 +448,7 @@ plv_status plv_metrics(plv_handle *h, void *stream, const void *C, int batch,
  * and three products per term (BF16 for both handle kinds: gradients can
  * exceed the FP16 range).  Supported T: as plv_analytic.  Uses handle
  * scratch of batch*N*ld*20 bytes plus, on an FP32 handle, batch*N*N*8, or,
- * on a split handle, batch*(ceil(N/128) + ceil(ld/128))*128*ceil(N/32)*32*8;
+ * on a split handle, batch*ceil(N/128)*128*(32*ceil(N/32) + ld)*8;
  * allocated on first use for a size (cudaMalloc; fails with PLV_ERR_INVALID
  * if that first use is inside a stream capture).  A CUDA graph captured
  * with this call keeps using the scratch it was captured with: when a later,
@@ -459,6 +459,36 @@ plv_status plv_backward(plv_handle *h, void *stream, const void *x,
                         plv_dtype dtype, int batch, int N, int T, int64_t ldx,
                         const void *C, const float *g_plv, const float *g_iplv,
                         const float *g_ciplv, float *grad_x);
+
+/* The forward pass in the form that lets the backward pass skip its
+ * recompute (no counterpart in the paper; the trade of memory for time that
+ * plv_backward makes the other way): Eq. 3 and 4 as in plv_analytic, and
+ * what the gradient of Eq. 4 needs.
+ *   P    : the Gram operand for plv_gram on this handle (plv_phasor_bytes
+ *          bytes; on an FP32 handle the FP32 planar phasors, on a BF16X3
+ *          handle the tiled BF16 split layout, padding rows zeroed);
+ *   P32  : float [batch*N][2][ld] FP32 planar phasors (on an FP32 handle
+ *          P itself: pass P or NULL);
+ *   rinv : float [batch*N][ld], 1/|z| (0 where |z| counts as 0, reading c7).
+ * The phasors are those of plv_backward's recompute (one Newton step on
+ * 1/|z|), so on a BF16X3 handle they can differ in the last bits from
+ * plv_analytic's.  FP16X3 handles: PLV_ERR_UNSUPPORTED.  Supported T, x and
+ * capture rules as plv_analytic. */
+plv_status plv_analytic_save(plv_handle *h, void *stream, const void *x, plv_dtype dtype,
+                             int batch, int N, int T, int64_t ldx, void *P, float *P32,
+                             float *rinv);
+
+/* plv_backward from what plv_analytic_save wrote (P, P32, rinv of the same
+ * x), without the recompute of the analytic signal: the same gradient, bit
+ * for bit, as plv_backward gives for that x and C.  Arguments, conventions,
+ * arithmetic and errors as plv_backward; handle scratch of batch*N*ld*8
+ * bytes plus, on an FP32 handle, batch*N*N*8, or, on a BF16X3 handle,
+ * batch*ceil(N/128)*128*ceil(N/32)*32*8.  FP16X3 handles:
+ * PLV_ERR_UNSUPPORTED. */
+plv_status plv_backward_saved(plv_handle *h, void *stream, int batch, int N, int T,
+                              const void *P, const float *P32, const float *rinv, const void *C,
+                              const float *g_plv, const float *g_iplv, const float *g_ciplv,
+                              float *grad_x);
 
 /* Normalisation of plv_trial_operands. */
 enum {

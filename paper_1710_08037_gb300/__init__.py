@@ -236,6 +236,44 @@ class Handle:
                                          _ptr(gs[2]), _ptr(grad_x)), self.h)
         return grad_x
 
+    def plv_analytic_save(self, x):
+        """Eq. 3 + 4 in the form plv_backward_saved takes: returns a dict
+        with the Gram operand "P" (for plv_gram), the FP32 planar phasors
+        "P32" and "rinv" = 1/|z| [batch*N][ld].  FP32 and BF16X3 handles."""
+        assert x.is_cuda and x.dim() == 3
+        B, N, T = x.shape
+        if not (x.stride(-1) == 1 and (N == 1 or x.stride(0) == N * x.stride(1))):
+            x = x.contiguous()
+        ldx = x.stride(1) if N > 1 else max(x.stride(0), T)
+        ld = phasor_ld(T)
+        P = self.empty_phasors(B, N, T)
+        if self.precision == 0:
+            P32 = P
+        else:
+            P32 = torch.empty(B * N * 2 * ld, dtype=torch.float32, device=self.device)
+        rinv = torch.empty(B * N * ld, dtype=torch.float32, device=self.device)
+        _lib.check(self.lib.plv_analytic_save(self.h, _stream(self.device), _ptr(x),
+                                              _dtype_code(x), B, N, T, ldx, _ptr(P),
+                                              _ptr(P32), _ptr(rinv)), self.h)
+        return {"P": P, "P32": P32, "rinv": rinv, "shape": (B, N, T)}
+
+    def plv_backward_saved(self, saved, C, g_plv=None, g_iplv=None, g_ciplv=None,
+                           grad_x=None):
+        """plv_backward from plv_analytic_save's outputs (no recompute)."""
+        B, N, T = saved["shape"]
+        assert C.dtype == torch.complex64
+        C = C.contiguous()
+        gs = [None if g is None else g.to(torch.float32).contiguous()
+              for g in (g_plv, g_iplv, g_ciplv)]
+        if grad_x is None:
+            grad_x = torch.empty((B, N, T), dtype=torch.float32, device=self.device)
+        _lib.check(self.lib.plv_backward_saved(self.h, _stream(self.device), B, N, T,
+                                               _ptr(saved["P"]), _ptr(saved["P32"]),
+                                               _ptr(saved["rinv"]), _ptr(C), _ptr(gs[0]),
+                                               _ptr(gs[1]), _ptr(gs[2]), _ptr(grad_x)),
+                   self.h)
+        return grad_x
+
     def plv_group_create(self, problems, plv=True, iplv=True, ciplv=True,
                          C=False, diag=False):
         """Plan a grouped run.  `problems`: list of dicts with keys P,
@@ -456,33 +494,51 @@ class Group:
 
 
 class _Connectivity(torch.autograd.Function):
-    """PLV, iPLV, ciPLV of x (batch, N, T) with a hand-written backward:
-    forward saves x and C (not the analytic signal); backward recomputes the
-    analytic signal from x inside plv_backward."""
+    """PLV, iPLV, ciPLV of x (batch, N, T) with a hand-written backward.
+    recompute=True: forward saves x and C (not the analytic signal); backward
+    recomputes the analytic signal from x inside plv_backward.
+    recompute=False: forward keeps the phasors and 1/|z| of
+    plv_analytic_save (20 bytes per sample on a BF16X3 handle, 12 on FP32)
+    and backward skips the recompute (plv_backward_saved)."""
 
     @staticmethod
-    def forward(ctx, x, handle):
+    def forward(ctx, x, handle, recompute):
         E, N, T = x.shape
-        P = handle.plv_analytic(x.detach())
-        res = handle.plv_gram(P, E, N, T, C=True)
         ctx.handle = handle
-        ctx.save_for_backward(x.detach(), res["C"])
         ctx.x_dtype = x.dtype
+        ctx.recompute = recompute
+        if recompute:
+            P = handle.plv_analytic(x.detach())
+            res = handle.plv_gram(P, E, N, T, C=True)
+            ctx.save_for_backward(x.detach(), res["C"])
+        else:
+            saved = handle.plv_analytic_save(x.detach())
+            res = handle.plv_gram(saved["P"], E, N, T, C=True)
+            ctx.saved = saved
+            ctx.save_for_backward(res["C"])
         return res["plv"], res["iplv"], res["ciplv"]
 
     @staticmethod
     def backward(ctx, g_plv, g_iplv, g_ciplv):
-        x, C = ctx.saved_tensors
-        g = ctx.handle.plv_backward(x, C, g_plv, g_iplv, g_ciplv)
-        return g.to(ctx.x_dtype), None
+        if ctx.recompute:
+            x, C = ctx.saved_tensors
+            g = ctx.handle.plv_backward(x, C, g_plv, g_iplv, g_ciplv)
+        else:
+            (C,) = ctx.saved_tensors
+            g = ctx.handle.plv_backward_saved(ctx.saved, C, g_plv, g_iplv, g_ciplv)
+            ctx.saved = None
+        return g.to(ctx.x_dtype), None, None
 
 
-def connectivity(x, handle=None):
+def connectivity(x, handle=None, recompute=True):
     """Differentiable (PLV, iPLV, ciPLV) of real x (batch, N, T) on the GPU;
-    gradients flow to x through the library's backward kernels."""
+    gradients flow to x through the library's backward kernels.  With
+    recompute=False the forward pass keeps the analytic signal's phasors for
+    the backward pass instead of recomputing them (more memory, less time;
+    FP32 and BF16X3 handles)."""
     if handle is None:
         handle = _default_handle(x.device)
-    return _Connectivity.apply(x, handle)
+    return _Connectivity.apply(x, handle, recompute)
 
 
 def gram_split_plan(nkb, chunk, grid, split):

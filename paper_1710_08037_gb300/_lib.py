@@ -81,6 +81,8 @@ SIGNATURES = {
     "plv_group_tune": (_i, [_vp, _vp, _vp, _i, _vp]),
     "plv_group_configure": (_i, [_vp, _vp, _vp, _i, _vp, _i, _i, _i]),
     "plv_gram_split_plan": (_i, [_vp, _i, _i, _i, _i, _vp]),
+    "plv_analytic_save": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i64, _vp, _vp, _vp]),
+    "plv_backward_saved": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "plv_group_destroy": (_i, [_vp]),
     "plv_sync_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
 }

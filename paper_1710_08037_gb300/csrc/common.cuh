@@ -326,14 +326,15 @@ cudaError_t launch_bwd_prep(const Handle *h, cudaStream_t s, const void *x, plv_
                             int64_t rows, int log2T, int64_t ldx, float *P, float *rinv,
                             int T, const ConvPlan *plan, void *Ps = nullptr, int N = 0);
 // K5: S = G + G^H, Gamma = S P / T, grad = Re Gamma_z - H{Im Gamma_z}.
-// tc_ops NULL: FP32 contraction on the CUDA cores with S FP32 planar
-// [batch][2][N][N]; else the tensor-core contraction with its split operands
-// (backward_tc_bytes bytes at tc_ops: S rows, then P in the split operand
-// layout, which the preparation wrote) and S unused.
+// tc_a NULL: FP32 contraction on the CUDA cores with S FP32 planar
+// [batch][2][N][N]; else the tensor-core contraction, with S written as
+// split rows at tc_a (the first a_bytes of backward_tc_bytes) and tc_b P's
+// BF16 split rows in the operand layout (the preparation wrote them), S unused.
 cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
                             int log2T, const float2 *C, const float *g1, const float *g2,
                             const float *g3, const float *P, const float *rinv, float *S,
-                            float *Gm, float *grad, const ConvPlan *plan, void *tc_ops);
+                            float *Gm, float *grad, const ConvPlan *plan, void *tc_a,
+                            const void *tc_b);
 // Bytes of the tensor-core backward's split operands (S rows, then P's split
 // rows); *a_bytes receives the first part's size.
 size_t backward_tc_bytes(int batch, int N, int T, size_t *a_bytes);

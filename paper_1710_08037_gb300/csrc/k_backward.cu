@@ -366,15 +366,15 @@ size_t backward_tc_bytes(int batch, int N, int T, size_t *a_bytes) {
 cudaError_t launch_backward(const Handle *h, cudaStream_t st, int batch, int N, int T,
                             int log2T, const float2 *C, const float *g1, const float *g2,
                             const float *g3, const float *P, const float *rinv, float *S,
-                            float *Gm, float *grad, const ConvPlan *plan, void *tc_ops) {
+                            float *Gm, float *grad, const ConvPlan *plan, void *tc_a,
+                            const void *tc_b) {
     const int64_t ld = padded_len(T);
     cudaError_t e;
-    if (tc_ops) {
-        // split operands, then the contraction on the tensor cores
-        size_t a_bytes = 0;
-        backward_tc_bytes(batch, N, T, &a_bytes);
-        __nv_bfloat16 *A = (__nv_bfloat16 *)tc_ops;
-        const uint8_t *B = (const uint8_t *)tc_ops + a_bytes;  // stage 1 wrote it
+    if (tc_a) {
+        // S as split rows, then the contraction on the tensor cores
+        if (!tc_b) return cudaErrorInvalidValue;
+        __nv_bfloat16 *A = (__nv_bfloat16 *)tc_a;
+        const uint8_t *B = (const uint8_t *)tc_b;  // stage 1 wrote it
         const int64_t NRB = row_blocks(N), NKB = ((int64_t)N + kTileK - 1) / kTileK;
         const int64_t NRBT = (ld + 127) / 128;  // output tiles along t
         const unsigned nt = (unsigned)NKB;  // 32-tiles along i and along k

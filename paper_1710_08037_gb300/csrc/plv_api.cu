@@ -937,8 +937,125 @@ plv_status plv_backward(plv_handle *hp, void *stream, const void *x, plv_dtype d
     if (st != PLV_OK) return st;
     return PLV_CHECK_LAUNCH(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,
                                       g_ciplv, P, rinv, tc ? nullptr : S, Gm, grad_x, plan,
-                                      tc ? (void *)S : nullptr),
+                                      tc ? (void *)S : nullptr, Ps),
                       "plv_backward launch");
+}
+
+// The any-length plan for T, made outside stream capture (shared by the
+// saved-signal entry points).
+static plv_status conv_plan_for(Handle &h, cudaStream_t s, int T, const char *who,
+                                const ConvPlan **plan) {
+    if (!h.conv.count(T)) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            return fail(PLV_ERR_INVALID,
+                        "%s: tables for T = %d must be made before capture (call plv_prepare)",
+                        who, T);
+    }
+    return get_conv_plan(h, T, plan);
+}
+
+plv_status plv_analytic_save(plv_handle *hp, void *stream, const void *x, plv_dtype dtype,
+                             int batch, int N, int T, int64_t ldx, void *P, float *P32,
+                             float *rinv) {
+    PLV_RANGE("plv_analytic_save");
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_analytic_save: handle is NULL");
+    if (batch < 0 || N < 0 || T <= 0)
+        return fail(PLV_ERR_INVALID, "plv_analytic_save: bad sizes batch=%d N=%d T=%d", batch, N,
+                    T);
+    if (dtype != PLV_F32 && dtype != PLV_F64)
+        return fail(PLV_ERR_INVALID, "plv_analytic_save: unknown dtype %d", (int)dtype);
+    if (ldx < T) return fail(PLV_ERR_INVALID, "plv_analytic_save: ldx < T");
+    Handle &h = hp->h;
+    if (h.prec == PLV_PREC_FP16X3)
+        return fail(PLV_ERR_UNSUPPORTED, "plv_analytic_save: FP16X3 handles (use plv_analytic "
+                                         "and plv_backward)");
+    if (batch == 0 || N == 0) return PLV_OK;
+    const bool fp32 = h.prec == PLV_PREC_FP32;
+    if (fp32 && !P32) P32 = (float *)P;
+    if (!x || !P || !P32 || !rinv)
+        return fail(PLV_ERR_INVALID, "plv_analytic_save: NULL data pointer");
+    if (fp32 && (void *)P32 != P)
+        return fail(PLV_ERR_INVALID, "plv_analytic_save: on an FP32 handle P32 is P (or NULL)");
+    const int L = log2_exact(T);
+    const bool direct = L >= kMinLog2T && L <= kMaxLog2Direct;
+    if (!direct && (T < 2 || 2 * T - 1 > kMaxConvM))
+        return fail(PLV_ERR_UNSUPPORTED, "plv_analytic_save: T = %d (supported: 2 <= T <= %d)",
+                    T, kMaxConvM / 2);
+    if (((uintptr_t)x % (dtype == PLV_F32 ? 4 : 8)) != 0 || ((uintptr_t)P % 16) != 0 ||
+        ((uintptr_t)P32 % 16) != 0 || ((uintptr_t)rinv % 16) != 0)
+        return fail(PLV_ERR_INVALID, "plv_analytic_save: misaligned pointer");
+    PLV_GUARD(&h);
+    cudaStream_t s = (cudaStream_t)stream;
+    const ConvPlan *plan = nullptr;
+    if (!direct) {
+        std::lock_guard<std::mutex> lock(h.mu);
+        plv_status st = conv_plan_for(h, s, T, "plv_analytic_save", &plan);
+        if (st != PLV_OK) return st;
+    }
+    if (!fp32) {
+        plv_status st = PLV_CHECK_LAUNCH(launch_zero_pad_rows(s, P, batch, N, T),
+                                         "plv_analytic_save: pad rows");
+        if (st != PLV_OK) return st;
+    }
+    return PLV_CHECK_LAUNCH(launch_bwd_prep(&h, s, x, dtype, (int64_t)batch * N, L, ldx, P32,
+                                            rinv, T, plan, fp32 ? nullptr : P, N),
+                            "plv_analytic_save launch");
+}
+
+plv_status plv_backward_saved(plv_handle *hp, void *stream, int batch, int N, int T,
+                              const void *P, const float *P32, const float *rinv, const void *C,
+                              const float *g_plv, const float *g_iplv, const float *g_ciplv,
+                              float *grad_x) {
+    PLV_RANGE("plv_backward_saved");
+    if (!hp) return fail(PLV_ERR_INVALID, "plv_backward_saved: handle is NULL");
+    if (batch < 0 || N < 0 || T <= 0)
+        return fail(PLV_ERR_INVALID, "plv_backward_saved: bad sizes batch=%d N=%d T=%d", batch,
+                    N, T);
+    Handle &h = hp->h;
+    if (h.prec == PLV_PREC_FP16X3)
+        return fail(PLV_ERR_UNSUPPORTED, "plv_backward_saved: FP16X3 handles");
+    if (batch == 0 || N == 0) return PLV_OK;
+    if (!grad_x) return fail(PLV_ERR_INVALID, "plv_backward_saved: grad_x is NULL");
+    const int L = log2_exact(T);
+    const bool direct = L >= kMinLog2T && L <= kMaxLog2Direct;
+    if (!direct && (T < 2 || 2 * T - 1 > kMaxConvM))
+        return fail(PLV_ERR_UNSUPPORTED, "plv_backward_saved: T = %d (supported: 2 <= T <= %d)",
+                    T, kMaxConvM / 2);
+    PLV_GUARD(&h);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!g_plv && !g_iplv && !g_ciplv)
+        return check_cuda(cudaMemsetAsync(grad_x, 0, sizeof(float) * (size_t)batch * N * T, s),
+                          "plv_backward_saved: zero grad");
+    const bool tc = h.prec != PLV_PREC_FP32;
+    if (!tc && !P32) P32 = (const float *)P;
+    if (!P || !P32 || !rinv || !C)
+        return fail(PLV_ERR_INVALID, "plv_backward_saved: NULL P, P32, rinv or C");
+    if (((uintptr_t)C % 8) != 0 || ((uintptr_t)P % 16) != 0 || ((uintptr_t)P32 % 16) != 0 ||
+        ((uintptr_t)rinv % 16) != 0 || ((uintptr_t)grad_x % 4) != 0)
+        return fail(PLV_ERR_INVALID, "plv_backward_saved: misaligned pointer");
+    const int64_t ld = padded_len(T);
+    const size_t rows = (size_t)batch * N;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t a_bytes = 0;
+    if (tc) backward_tc_bytes(batch, N, T, &a_bytes);
+    const size_t bG = up(rows * 2 * ld * 4),
+                 bS = tc ? up(a_bytes) : up((size_t)batch * 2 * N * N * 4);
+    std::lock_guard<std::mutex> lock(h.mu);
+    plv_status st = ensure_workspace(h, s, bG + bS);
+    if (st != PLV_OK) return st;
+    const ConvPlan *plan = nullptr;
+    if (!direct) {
+        st = conv_plan_for(h, s, T, "plv_backward_saved", &plan);
+        if (st != PLV_OK) return st;
+    }
+    char *w = (char *)h.ws;
+    float *Gm = (float *)w, *S = (float *)(w + bG);
+    return PLV_CHECK_LAUNCH(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv,
+                                            g_iplv, g_ciplv, P32, rinv, tc ? nullptr : S, Gm,
+                                            grad_x, plan, tc ? (void *)S : nullptr,
+                                            tc ? P : nullptr),
+                            "plv_backward_saved launch");
 }
 
 plv_status plv_sync_status(plv_handle *hp, void *stream, int *device_status) {

@@ -152,6 +152,6 @@ extern "C" plv_status plv_backward_noalloc(void *stream, const void *x, plv_dtyp
         "plv_backward_noalloc: recompute");
     if (r != PLV_OK) return r;
     return check_cuda(launch_backward(&h, s, batch, N, T, L, (const float2 *)C, g_plv, g_iplv,
-                                      g_ciplv, P, rinv, S, Gm, grad_x, nullptr, nullptr),
+                                      g_ciplv, P, rinv, S, Gm, grad_x, nullptr, nullptr, nullptr),
                       "plv_backward_noalloc launch");
 }

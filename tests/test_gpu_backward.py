@@ -204,3 +204,63 @@ def test_graph_keeps_its_scratch_after_growth(prec):
     assert h.plv_sync_status() == 0
     del graph
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("N,T", [(67, 300), (130, 1024), (33, 4096), (129, 1000)])
+def test_saved_backward_equals_recompute(prec, N, T):
+    """plv_backward_saved on plv_analytic_save's outputs gives plv_backward's
+    gradient bit for bit (same x, same C): the saved phasors are the
+    recompute's.  The saved forward's Gram agrees with the FP64 oracle."""
+    import oracle
+    import paper_1710_08037_gb300 as plv
+    from tests.helpers import TOL, compare
+    h = plv.Handle(precision=prec)
+    B = 2
+    x = synth.bandlimited(B, N, T, seed=N + 7 * T, band=(8, 60), device="cuda")
+    saved = h.plv_analytic_save(x)
+    res = h.plv_gram(saved["P"], B, N, T, C=True)
+    C = res["C"]
+    rng = np.random.default_rng(N * T)
+    gs = [torch.tensor(rng.standard_normal((B, N, N)), device="cuda", dtype=torch.float32)
+          for _ in range(3)]
+    a = h.plv_backward(x, C, *gs)
+    b = h.plv_backward_saved(saved, C, *gs)
+    c = h.plv_backward_saved(saved, C, None, None, gs[2])
+    d = h.plv_backward(x, C, None, None, gs[2])
+    torch.cuda.synchronize()
+    assert h.plv_sync_status() == 0
+    assert torch.equal(a, b)
+    assert torch.equal(c, d)
+    ref = oracle.connectivity(x[0].double().cpu().numpy())
+    compare({k: res[k][0].double().cpu().numpy() for k in ("plv", "iplv", "ciplv")}, ref,
+            TOL[prec])
+    h.close()
+
+
+def test_saved_mode_autograd():
+    """connectivity(recompute=False) keeps the phasors for the backward pass:
+    its gradient of a ciPLV loss matches the recomputing path's (their
+    forward phasors differ only in the last bits on a BF16X3 handle), and
+    FP16X3 handles refuse the saved form."""
+    import paper_1710_08037_gb300 as plv
+    from paper_1710_08037_gb300 import _lib
+    h = plv.Handle(precision="bf16x3")
+    B, N, T = 2, 96, 2048
+    x0 = synth.bandlimited(B, N, T, seed=31, band=(8, 40), device="cuda")
+    rng = np.random.default_rng(5)
+    w = torch.tensor(rng.standard_normal((B, N, N)), device="cuda", dtype=torch.float32)
+    grads = []
+    for recompute in (True, False):
+        x = x0.clone().requires_grad_(True)
+        _, _, ciplv = plv.connectivity(x, h, recompute=recompute)
+        (ciplv * w).sum().backward()
+        grads.append(x.grad.detach().clone())
+    rel = float(torch.linalg.norm(grads[0] - grads[1]) / torch.linalg.norm(grads[0]))
+    assert rel < 1e-4, rel
+    h16 = plv.Handle(precision="fp16x3")
+    with pytest.raises(_lib.PlvError) as ei:
+        h16.plv_analytic_save(x0)
+    assert ei.value.status == _lib.PLV_ERR_UNSUPPORTED
+    h16.close()
+    h.close()
