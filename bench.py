@@ -164,10 +164,10 @@ class ClockSampler:
 # epoch: its tiles never span epochs).  Keyed by kernel, workload and
 # precision; an entry is removed when the kernel changes after its capture.
 TRAFFIC = {
-    # k_gram_tc on bandlimited-N8192-T8192-E2 (super-block raster of width 16,
+    # k_gram_tc on bandlimited-N8192-T8192-E2 (super-block raster of width 8,
     # MMA width per tile, collector-buffer A reuse, 1024-sample summation
     # chunks), read + write of its 4th launch, scaled by 20 / 2 epochs
-    ("k_gram_tc", "bandlimited-N8192-T8192-E20", "bf16x3"): (9.320439040e9 + 2.290635264e9) * 10,
+    ("k_gram_tc", "bandlimited-N8192-T8192-E20", "bf16x3"): (9.401593344e9 + 2.281091840e9) * 10,
 }
 
 

@@ -99,7 +99,7 @@ plv_precision plv_get_precision(const plv_handle *h);
  * Eq. 7 tiles, which changes which CTA computes a tile, never its value).
  * The 128 x 128 upper-triangle tiles of each epoch go by super-columns of
  * `width` 128-row blocks, so that the tiles running at the same time share
- * their row panels in L2.  width 0 restores the default (16); a width of at
+ * their row panels in L2.  width 0 restores the default (8); a width of at
  * least ceil(N / 128) gives the plain column-major triangle.  FP32 handles
  * accept and ignore it.  PLV_ERR_INVALID for a NULL handle or width < 0. */
 plv_status plv_set_gram_raster(plv_handle *h, int width);

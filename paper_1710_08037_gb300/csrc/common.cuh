@@ -165,7 +165,7 @@ struct GroupConfig {
 };
 
 // Default raster width of the single-problem Gram's tile order (k_gram_tc.cu).
-constexpr int kDefaultRaster = 16;
+constexpr int kDefaultRaster = 8;
 // Default bound of every wait of the tensor-core Gram's pipeline (4 s).  The
 // clean-up waits of an aborting CTA keep their own fixed bound (0.1 s).
 constexpr uint64_t kDefaultWaitNs = 4000000000ull;
