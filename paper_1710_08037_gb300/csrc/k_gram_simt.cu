@@ -21,15 +21,6 @@ constexpr int BM = 128;      // tile edge (rows of I and of J)
 constexpr int BK = 8;        // samples per stage
 constexpr int LDS = BM + 4;  // padded shared row (conflict-free transposed store)
 
-__device__ __forceinline__ void tile_of(int t, int &I, int &J) {
-    // column-major enumeration of the upper triangle: t = J (J+1) / 2 + I
-    int j = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((j + 1) * (j + 2) / 2 <= t) ++j;
-    while (j * (j + 1) / 2 > t) --j;
-    J = j;
-    I = t - j * (j + 1) / 2;
-}
-
 // Output matrix e is window w = e % nw of epoch e / nw: samples t0 + w hop
 // .. + kl (kl, t0, hop multiples of BK; one window of kl = ld for the whole
 // epoch).
@@ -42,7 +33,7 @@ k_gram_fp32(const float *__restrict__ P, int N, int kl, int64_t ld,
 
     const int e = blockIdx.x / tiles_per_epoch;
     int I, J;
-    tile_of(blockIdx.x - e * tiles_per_epoch, I, J);
+    upper_tile_of(blockIdx.x - e * tiles_per_epoch, I, J);
     const int eb = e / nw, w = e - eb * nw;
     const float *Pe = P + (int64_t)eb * N * 2 * ld + t0 + (int64_t)w * hop;
 

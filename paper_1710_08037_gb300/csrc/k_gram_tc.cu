@@ -279,48 +279,6 @@ __device__ __forceinline__ int mma_width(int valid) {
     return valid >= TN ? TN : ((valid + 15) & ~15);
 }
 
-__device__ __forceinline__ void tile_of(int t, int &I, int &J) {
-    int j = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((j + 1) * (j + 2) / 2 <= t) ++j;
-    while (j * (j + 1) / 2 > t) --j;
-    J = j;
-    I = t - j * (j + 1) / 2;
-}
-
-// Tile order of a single problem's epoch.  The persistent CTAs take items
-// round-robin, so G consecutive items (G = the grid) run at about the same
-// time and stream their row panels through L2 together; an order whose G
-// consecutive tiles touch few distinct row blocks re-reads fewer panels from
-// DRAM.  Tiles go by super-columns of W block columns; in each, the
-// off-diagonal super-blocks (W rows x wj columns, column-major), then the
-// diagonal super-block's triangle (column-major).  With nrb <= W this is the
-// plain column-major triangle.  (A lockstep model of N = 8192, 152 CTAs:
-// 431 panel reads per epoch at W = 16 against 639 for the column-major
-// triangle.)  The order changes which CTA computes a tile, never its value.
-__device__ __forceinline__ void tile_raster(int t, int nrb, int W, int &I, int &J) {
-    int SJ = 0, wj = nrb < W ? nrb : W;
-    for (;;) {
-        const int cnt = SJ * W * wj + wj * (wj + 1) / 2;  // tiles of super-column SJ
-        if (t < cnt) break;
-        t -= cnt;
-        ++SJ;
-        wj = nrb - SJ * W < W ? nrb - SJ * W : W;
-    }
-    const int offd = SJ * W * wj;
-    if (t < offd) {
-        const int SI = t / (W * wj);
-        const int r = t - SI * W * wj;
-        const int jj = r / W;
-        I = SI * W + (r - jj * W);
-        J = SJ * W + jj;
-    } else {
-        int ii, jj;
-        tile_of(t - offd, ii, jj);
-        I = SJ * W + ii;
-        J = SJ * W + jj;
-    }
-}
-
 struct TcArgs {
     TcProblem single;         // the problem when items == nullptr
     const TcProblem *probs;   // group: problem descriptors

@@ -2,8 +2,10 @@
 against the built library (pure host functions: no GPU needed):
 - the autotuner's work lists: plv::gram_order (the grouped Gram's tile
   schedules), plv::gram_list with split K (parts of whole chunks covering
-  every tile once, their slots and counters) and plv::k1_layout (the grouped
-  analytic signal's items by thread class);
+  every tile once, their slots and counters), plv::tile_raster (the
+  single-problem Gram's tile order: a permutation of the upper triangle for
+  every width) and plv::k1_layout (the grouped analytic signal's items by
+  thread class);
 - the any-length plans: the transform length for T, its radix order, and
   the FP64 inverse DFT of any length that builds the band kernels, against
   a direct sum."""
@@ -140,6 +142,29 @@ int main() {
         CHECK(L.parts.size() == 5 && L.ntiles == 1 && L.nslots == 5);
         CHECK(L.parts[0].kb_lo == 0 && L.parts[4].kb_hi == 313);
     }
+    // the single-problem tile raster: for every width and triangle size, a
+    // permutation of the upper-triangle tiles, each super-column of W block
+    // columns before the next, and the plain column-major triangle when W >= nrb
+    for (int nrb = 1; nrb <= 70; ++nrb)
+        for (int W = 1; W <= 20; ++W) {
+            const int n = nrb * (nrb + 1) / 2;
+            std::vector<char> seen((size_t)nrb * nrb, 0);
+            int prev_sj = 0;
+            for (int t = 0; t < n; ++t) {
+                int I = -1, J = -1;
+                tile_raster(t, nrb, W, I, J);
+                CHECK(0 <= I && I <= J && J < nrb);
+                CHECK(!seen[(size_t)I * nrb + J]);
+                seen[(size_t)I * nrb + J] = 1;
+                CHECK(J / W >= prev_sj);
+                prev_sj = J / W;
+                if (W >= nrb) {
+                    int I0, J0;
+                    upper_tile_of(t, I0, J0);
+                    CHECK(I0 == I && J0 == J);
+                }
+            }
+        }
     // grouped analytic signal: problems with transform lengths in all classes
     const int Ms[6] = {1280, 20480, 4096, 1280, 10240, 768};
     const long rows[6] = {70, 40, 201, 1, 130, 9};
